@@ -1,0 +1,233 @@
+/*
+ * finger.h — C ABI of the GB300 (sm_103a) FINGER search library, libfinger.so.
+ *
+ * FINGER (Chen, Chang, Yu, Dhillon, Hsieh, arXiv 2206.11408) speeds up greedy
+ * search on a proximity graph by estimating most neighbour distances from a
+ * rank-r model of the residual angle and computing the exact distance only
+ * when the estimate does not exceed the current upper bound.
+ *
+ * Conventions for every entry point
+ *   - Distances are squared L2 (the paper's L2 distance, Sec. 3.2, squared; the
+ *     order is the same).  Keys are (distance, id), compared lexicographically.
+ *   - "device" pointers are CUDA global-memory addresses on the index's device;
+ *     "host" pointers are ordinary (preferably pinned) CPU memory.  The caller
+ *     owns every buffer it passes; the library owns the index and its scratch.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Calls that take a stream are asynchronous on it; argument errors are
+ *     returned synchronously, before anything is enqueued.  Errors raised
+ *     inside a kernel (an iteration or capacity limit) are latched in a device
+ *     status word and returned by finger_get_stats() and finger_sync().
+ *   - No entry point falls back to the CPU: the compute runs in this library's
+ *     CUDA kernels or the call fails.
+ *   - The library is not thread-safe for concurrent calls on one index.
+ */
+#ifndef FINGER_H
+#define FINGER_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct finger_index finger_index; /* opaque, library-owned */
+
+typedef enum {
+    FINGER_OK = 0,
+    FINGER_ERR_INVALID_ARG = 1, /* bad pointer, size, K > ef, ef above capacity, ... */
+    FINGER_ERR_IO = 2,          /* file could not be opened, read or written */
+    FINGER_ERR_FORMAT = 3,      /* index file with wrong magic, version or sizes */
+    FINGER_ERR_OOM = 4,         /* device or host allocation failed */
+    FINGER_ERR_CUDA = 5,        /* a CUDA runtime call failed */
+    FINGER_ERR_NOT_BUILT = 6,   /* graph or FINGER tables missing for the request */
+    FINGER_ERR_LIMIT = 7,       /* a kernel hit an iteration/capacity bound (latched) */
+    FINGER_ERR_UNSUPPORTED = 8  /* a size this build does not handle (e.g. m > 1024) */
+} finger_status;
+
+/* search modes (finger_set_mode) */
+enum {
+    FINGER_MODE_PLAIN = 0,      /* Algorithm 1: exact distance for every new neighbour */
+    FINGER_MODE_FINGER = 1,     /* Algorithm 4 with Algorithm 3 as the gate */
+    FINGER_MODE_FINGER_LP = 2,  /* Algorithm 4 on BF16 rows and FP8-e4m3 residual codes,
+                                   FP32 accumulation, final top-K re-ranked in FP32 */
+    FINGER_MODE_FINGER_MLP = 3  /* Algorithm 4 with a learned angle predictor in place of
+                                   distribution matching; matching is the fallback */
+};
+
+/* --------------------------------------------------------------- index */
+
+/* Create an index on CUDA device `device` from n row-major FP32 vectors of
+ * dimension m (host pointer, n*m floats, copied).  1 <= m <= 1024, n < 2^31.
+ * The index has no graph yet. */
+finger_status finger_index_create(int device, int64_t n, int m, const float* vectors_host,
+                                  finger_index** out);
+
+/* Attach an HNSW-style graph given in host arrays (copied):
+ *   adj0     n x deg0 int32  layer-0 neighbour lists, valid ids first, -1 pad,
+ *                            no duplicates and no self-loops within a row
+ *   level    n int32         top level of each node (0 for layer-0 only)
+ *   up_off   n int64         row of (v, level 1) in up_adj, -1 if level[v] == 0;
+ *                            rows of levels 1..level[v] are consecutive
+ *   up_adj   up_rows x M int32  upper-level neighbour lists, -1 pad
+ *   entry, maxlevel          entry point (level[entry] == maxlevel)
+ * deg0 <= 64, M <= 32.  Invalidates FINGER tables built for a previous graph. */
+finger_status finger_index_set_graph(finger_index* ix, int deg0, const int32_t* adj0,
+                                     const int32_t* level, const int64_t* up_off,
+                                     int64_t up_rows, int M, const int32_t* up_adj,
+                                     int32_t entry, int32_t maxlevel);
+
+typedef struct {
+    int M;                /* degree cap on levels >= 1; layer 0 allows 2M (<= 32) */
+    int candidates;       /* exact nearest neighbours offered to the pruning step
+                             (<= 128; 0 = 2 * 2M) */
+    uint64_t level_seed;  /* seed of the level draw floor(-ln U / ln M) */
+} finger_graph_params;
+
+/* Build an HNSW-style graph on the device: levels drawn as in HNSW from a
+ * counter-based generator, then for every level the exact k nearest neighbours
+ * among that level's nodes (brute force on the GPU), heuristic neighbour
+ * selection (keep a candidate only if it is closer to the node than to every
+ * neighbour kept so far, as in HNSW), reverse edges, and a second heuristic
+ * pass to the degree cap.  Synchronous (returns when the graph is built). */
+finger_status finger_build_graph(finger_index* ix, const finger_graph_params* p, void* stream);
+
+/* Copy the graph back to host arrays of the sizes given by finger_get_info().
+ * Any pointer may be NULL to skip that array. */
+finger_status finger_get_graph(const finger_index* ix, int32_t* adj0, int32_t* level,
+                               int64_t* up_off, int32_t* up_adj, int32_t* entry,
+                               int32_t* maxlevel);
+
+typedef struct {
+    int64_t n;
+    int m;
+    int deg0;
+    int M;
+    int maxlevel;
+    int entry;
+    int64_t up_rows;
+    int r;               /* FINGER rank, 0 before finger_build_tables */
+    int has_lp;          /* BF16/FP8 tables present */
+    int has_mlp;         /* learned predictor present */
+    int64_t device_bytes;/* device memory held by the index */
+} finger_info;
+
+finger_status finger_get_info(const finger_index* ix, finger_info* out);
+
+/* Save / load the whole index (vectors, graph, tables, predictor) in a
+ * versioned little-endian binary file.  load places it on `device`. */
+finger_status finger_index_save(const finger_index* ix, const char* path);
+finger_status finger_index_load(const char* path, int device, finger_index** out);
+void finger_index_free(finger_index* ix);
+
+/* ------------------------------------------------------- FINGER tables */
+
+typedef struct {
+    int r;                    /* rank, 1 <= r <= 64 (Sec. 3.3, Supplementary E) */
+    uint64_t seed;            /* seed of the neighbour-pair draw of Algorithm 2 */
+    int samples_per_node;     /* pairs drawn per node (Algorithm 2 draws one); 0 = 1 */
+    const float* basis_host;  /* optional r x m row-major P; NULL = SVD on the device */
+    const double* stats_host; /* optional {mu, sigma, mu_hat, sigma_hat, eps};
+                                 NULL = computed from the sampled pairs */
+    int build_lp;             /* also build BF16 rows and FP8-e4m3 codes (mode LP) */
+} finger_build_params;
+
+/* Algorithm 2 and Supplementary G on the device.  For every node c with at
+ * least two layer-0 neighbours a pair (d, d') is drawn with the counter rule
+ *   h1 = splitmix64(seed ^ (c * spn + k)), h2 = splitmix64(h1),
+ *   i = h1 mod deg(c), j = h2 mod (deg(c) - 1), j += (j >= i)
+ * (i, j index the valid neighbours in row order); D_res collects
+ * d_res = d - (c^T d / c^T c) c; P = top-r eigenvectors of D_res D_res^T
+ * (= U_{1:r}^T of the SVD, Proposition 1) by FP64 Jacobi; then per node
+ * ||c||^2 and P c, per layer-0 edge (c, d) the row (P d_res / ||P d_res||,
+ * ||d_res||, c^T d / c^T c) — (r + 2) floats per edge slot, Supplementary F —
+ * and the matching statistics mu, sigma, mu_hat, sigma_hat (standard
+ * deviations) and eps of Algorithm 2 over the drawn pairs, with
+ * X = cos(d_res, d'_res), Y = cos(P d_res, P d'_res).  Synchronous. */
+finger_status finger_build_tables(finger_index* ix, const finger_build_params* p, void* stream);
+
+/* Copy FINGER tables to host buffers (any may be NULL):
+ *   P r x m, stats[5] as above, node_proj n x r (P c), edge_u (n*deg0) x r,
+ *   edge_s (n*deg0) x 2 {||d_res||, b} (zeros for -1 slots). */
+finger_status finger_get_tables(const finger_index* ix, float* P, double* stats, float* node_proj,
+                                float* edge_u, float* edge_s);
+
+/* Bytes of the per-edge FINGER tables for n nodes, layer-0 degree deg0 and
+ * rank r: (r + 2) * n * deg0 * 4 for FP32 (Supplementary F); for the LP
+ * tables r_pad16 bytes of FP8 codes + 8 bytes of scalars per edge slot. */
+int64_t finger_table_bytes(int64_t n, int deg0, int r, int lp);
+
+/* -------------------------------------------------------------- search */
+
+/* Set the search mode (FINGER_MODE_*) and the warm-up: the first `warmup`
+ * layer-0 expansions of every query use exact distances only (Algorithm 4,
+ * "#updates of cur > 5"; default 5).  warmup < 0 leaves it unchanged. */
+finger_status finger_set_mode(finger_index* ix, int mode, int warmup);
+
+/* Greedy search for nq queries (device, nq x m row-major FP32): descent with
+ * ef = 1 through levels maxlevel..1, then Algorithm 1 (PLAIN) or Algorithm 4
+ * (FINGER modes) on layer 0 with a result list of ef entries.  Writes the K
+ * best (ascending (distance, id)) to out_ids (device, nq x K int64) and
+ * out_dists (device, nq x K float); rows with fewer than K results are padded
+ * with id -1 and distance +inf.  1 <= K <= ef <= 1024.  Asynchronous. */
+finger_status finger_search(finger_index* ix, const float* queries, int64_t nq, int K, int ef,
+                            int64_t* out_ids, float* out_dists, void* stream);
+
+/* finger_search on HOST buffers: copies the queries in, searches, copies the
+ * results out and synchronises `stream` before returning. */
+finger_status finger_search_host(finger_index* ix, const float* queries_host, int64_t nq, int K,
+                                 int ef, int64_t* out_ids_host, float* out_dists_host,
+                                 void* stream);
+
+/* Uneven batch: per-query K[i] and ef[i] (device int32 arrays, K[i] <= ef[i]),
+ * results of query i at out_ids[out_off[i] .. out_off[i] + K[i]) (device
+ * int64 offsets).  One persistent launch sized for max ef; replayed from a
+ * captured CUDA graph when the (nq, max ef) shape was seen before.
+ * max_ef must bound every ef[i] (the host does not read the device arrays). */
+finger_status finger_search_batch(finger_index* ix, const float* queries, int64_t nq,
+                                  const int32_t* K, const int32_t* ef, int max_ef,
+                                  const int64_t* out_off, int64_t* out_ids, float* out_dists,
+                                  void* stream);
+
+/* Autotuner for finger_search_batch: times the candidate launch shapes (warps
+ * per block x visited-hash size) of the power-of-two ef bucket of `ef` on a
+ * sample batch (device queries, nq x m, uniform K and ef; scratch outputs of
+ * nq x K) and keeps the fastest for later batches of that bucket.  The best
+ * time in milliseconds is written to *best_ms when it is not NULL. */
+finger_status finger_autotune(finger_index* ix, const float* queries, int64_t nq, int K, int ef,
+                              int64_t* scratch_ids, float* scratch_dists, float* best_ms,
+                              void* stream);
+
+/* Per-query traversal counters of the last search (device int32, nq x 8:
+ * expansions, examined, estimates, skipped, exact, admitted, upper, gathered)
+ * are written when `counters` is set here (NULL disables). */
+finger_status finger_set_counters(finger_index* ix, int32_t* counters_device);
+
+/* ------------------------------------------------------- ground truth */
+
+/* Exact K nearest neighbours of nq queries (device, nq x m) over all n base
+ * rows by brute force on the GPU; ascending (distance, id), distances summed
+ * as (q - x)^2 in FP32.  K <= 256.  Asynchronous. */
+finger_status finger_knn(finger_index* ix, const float* queries, int64_t nq, int K,
+                         int64_t* out_ids, float* out_dists, void* stream);
+
+/* --------------------------------------------------- status and stats */
+
+typedef struct {
+    int64_t searches;       /* queries searched since the last reset */
+    int64_t counters[8];    /* summed traversal counters (order as above) */
+    int32_t device_error;   /* latched FINGER_ERR_* from kernels, 0 if none */
+    double mu, sigma, mu_hat, sigma_hat, eps; /* matching statistics */
+    double build_ms;        /* wall time of the last table build */
+} finger_stats;
+
+/* Synchronise the index's device and return the latched kernel status. */
+finger_status finger_sync(finger_index* ix);
+finger_status finger_get_stats(finger_index* ix, finger_stats* out);
+finger_status finger_reset_stats(finger_index* ix);
+const char* finger_status_str(finger_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FINGER_H */

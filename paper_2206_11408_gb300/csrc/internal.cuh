@@ -1,0 +1,176 @@
+// Internal declarations of libfinger.so (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+#include <stdint.h>
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/finger.h"
+
+namespace fg {
+
+constexpr uint32_t PAD = 0xFFFFFFFFu;     // empty adjacency slot / empty hash slot
+constexpr uint32_t EXP = 0x80000000u;     // "expanded" flag kept in the result-list ids
+constexpr int MAX_M = 1024;
+constexpr int MAX_DEG0 = 64;
+constexpr int MAX_MUP = 32;
+constexpr int MAX_R = 64;
+constexpr int MAX_EF = 1024;
+constexpr int MLP_H = 64;                 // hidden width of the learned predictor
+
+// Device view of an index, passed by value to the kernels.
+struct DevIndex {
+    int64_t n;
+    int m, m4, m8;          // dims; float4 chunks per FP32 row; uint4 chunks per BF16 row
+    int deg0, Mup, maxlevel, entry;
+    const float4* X;        // n x m4
+    const float* xnorm2;    // n
+    const uint32_t* adj0;   // n x deg0
+    const int64_t* up_off;  // n
+    const uint32_t* up_adj; // up_rows x Mup
+    // FINGER tables
+    int r, r4, r16;         // rank; float4 chunks of r_pad; uint4 chunks of the FP8 codes
+    const float4* P;        // r_pad x m4
+    const float4* Pc;       // n x r4
+    const float4* edge_u;   // (n*deg0) x r4
+    const float2* edge_s;   // n*deg0: {||d_res||, b}
+    float alpha, beta;      // t = t_hat * alpha + beta
+    // reduced precision
+    const uint4* Xh;        // n x m8 (BF16)
+    const uint4* edge_q;    // (n*deg0) x r16 FP8-e4m3 codes of edge_u * code_scale
+    float code_inv;         // 1 / code_scale
+    // learned predictor: BF16 weights W1 (H x (r+4)), W2 (H x H), w3 (H); FP32 biases
+    const __nv_bfloat16* W1;
+    const __nv_bfloat16* W2;
+    const __nv_bfloat16* w3;
+    const float* b1;
+    const float* b2;
+    float b3, mlp_eps;
+};
+
+struct SearchArgs {
+    const float* Q;         // nq x m (row stride m)
+    int64_t nq;
+    int K, ef;              // uniform K / ef (batch arrays override when non-null)
+    const int32_t* K_arr;
+    const int32_t* ef_arr;
+    const int64_t* out_off;
+    int64_t* out_ids;
+    float* out_d;
+    int warmup;
+    int ef_cap, H, rerank;
+    int max_expansions;
+    uint32_t* work;         // [0] = next query
+    int* err;
+    unsigned long long* cnt;   // 8 summed counters
+    int32_t* cnt_q;            // nq x 8 or null
+    uint32_t* bitmap;          // slots x words
+    int64_t words;
+    uint32_t* spill;           // slots x spill_cap
+    int spill_cap;
+    int warp_smem;             // bytes per warp
+    // harvest (learned predictor training data); null when off
+    float* hv_feat;            // cap x (r+4)
+    float* hv_target;          // cap
+    unsigned long long* hv_count;
+    int64_t hv_cap;
+};
+
+struct SearchPlan {
+    int mode;
+    int G, VPL, NPL;
+    int wpb;            // warps per block
+    int blocks;
+    int ef_cap, H;
+    int smem_per_warp;
+};
+
+// kernels / launchers (search.cu)
+cudaError_t launch_search(const DevIndex& ix, const SearchArgs& a, const SearchPlan& p,
+                          cudaStream_t s);
+int search_smem_per_warp(const DevIndex& ix, int mode, int ef_cap, int H, int NPL);
+cudaError_t search_occupancy(const DevIndex& ix, const SearchPlan& p, int* blocks_per_sm);
+void choose_groups(int nchunks, int* G, int* VPL);
+
+// brute force (build.cu)
+cudaError_t launch_knn(const float4* Xb, int64_t nb, int m4, const float* Q, int64_t q_stride,
+                       int q_m, int64_t nq, int K, bool exclude_self, const int32_t* remap,
+                       int64_t* out_ids, float* out_d, cudaStream_t s);
+size_t knn_smem(int K);
+
+// graph construction (graph.cu)
+finger_status build_graph(finger_index* ix, const finger_graph_params* p, cudaStream_t s);
+// FINGER tables (tables.cu)
+finger_status build_tables(finger_index* ix, const finger_build_params* p, cudaStream_t s);
+cudaError_t launch_xnorm2(const float4* X, int64_t n, int m4, float* out, cudaStream_t s);
+cudaError_t launch_to_bf16(const float* X, int64_t n, int m_pad, int m8, __nv_bfloat16* out,
+                           cudaStream_t s);
+
+}  // namespace fg
+
+// The index object behind the opaque handle.
+struct finger_index {
+    int device = 0;
+    int num_sms = 0;
+    int64_t n = 0;
+    int m = 0, m_pad = 0, m4 = 0, m8 = 0;
+    float* X = nullptr;
+    float* xnorm2 = nullptr;
+    // graph
+    int deg0 = 0, M = 0, maxlevel = 0, entry = 0;
+    int64_t up_rows = 0;
+    uint32_t* adj0 = nullptr;
+    int64_t* up_off = nullptr;
+    uint32_t* up_adj = nullptr;
+    std::vector<int32_t> h_level;
+    // FINGER tables
+    int r = 0, r_pad = 0;
+    float* P = nullptr;
+    float* Pc = nullptr;
+    float* edge_u = nullptr;
+    float2* edge_s = nullptr;
+    double stats[5] = {0, 0, 0, 0, 0};
+    // LP tables
+    __nv_bfloat16* Xh = nullptr;
+    uint8_t* edge_q = nullptr;
+    int r16 = 0;
+    float code_scale = 256.0f;
+    // learned predictor
+    int has_mlp = 0;
+    __nv_bfloat16* W1 = nullptr;
+    __nv_bfloat16* W2 = nullptr;
+    __nv_bfloat16* w3 = nullptr;
+    float* b1 = nullptr;
+    float* b2 = nullptr;
+    float b3 = 0.f, mlp_eps = 0.f;
+    std::vector<float> h_mlp;     // FP32 master copy (W1, b1, W2, b2, w3, b3)
+    // search state
+    int mode = FINGER_MODE_PLAIN;
+    int warmup = 5;
+    int32_t* cnt_q = nullptr;
+    // scratch
+    uint32_t* work = nullptr;     // 4 words
+    int* err = nullptr;
+    unsigned long long* cnt = nullptr;
+    uint32_t* bitmap = nullptr;
+    int64_t bitmap_slots = 0, words = 0;
+    uint32_t* spill = nullptr;
+    int spill_cap = 0;
+    // staging for host-buffer search
+    float* stage_q = nullptr;
+    int64_t* stage_ids = nullptr;
+    float* stage_d = nullptr;
+    int64_t stage_cap_q = 0, stage_cap_o = 0;
+    std::map<int, fg::SearchPlan> tuned;     // autotuned plans keyed by ef bucket
+    int64_t searches = 0;
+    double build_ms = 0;
+    int64_t device_bytes = 0;
+    std::vector<void*> allocs;
+};
+
+fg::DevIndex make_dev(const finger_index* ix);

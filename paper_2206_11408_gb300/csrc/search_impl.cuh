@@ -1,0 +1,673 @@
+// Persistent greedy-search kernel: one warp per query.
+//
+// Layer 0 follows Algorithm 1 (PLAIN) or Algorithm 4 (FINGER modes) of
+// arXiv 2206.11408 with these readings of the paper:
+//   * keys are (distance, id) compared lexicographically;
+//   * a neighbour is admitted iff |T| < ef or its key is below the key of the
+//     worst entry of T (Algorithm 1, "dist <= ub or |T| <= efs" read with the
+//     eviction that keeps |T| <= ef); entries evicted from T are never
+//     expanded, so the candidate queue C is exactly the unexpanded part of T
+//     and one sorted array holds both;
+//   * a neighbour is marked visited before it is evaluated, so one skipped by
+//     the estimate is never examined again;
+//   * from the (warmup+1)-th expansion on, while |T| = ef, a new neighbour
+//     whose estimate (Algorithm 3) exceeds the current ub is skipped; ub is the
+//     distance of the worst entry of T at that moment (neighbours are taken in
+//     adjacency order, so ub can fall between two neighbours of one centre).
+//
+// GB300 mapping.  A warp owns one query from an atomic work counter until the
+// batch is drained (grid = SMs x resident blocks).  Per warp in shared memory:
+// the result list T (keys and ids, the EXP bit marks expanded entries), an
+// exact open-addressing visited hash that spills to a per-warp global bitmap
+// once half full, the unit residual projection of the query, and staging.
+// One expansion is three dependent gathers: the adjacency row (coalesced,
+// lane j <- neighbour j), the per-edge rows of the new neighbours (lane-per-
+// neighbour 16-byte loads, r-dot against the query projection broadcast from
+// shared memory), and the full rows of the neighbours whose estimate passes
+// (groups of G lanes per row, 16-byte loads, shuffle reduction).  Estimates
+// are formed for every new neighbour against the ub at the start of the
+// expansion; the sequential gate is then replayed in adjacency order so the
+// traversal is exactly the per-neighbour one of Algorithm 4.
+#pragma once
+
+#include "internal.cuh"
+
+namespace fg {
+
+#define FULLMASK 0xffffffffu
+
+__device__ __forceinline__ bool key_lt(float da, uint32_t ia, float db, uint32_t ib) {
+    return da < db || (da == db && ia < ib);
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULLMASK, v, o);
+    return v;
+}
+
+template <bool LP, int VPL>
+struct QRegs {
+    float v[VPL][LP ? 8 : 4];
+};
+
+template <bool LP, int G, int VPL>
+__device__ __forceinline__ void load_qregs(QRegs<LP, VPL>& q, const float* qs, int nchunks,
+                                           int kin) {
+    constexpr int W = LP ? 8 : 4;
+#pragma unroll
+    for (int v = 0; v < VPL; ++v) {
+        const int ch = kin + G * v;
+#pragma unroll
+        for (int e = 0; e < W; ++e) q.v[v][e] = ch < nchunks ? qs[ch * W + e] : 0.f;
+    }
+}
+
+__device__ __forceinline__ void bf16x8(const uint4& x, float* f) {
+    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&x);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        float2 t = __bfloat1622float2(h[i]);
+        f[2 * i] = t.x;
+        f[2 * i + 1] = t.y;
+    }
+}
+
+// partial sum of (q - x)^2 over this lane's chunks of row `id`
+template <bool LP, int G, int VPL>
+__device__ __forceinline__ float row_partial(const QRegs<LP, VPL>& q, const DevIndex& ix,
+                                             uint32_t id, int kin) {
+    float acc = 0.f;
+    if constexpr (!LP) {
+        const float4* row = ix.X + (size_t)id * ix.m4;
+        float4 x[VPL];
+#pragma unroll
+        for (int v = 0; v < VPL; ++v) {
+            const int ch = kin + G * v;
+            x[v] = ch < ix.m4 ? __ldg(row + ch) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int v = 0; v < VPL; ++v) {
+            float d;
+            d = q.v[v][0] - x[v].x; acc = fmaf(d, d, acc);
+            d = q.v[v][1] - x[v].y; acc = fmaf(d, d, acc);
+            d = q.v[v][2] - x[v].z; acc = fmaf(d, d, acc);
+            d = q.v[v][3] - x[v].w; acc = fmaf(d, d, acc);
+        }
+    } else {
+        const uint4* row = ix.Xh + (size_t)id * ix.m8;
+        uint4 x[VPL];
+#pragma unroll
+        for (int v = 0; v < VPL; ++v) {
+            const int ch = kin + G * v;
+            x[v] = ch < ix.m8 ? __ldg(row + ch) : make_uint4(0u, 0u, 0u, 0u);
+        }
+#pragma unroll
+        for (int v = 0; v < VPL; ++v) {
+            float f[8];
+            bf16x8(x[v], f);
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const float d = q.v[v][e] - f[e];
+                acc = fmaf(d, d, acc);
+            }
+        }
+    }
+    return acc;
+}
+
+// exact distances of the rows nbs[lst[i]], i < nlist, into xb[lst[i]]
+template <bool LP, int G, int VPL>
+__device__ __forceinline__ void exact_list(const QRegs<LP, VPL>& q, const DevIndex& ix,
+                                           const uint32_t* nbs, const int* lst, int nlist,
+                                           float* xb, int lane) {
+    constexpr int RPW = 32 / G;
+    const int grp = lane / G, kin = lane % G;
+    for (int base = 0; base < nlist; base += 2 * RPW) {
+        const int i0 = base + grp, i1 = base + RPW + grp;
+        const int o0 = i0 < nlist ? lst[i0] : -1;
+        const int o1 = i1 < nlist ? lst[i1] : -1;
+        float p0 = 0.f, p1 = 0.f;
+        if (o0 >= 0) p0 = row_partial<LP, G, VPL>(q, ix, nbs[o0], kin);
+        if (o1 >= 0) p1 = row_partial<LP, G, VPL>(q, ix, nbs[o1], kin);
+#pragma unroll
+        for (int off = G / 2; off > 0; off >>= 1) {
+            p0 += __shfl_xor_sync(FULLMASK, p0, off);
+            p1 += __shfl_xor_sync(FULLMASK, p1, off);
+        }
+        if (kin == 0) {
+            if (o0 >= 0) xb[o0] = p0;
+            if (o1 >= 0) xb[o1] = p1;
+        }
+    }
+    __syncwarp();
+}
+
+// exact FP32 distance of one row, whole warp (used for the FP32 re-rank)
+__device__ __forceinline__ float exact_f32_row(const float* qs, const DevIndex& ix, uint32_t id,
+                                               int lane) {
+    const float4* row = ix.X + (size_t)id * ix.m4;
+    const float4* q4 = reinterpret_cast<const float4*>(qs);
+    float acc = 0.f;
+    for (int k = lane; k < ix.m4; k += 32) {
+        const float4 x = __ldg(row + k);
+        const float4 y = q4[k];
+        float d;
+        d = y.x - x.x; acc = fmaf(d, d, acc);
+        d = y.y - x.y; acc = fmaf(d, d, acc);
+        d = y.z - x.z; acc = fmaf(d, d, acc);
+        d = y.w - x.w; acc = fmaf(d, d, acc);
+    }
+    return warp_sum(acc);
+}
+
+__device__ __forceinline__ int find_next(const uint32_t* Ti, int sz, int from, int lane) {
+    for (int b = from; b < sz; b += 32) {
+        const int i = b + lane;
+        const bool un = i < sz && !(Ti[i] & EXP);
+        const unsigned m = __ballot_sync(FULLMASK, un);
+        if (m) return b + __ffs(m) - 1;
+    }
+    return sz;
+}
+
+// insert key (d, id) into the sorted list T (size sz <= ef), dropping the
+// worst entry when full.  Caller has checked admission.
+__device__ __forceinline__ void t_insert(float* Tk, uint32_t* Ti, int& sz, int ef, float d,
+                                         uint32_t id, int& cursor, int lane) {
+    int p = 0;
+    for (int b = 0; b < sz; b += 32) {
+        const int i = b + lane;
+        const bool lt = i < sz && key_lt(Tk[i], Ti[i] & ~EXP, d, id);
+        p += __popc(__ballot_sync(FULLMASK, lt));
+    }
+    const int last = sz < ef ? sz : ef - 1;
+    for (int top = last - 1; top >= p; top -= 32) {
+        const int i = top - lane;
+        const bool act = i >= p;
+        float kd = 0.f;
+        uint32_t ki = 0;
+        if (act) {
+            kd = Tk[i];
+            ki = Ti[i];
+        }
+        __syncwarp();
+        if (act) {
+            Tk[i + 1] = kd;
+            Ti[i + 1] = ki;
+        }
+        __syncwarp();
+    }
+    if (lane == 0) {
+        Tk[p] = d;
+        Ti[p] = id;
+    }
+    __syncwarp();
+    if (sz < ef) sz++;
+    if (p < cursor) cursor = p;
+}
+
+enum { V_SEEN = 0, V_NEW = 1, V_NEW_SPILL = 2 };
+
+__device__ __forceinline__ uint32_t hslot(uint32_t id, int logH) {
+    return (id * 2654435769u) >> (32 - logH);
+}
+
+// exact test-and-set of the visited set
+__device__ __forceinline__ int visit(uint32_t* hash, int H, int logH, uint32_t id, bool spill_mode,
+                                     uint32_t* bitmap) {
+    uint32_t h = hslot(id, logH);
+    for (int probe = 0; probe < H; ++probe) {
+        if (!spill_mode) {
+            const uint32_t old = atomicCAS(&hash[h], PAD, id);
+            if (old == PAD) return V_NEW;
+            if (old == id) return V_SEEN;
+        } else {
+            const uint32_t v = hash[h];
+            if (v == id) return V_SEEN;
+            if (v == PAD) {
+                const uint32_t bit = 1u << (id & 31);
+                const uint32_t old = atomicOr(&bitmap[id >> 5], bit);
+                return (old & bit) ? V_SEEN : V_NEW_SPILL;
+            }
+        }
+        h = (h + 1) & (H - 1);
+    }
+    return V_SEEN;  // unreachable: the table is never more than half full plus one batch
+}
+
+// t_hat for one edge: r-dot of the stored unit residual projection with uq
+template <bool LP>
+__device__ __forceinline__ float edge_cos(const DevIndex& ix, size_t e, const float* uq) {
+    float acc = 0.f;
+    if constexpr (!LP) {
+        const float4* u = ix.edge_u + e * ix.r4;
+        const float4* v = reinterpret_cast<const float4*>(uq);
+#pragma unroll 4
+        for (int k = 0; k < ix.r4; ++k) {
+            const float4 x = __ldg(u + k);
+            const float4 y = v[k];
+            acc = fmaf(x.x, y.x, acc);
+            acc = fmaf(x.y, y.y, acc);
+            acc = fmaf(x.z, y.z, acc);
+            acc = fmaf(x.w, y.w, acc);
+        }
+    } else {
+        const uint4* u = ix.edge_q + e * ix.r16;
+        for (int k = 0; k < ix.r16; ++k) {
+            const uint4 x = __ldg(u + k);
+            const uint32_t w[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const __half2_raw lo = __nv_cvt_fp8x2_to_halfraw2(
+                    (__nv_fp8x2_storage_t)(w[i] & 0xFFFFu), __NV_E4M3);
+                const __half2_raw hi = __nv_cvt_fp8x2_to_halfraw2(
+                    (__nv_fp8x2_storage_t)(w[i] >> 16), __NV_E4M3);
+                const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&lo));
+                const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&hi));
+                const float* y = uq + k * 16 + i * 4;
+                acc = fmaf(a.x, y[0], acc);
+                acc = fmaf(a.y, y[1], acc);
+                acc = fmaf(b.x, y[2], acc);
+                acc = fmaf(b.y, y[3], acc);
+            }
+        }
+        acc *= ix.code_inv;
+    }
+    return acc;
+}
+
+// learned predictor: t = w3 . relu(W2 relu(W1 f + b1) + b2) + b3, features f of
+// length r+4 (uq*ud elementwise, t_hat, ||q_res||/||q||, ||d_res||/||d||,
+// a/(|a|+|b|+1e-6)); BF16 weights, FP32 accumulation.
+__device__ __forceinline__ float mlp_predict(const DevIndex& ix, const float* f, int nf) {
+    float h1[MLP_H];
+#pragma unroll 4
+    for (int j = 0; j < MLP_H; ++j) {
+        float acc = ix.b1[j];
+        const __nv_bfloat16* w = ix.W1 + (size_t)j * nf;
+        for (int i = 0; i < nf; ++i) acc = fmaf(__bfloat162float(w[i]), f[i], acc);
+        h1[j] = fmaxf(acc, 0.f);
+    }
+    float out = ix.b3;
+    for (int j = 0; j < MLP_H; ++j) {
+        float acc = ix.b2[j];
+        const __nv_bfloat16* w = ix.W2 + (size_t)j * MLP_H;
+#pragma unroll 8
+        for (int i = 0; i < MLP_H; ++i) acc = fmaf(__bfloat162float(w[i]), h1[i], acc);
+        out = fmaf(__bfloat162float(ix.w3[j]), fmaxf(acc, 0.f), out);
+    }
+    return out;
+}
+
+template <int MODE, int G, int VPL, int NPL>
+__global__ void __launch_bounds__(256) k_search(DevIndex ix, SearchArgs a) {
+    constexpr bool LP = MODE == FINGER_MODE_FINGER_LP;
+    constexpr bool EST = MODE != FINGER_MODE_PLAIN;
+    constexpr bool MLP = MODE == FINGER_MODE_FINGER_MLP;
+    extern __shared__ __align__(16) unsigned char sm[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int wpb = blockDim.x >> 5;
+    const unsigned ltmask = (1u << lane) - 1u;
+    const int r_pad = ix.r4 * 4;
+    const int nchunks = LP ? ix.m8 : ix.m4;
+    const int qs_len = LP ? ix.m8 * 8 : ix.m4 * 4;
+
+    unsigned char* wb = sm + (size_t)wib * a.warp_smem;
+    float* Tk = reinterpret_cast<float*>(wb);
+    uint32_t* Ti = reinterpret_cast<uint32_t*>(Tk + a.ef_cap);
+    uint32_t* hash = Ti + a.ef_cap;
+    float* uq = reinterpret_cast<float*>(hash + a.H);
+    float* pq = uq + r_pad;
+    float* qs = pq + r_pad;
+    uint32_t* nbs = reinterpret_cast<uint32_t*>(qs + ((qs_len + 3) & ~3));
+    float* es = reinterpret_cast<float*>(nbs + 32 * NPL);
+    float* xb = es + 32 * NPL;
+    int* lst = reinterpret_cast<int*>(xb + 32 * NPL);
+
+    const int64_t slot = (int64_t)blockIdx.x * wpb + wib;
+    uint32_t* bitmap = a.bitmap + slot * a.words;
+    uint32_t* spl = a.spill + slot * a.spill_cap;
+    const int logH = 31 - __clz(a.H);
+
+    for (;;) {
+        int qi = 0;
+        if (lane == 0) qi = (int)atomicAdd(a.work, 1u);
+        qi = __shfl_sync(FULLMASK, qi, 0);
+        if (qi >= a.nq) break;
+        const int K = a.K_arr ? a.K_arr[qi] : a.K;
+        const int ef = min(max(a.ef_arr ? a.ef_arr[qi] : a.ef, 1), a.ef_cap);
+        const int64_t ooff = a.out_off ? a.out_off[qi] : (int64_t)qi * K;
+
+        // ---- stage the query (a1: ||q||^2 and P q)
+        const float* qg = a.Q + (size_t)qi * ix.m;
+        for (int i = lane; i < qs_len; i += 32) qs[i] = i < ix.m ? qg[i] : 0.f;
+        __syncwarp();
+        QRegs<LP, VPL> q;
+        load_qregs<LP, G, VPL>(q, qs, nchunks, lane % G);
+        float qn2 = 0.f;
+        for (int i = lane; i < ix.m; i += 32) qn2 = fmaf(qs[i], qs[i], qn2);
+        qn2 = warp_sum(qn2);
+        if constexpr (EST) {
+            for (int i = lane; i < r_pad; i += 32) {
+                const float4* prow = ix.P + (size_t)i * ix.m4;
+                const float4* q4 = reinterpret_cast<const float4*>(qs);
+                float acc = 0.f;
+                for (int k = 0; k < ix.m4; ++k) {
+                    const float4 p = __ldg(prow + k);
+                    const float4 y = q4[k];
+                    acc = fmaf(p.x, y.x, acc);
+                    acc = fmaf(p.y, y.y, acc);
+                    acc = fmaf(p.z, y.z, acc);
+                    acc = fmaf(p.w, y.w, acc);
+                }
+                pq[i] = acc;
+            }
+            __syncwarp();
+        }
+        int c_exp = 0, c_exa = 0, c_est = 0, c_skip = 0, c_exact = 0, c_adm = 0, c_up = 0,
+            c_gath = 0;
+        bool fail = false;
+
+        // ---- a2: greedy descent through levels maxlevel..1 (exact distances)
+        uint32_t cur = (uint32_t)ix.entry;
+        if (lane == 0) {
+            nbs[0] = cur;
+            lst[0] = 0;
+        }
+        __syncwarp();
+        exact_list<LP, G, VPL>(q, ix, nbs, lst, 1, xb, lane);
+        float dcur = xb[0];
+        c_up++;
+        c_gath++;
+        __syncwarp();
+        for (int l = ix.maxlevel; l >= 1; --l) {
+            for (int it = 0;; ++it) {
+                if (it >= a.max_expansions) {
+                    fail = true;
+                    break;
+                }
+                const uint32_t* row = ix.up_adj + (size_t)(ix.up_off[cur] + l - 1) * ix.Mup;
+                const uint32_t id = lane < ix.Mup ? row[lane] : PAD;
+                const bool v = id != PAD;
+                const unsigned bm = __ballot_sync(FULLMASK, v);
+                nbs[lane] = id;
+                if (v) lst[__popc(bm & ltmask)] = lane;
+                __syncwarp();
+                const int cv = __popc(bm);
+                exact_list<LP, G, VPL>(q, ix, nbs, lst, cv, xb, lane);
+                c_up += cv;
+                c_gath += cv;
+                float bd = v ? xb[lane] : INFINITY;
+                uint32_t bi = v ? id : PAD;
+                if (key_lt(dcur, cur, bd, bi)) {
+                    bd = dcur;
+                    bi = cur;
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const float od = __shfl_xor_sync(FULLMASK, bd, o);
+                    const uint32_t oi = __shfl_xor_sync(FULLMASK, bi, o);
+                    if (key_lt(od, oi, bd, bi)) {
+                        bd = od;
+                        bi = oi;
+                    }
+                }
+                __syncwarp();
+                if (bi == cur) break;
+                cur = bi;
+                dcur = bd;
+            }
+        }
+
+        // ---- a3..a6: layer 0
+        for (int i = lane; i < a.H; i += 32) hash[i] = PAD;
+        __syncwarp();
+        if (lane == 0) {
+            Tk[0] = dcur;
+            Ti[0] = cur;
+            hash[hslot(cur, logH)] = cur;
+        }
+        __syncwarp();
+        int sz = 1, cursor = 0, hcount = 1, nspill = 0;
+        bool spill_mode = false;
+        int expansions = 0;
+        while (!fail) {
+            cursor = find_next(Ti, sz, cursor, lane);
+            if (cursor >= sz) break;
+            if (expansions >= a.max_expansions || nspill + 32 * NPL > a.spill_cap) {
+                fail = true;
+                break;
+            }
+            const uint32_t c = Ti[cursor];
+            const float dc = Tk[cursor];
+            __syncwarp();
+            if (lane == 0) Ti[cursor] = c | EXP;
+            expansions++;
+            const bool use_est = EST && expansions > a.warmup;
+
+            uint32_t nb[NPL];
+#pragma unroll
+            for (int s = 0; s < NPL; ++s) {
+                const int j = s * 32 + lane;
+                nb[s] = j < ix.deg0 ? __ldg(ix.adj0 + (size_t)c * ix.deg0 + j) : PAD;
+            }
+            float cc = 0.f, pc0 = 0.f, pc1 = 0.f;
+            if (use_est) {
+                cc = __ldg(ix.xnorm2 + c);
+                const float* pcr = reinterpret_cast<const float*>(ix.Pc) + (size_t)c * r_pad;
+                if (lane < r_pad) pc0 = __ldg(pcr + lane);
+                if (lane + 32 < r_pad) pc1 = __ldg(pcr + lane + 32);
+            }
+            bool isnew[NPL];
+#pragma unroll
+            for (int s = 0; s < NPL; ++s) {
+                int res = V_SEEN;
+                if (nb[s] != PAD) res = visit(hash, a.H, logH, nb[s], spill_mode, bitmap);
+                isnew[s] = res != V_SEEN;
+                const unsigned sb = __ballot_sync(FULLMASK, res == V_NEW_SPILL);
+                if (res == V_NEW_SPILL) spl[nspill + __popc(sb & ltmask)] = nb[s];
+                nspill += __popc(sb);
+                hcount += __popc(__ballot_sync(FULLMASK, res == V_NEW));
+                nbs[s * 32 + lane] = nb[s];
+            }
+            if (hcount > (a.H >> 1)) spill_mode = true;
+
+            // a4: per-centre prep (Sec. 3.2 identity for q^T c, Supplementary G)
+            float ac = 0.f, qres2 = 0.f, qres_n = 0.f;
+            if (use_est) {
+                const float qc = 0.5f * (qn2 + cc - dc);
+                ac = cc > 0.f ? qc / cc : 0.f;
+                qres2 = fmaxf(qn2 - ac * qc, 0.f);
+                qres_n = sqrtf(qres2);
+                const float u0 = lane < r_pad ? pq[lane] - ac * pc0 : 0.f;
+                const float u1 = lane + 32 < r_pad ? pq[lane + 32] - ac * pc1 : 0.f;
+                const float nrm = warp_sum(u0 * u0 + u1 * u1);
+                const float inv = nrm > 0.f ? rsqrtf(nrm) : 0.f;
+                if (lane < r_pad) uq[lane] = u0 * inv;
+                if (lane + 32 < r_pad) uq[lane + 32] = u1 * inv;
+                __syncwarp();
+            }
+
+            // a5: estimates of the new neighbours against ub at expansion start
+            const bool full0 = sz == ef;
+            const float ub0 = full0 ? Tk[ef - 1] : INFINITY;
+            int nl = 0;
+#pragma unroll
+            for (int s = 0; s < NPL; ++s) {
+                float est = -INFINITY;
+                if (use_est && isnew[s]) {
+                    const size_t e = (size_t)c * ix.deg0 + s * 32 + lane;
+                    const float2 sc = __ldg(ix.edge_s + e);
+                    const float th = edge_cos<LP>(ix, e, uq);
+                    float t;
+                    if constexpr (MLP) {
+                        // learned predictor in place of distribution matching
+                        float f[MAX_R + 8];
+                        const float4* ud = ix.edge_u + e * ix.r4;
+                        for (int k = 0; k < ix.r4; ++k) {
+                            const float4 x = __ldg(ud + k);
+                            f[4 * k + 0] = x.x * uq[4 * k + 0];
+                            f[4 * k + 1] = x.y * uq[4 * k + 1];
+                            f[4 * k + 2] = x.z * uq[4 * k + 2];
+                            f[4 * k + 3] = x.w * uq[4 * k + 3];
+                        }
+                        const float dnorm = sqrtf(sc.y * sc.y * cc + sc.x * sc.x);
+                        f[ix.r] = th;
+                        f[ix.r + 1] = qn2 > 0.f ? qres_n * rsqrtf(qn2) : 0.f;
+                        f[ix.r + 2] = dnorm > 0.f ? sc.x / dnorm : 0.f;
+                        f[ix.r + 3] = ac / (fabsf(ac) + fabsf(sc.y) + 1e-6f);
+                        const float pred = mlp_predict(ix, f, ix.r + 4);
+                        t = isfinite(pred) ? pred + ix.mlp_eps : fmaf(th, ix.alpha, ix.beta);
+                    } else {
+                        t = fmaf(th, ix.alpha, ix.beta);
+                    }
+                    const float dd = ac - sc.y;
+                    est = dd * dd * cc + qres2 + sc.x * sc.x - 2.f * qres_n * sc.x * t;
+                }
+                const bool need = isnew[s] && (!use_est || !full0 || !(est > ub0));
+                es[s * 32 + lane] = est;
+                const unsigned bm = __ballot_sync(FULLMASK, need);
+                if (need) lst[nl + __popc(bm & ltmask)] = s * 32 + lane;
+                nl += __popc(bm);
+            }
+            __syncwarp();
+            // a6: exact distances of the survivors
+            exact_list<LP, G, VPL>(q, ix, nbs, lst, nl, xb, lane);
+            c_gath += nl;
+
+            // sequential gate and admission in adjacency order
+#pragma unroll
+            for (int s = 0; s < NPL; ++s) {
+                unsigned bits = __ballot_sync(FULLMASK, isnew[s]);
+                c_exa += __popc(bits);
+                while (bits) {
+                    const int j = __ffs(bits) - 1;
+                    bits &= bits - 1;
+                    const int o = s * 32 + j;
+                    const bool full = sz == ef;
+                    if (use_est && full) {
+                        c_est++;
+                        if (es[o] > Tk[ef - 1]) {
+                            c_skip++;
+                            continue;
+                        }
+                    }
+                    const float d = xb[o];
+                    const uint32_t id = nbs[o];
+                    c_exact++;
+                    if (!full || key_lt(d, id, Tk[sz - 1], Ti[sz - 1] & ~EXP)) {
+                        t_insert(Tk, Ti, sz, ef, d, id, cursor, lane);
+                        c_adm++;
+                    }
+                }
+            }
+            __syncwarp();
+        }
+        c_exp = expansions;
+
+        // ---- LP: re-rank the head of T with FP32 rows
+        if constexpr (LP) {
+            const int R = min(sz, max(K, a.rerank));
+            float* rk = reinterpret_cast<float*>(hash);
+            uint32_t* ri = hash + a.ef_cap;   // the plan keeps H >= 2 ef_cap
+            for (int i = 0; i < R; ++i) {
+                const float d = exact_f32_row(qs, ix, Ti[i] & ~EXP, lane);
+                if (lane == 0) Tk[i] = d;
+            }
+            __syncwarp();
+            for (int i = lane; i < R; i += 32) {
+                const float d = Tk[i];
+                const uint32_t id = Ti[i] & ~EXP;
+                int rank = 0;
+                for (int j = 0; j < R; ++j) rank += key_lt(Tk[j], Ti[j] & ~EXP, d, id);
+                rk[rank] = d;
+                ri[rank] = id;
+            }
+            __syncwarp();
+            for (int i = lane; i < R; i += 32) {
+                Tk[i] = rk[i];
+                Ti[i] = ri[i];
+            }
+            __syncwarp();
+        }
+
+        // ---- a7: output
+        for (int k = lane; k < K; k += 32) {
+            a.out_ids[ooff + k] = k < sz ? (int64_t)(Ti[k] & ~EXP) : (int64_t)-1;
+            a.out_d[ooff + k] = k < sz ? Tk[k] : INFINITY;
+        }
+        for (int i = lane; i < nspill; i += 32) bitmap[spl[i] >> 5] = 0u;
+        if (lane == 0) {
+            if (fail) atomicOr(a.err, (int)FINGER_ERR_LIMIT);
+            unsigned long long* g = a.cnt;
+            atomicAdd(g + 0, (unsigned long long)c_exp);
+            atomicAdd(g + 1, (unsigned long long)c_exa);
+            atomicAdd(g + 2, (unsigned long long)c_est);
+            atomicAdd(g + 3, (unsigned long long)c_skip);
+            atomicAdd(g + 4, (unsigned long long)c_exact);
+            atomicAdd(g + 5, (unsigned long long)c_adm);
+            atomicAdd(g + 6, (unsigned long long)c_up);
+            atomicAdd(g + 7, (unsigned long long)c_gath);
+            if (a.cnt_q) {
+                int32_t* cq = a.cnt_q + (size_t)qi * 8;
+                cq[0] = c_exp;
+                cq[1] = c_exa;
+                cq[2] = c_est;
+                cq[3] = c_skip;
+                cq[4] = c_exact;
+                cq[5] = c_adm;
+                cq[6] = c_up;
+                cq[7] = c_gath;
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// instantiate and dispatch one mode over the (G, VPL, NPL) variants
+template <int MODE>
+cudaError_t launch_mode(const DevIndex& ix, const SearchArgs& a, const SearchPlan& p,
+                        cudaStream_t s) {
+    const int smem = p.smem_per_warp * p.wpb;
+    const dim3 grid(p.blocks), block(p.wpb * 32);
+#define FG_CASE(G_, V_, N_)                                                                    \
+    if (p.G == G_ && p.VPL == V_ && p.NPL == N_) {                                           \
+        auto k = k_search<MODE, G_, V_, N_>;                                                   \
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem); \
+        if (e != cudaSuccess) return e;                                                       \
+        k<<<grid, block, smem, s>>>(ix, a);                                                   \
+        return cudaGetLastError();                                                            \
+    }
+#define FG_NPL(N_)                                                                             \
+    FG_CASE(8, 1, N_) FG_CASE(16, 1, N_) FG_CASE(32, 1, N_) FG_CASE(32, 2, N_)               \
+    FG_CASE(32, 4, N_) FG_CASE(32, 8, N_)
+    FG_NPL(1)
+    FG_NPL(2)
+#undef FG_NPL
+#undef FG_CASE
+    return cudaErrorInvalidValue;
+}
+
+template <int MODE>
+cudaError_t occupancy_mode(const SearchPlan& p, int* blocks) {
+    const int smem = p.smem_per_warp * p.wpb;
+#define FG_CASE(G_, V_, N_)                                                                    \
+    if (p.G == G_ && p.VPL == V_ && p.NPL == N_) {                                           \
+        auto k = k_search<MODE, G_, V_, N_>;                                                   \
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem); \
+        if (e != cudaSuccess) return e;                                                       \
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k, p.wpb * 32, smem);     \
+    }
+#define FG_NPL(N_)                                                                             \
+    FG_CASE(8, 1, N_) FG_CASE(16, 1, N_) FG_CASE(32, 1, N_) FG_CASE(32, 2, N_)               \
+    FG_CASE(32, 4, N_) FG_CASE(32, 8, N_)
+    FG_NPL(1)
+    FG_NPL(2)
+#undef FG_NPL
+#undef FG_CASE
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace fg

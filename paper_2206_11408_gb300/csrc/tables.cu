@@ -1,0 +1,747 @@
+// FINGER construction on the device: Algorithm 2 and the precomputed tables of
+// Supplementary G (arXiv 2206.11408).
+//
+//   k_sample      neighbour-pair draw per node (counter-based, see finger.h)
+//   k_pair_b      b = c^T d / c^T c for the D_res member of every pair
+//   k_gram        G = sum d_res d_res^T (m x m): 64 x 64 output tiles, FP32 per
+//                 chunk of pairs, FP64 across chunks
+//   k_jacobi      cyclic parallel-order Jacobi on G in FP64 (cooperative grid);
+//                 the eigenvectors of the r largest eigenvalues are the left
+//                 singular vectors U_{1:r} of D_res (Proposition 1)
+//   k_node_proj   P c for every node (tiled FFMA)
+//   k_edge        per layer-0 edge (c, d): b, ||d_res|| = ||d - b c|| (explicit),
+//                 u = (P d - b P c) / ||P d - b P c|| (= P d_res normalised)
+//   k_pair_cos    X = cos(d_res, d'_res) (explicit residuals), Y = u_d . u_d'
+//   k_sum*        deterministic block reductions for mu, sigma, mu_hat,
+//                 sigma_hat (standard deviations, 1/N) and eps
+//   k_lp_codes    FP8-e4m3 codes of u * code_scale (reduced-precision tables)
+#include <cooperative_groups.h>
+#include <math.h>
+
+#include <algorithm>
+#include <chrono>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace fg {
+
+namespace {
+
+__device__ __forceinline__ float wsum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ uint64_t smix(uint64_t x) {
+    uint64_t z = x + 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+__global__ void k_xnorm2(const float4* X, int64_t n, int m4, float* out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (w >= n) return;
+    float acc = 0.f;
+    for (int k = lane; k < m4; k += 32) {
+        const float4 x = X[w * m4 + k];
+        acc = fmaf(x.x, x.x, acc);
+        acc = fmaf(x.y, x.y, acc);
+        acc = fmaf(x.z, x.z, acc);
+        acc = fmaf(x.w, x.w, acc);
+    }
+    acc = wsum(acc);
+    if (lane == 0) out[w] = acc;
+}
+
+__global__ void k_to_bf16(const float* X, int64_t n, int m_pad, int m8, __nv_bfloat16* out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int w = m8 * 8;
+    if (i >= n * w) return;
+    const int64_t r = i / w;
+    const int k = (int)(i % w);
+    out[i] = __float2bfloat16_rn(k < m_pad ? X[r * m_pad + k] : 0.f);
+}
+
+// pair rows (c, slot_i, slot_j); c = -1 when the node has < 2 neighbours
+__global__ void k_sample(const uint32_t* adj0, int64_t n, int deg0, uint64_t seed, int spn,
+                         int3* out) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n * spn) return;
+    const int64_t c = t / spn;
+    const uint32_t* row = adj0 + c * deg0;
+    int deg = 0;
+    for (int j = 0; j < deg0; ++j) deg += row[j] != PAD;
+    if (deg < 2) {
+        out[t] = make_int3(-1, -1, -1);
+        return;
+    }
+    const uint64_t h1 = smix(seed ^ (uint64_t)t);
+    const uint64_t h2 = smix(h1);
+    const int i = (int)(h1 % (uint64_t)deg);
+    int j = (int)(h2 % (uint64_t)(deg - 1));
+    j += j >= i;
+    // slots of the i-th and j-th valid entries in row order
+    int si = -1, sj = -1, v = 0;
+    for (int s = 0; s < deg0; ++s) {
+        if (row[s] == PAD) continue;
+        if (v == i) si = s;
+        if (v == j) sj = s;
+        v++;
+    }
+    out[t] = make_int3((int)c, si, sj);
+}
+
+// b of the pair's first member (warp per pair)
+__global__ void k_pair_b(const float4* X, int m4, const float* xn2, const uint32_t* adj0, int deg0,
+                         const int3* pairs, int64_t np, float* b_out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (w >= np) return;
+    const int3 p = pairs[w];
+    if (p.x < 0) {
+        if (lane == 0) b_out[w] = 0.f;
+        return;
+    }
+    const uint32_t d = adj0[(int64_t)p.x * deg0 + p.y];
+    float acc = 0.f;
+    for (int k = lane; k < m4; k += 32) {
+        const float4 a = X[(int64_t)p.x * m4 + k], b = X[(int64_t)d * m4 + k];
+        acc = fmaf(a.x, b.x, acc);
+        acc = fmaf(a.y, b.y, acc);
+        acc = fmaf(a.z, b.z, acc);
+        acc = fmaf(a.w, b.w, acc);
+    }
+    acc = wsum(acc);
+    const float cc = xn2[p.x];
+    if (lane == 0) b_out[w] = cc > 0.f ? acc / cc : 0.f;
+}
+
+constexpr int GT = 64;      // Gram output tile
+constexpr int GKP = 32;     // pairs per stage
+constexpr int GCHUNK = 4096;
+
+// G[I, J] += sum over a chunk of pairs of R[p, I] R[p, J], R = d - b c
+__global__ void __launch_bounds__(256) k_gram(const float* X, int m_pad, int m, const uint32_t* adj0,
+                                              int deg0, const int3* pairs, const float* bq,
+                                              int64_t np, double* G) {
+    __shared__ float Ri[GKP][GT + 1];
+    __shared__ float Rj[GKP][GT + 1];
+    const int ti = blockIdx.x * GT, tj = blockIdx.y * GT;
+    const int64_t p0 = (int64_t)blockIdx.z * GCHUNK;
+    const int64_t p1 = np < p0 + GCHUNK ? np : p0 + GCHUNK;
+    const int t = threadIdx.x;
+    const int oi = (t >> 4) * 4, oj = (t & 15) * 4;
+    float acc[4][4] = {};
+    for (int64_t pb = p0; pb < p1; pb += GKP) {
+        __syncthreads();
+        for (int e = t; e < GKP * GT; e += 256) {
+            const int pp = e / GT, k = e % GT;
+            const int64_t pi = pb + pp;
+            float ri = 0.f, rj = 0.f;
+            if (pi < p1) {
+                const int3 p = pairs[pi];
+                if (p.x >= 0) {
+                    const uint32_t d = adj0[(int64_t)p.x * deg0 + p.y];
+                    const float b = bq[pi];
+                    const int ki = ti + k, kj = tj + k;
+                    if (ki < m) ri = X[(int64_t)d * m_pad + ki] - b * X[(int64_t)p.x * m_pad + ki];
+                    if (kj < m) rj = X[(int64_t)d * m_pad + kj] - b * X[(int64_t)p.x * m_pad + kj];
+                }
+            }
+            Ri[pp][k] = ri;
+            Rj[pp][k] = rj;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int pp = 0; pp < GKP; ++pp) {
+            float a[4], b[4];
+#pragma unroll
+            for (int x = 0; x < 4; ++x) {
+                a[x] = Ri[pp][oi + x];
+                b[x] = Rj[pp][oj + x];
+            }
+#pragma unroll
+            for (int x = 0; x < 4; ++x)
+#pragma unroll
+                for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(a[x], b[y], acc[x][y]);
+        }
+    }
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) {
+            const int gi = ti + oi + x, gj = tj + oj + y;
+            if (gi < m && gj < m) atomicAdd(&G[(int64_t)gi * m + gj], (double)acc[x][y]);
+        }
+}
+
+// Parallel-order cyclic Jacobi on the symmetric m x m matrix A (row-major FP64),
+// accumulating V (initialised to I).  Round r of a sweep rotates the m/2
+// disjoint pairs of the round-robin schedule; each rotation zeroes A[p][q]:
+//   tau = (A_qq - A_pp) / (2 A_pq), t = sign(tau) / (|tau| + sqrt(1 + tau^2)),
+//   c = 1 / sqrt(1 + t^2), s = t c,  A <- J^T A J,  V <- V J,
+// with J = I except J_pp = J_qq = c, J_pq = s, J_qp = -s.
+__global__ void k_jacobi(double* A, double* V, int m, double2* rot, int2* pr, double* red,
+                         int max_sweeps, double tol, int* sweeps_out) {
+    cg::grid_group grid = cg::this_grid();
+    const int mm = (m + 1) & ~1;   // even number of slots; slot m (if m odd) is a dummy
+    const int half = mm / 2;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+    __shared__ double sred[32];
+    int sweep = 0;
+    for (; sweep < max_sweeps; ++sweep) {
+        // off-diagonal and total Frobenius mass
+        double off = 0.0, tot = 0.0;
+        for (int64_t i = tid; i < (int64_t)m * m; i += nth) {
+            const double v = A[i] * A[i];
+            tot += v;
+            if (i / m != i % m) off += v;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            off += __shfl_xor_sync(0xffffffffu, off, o);
+            tot += __shfl_xor_sync(0xffffffffu, tot, o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            sred[threadIdx.x >> 5] = off;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double s = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sred[w];
+            red[2 * blockIdx.x] = s;
+        }
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) sred[threadIdx.x >> 5] = tot;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double s = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sred[w];
+            red[2 * blockIdx.x + 1] = s;
+        }
+        grid.sync();
+        double OFF = 0, TOT = 0;
+        for (int b = 0; b < (int)gridDim.x; ++b) {
+            OFF += red[2 * b];
+            TOT += red[2 * b + 1];
+        }
+        grid.sync();
+        if (OFF <= tol * tol * TOT || OFF == 0.0) break;
+        for (int r = 0; r < mm - 1; ++r) {
+            // pairs and rotations of this round
+            for (int64_t k = tid; k < half; k += nth) {
+                int a, b;
+                if (k == 0) a = 0;
+                else a = (int)((k + r - 1) % (mm - 1)) + 1;
+                b = (int)((mm - 1 - k + r - 1) % (mm - 1)) + 1;
+                if (k == 0) b = (int)((mm - 1 + r - 1) % (mm - 1)) + 1;
+                int p = min(a, b), q = max(a, b);
+                double c = 1.0, s = 0.0;
+                if (q < m) {
+                    const double apq = A[(int64_t)p * m + q];
+                    if (apq != 0.0) {
+                        const double app = A[(int64_t)p * m + p], aqq = A[(int64_t)q * m + q];
+                        const double tau = (aqq - app) / (2.0 * apq);
+                        const double t = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+                        c = 1.0 / sqrt(1.0 + t * t);
+                        s = t * c;
+                    }
+                }
+                pr[k] = make_int2(p, q);
+                rot[k] = make_double2(c, s);
+            }
+            grid.sync();
+            // rows: A <- J^T A
+            for (int64_t e = tid; e < (int64_t)half * m; e += nth) {
+                const int k = (int)(e / m), j = (int)(e % m);
+                const int2 pq = pr[k];
+                if (pq.y >= m) continue;
+                const double2 cs = rot[k];
+                const double ap = A[(int64_t)pq.x * m + j], aq = A[(int64_t)pq.y * m + j];
+                A[(int64_t)pq.x * m + j] = cs.x * ap - cs.y * aq;
+                A[(int64_t)pq.y * m + j] = cs.y * ap + cs.x * aq;
+            }
+            grid.sync();
+            // columns: A <- A J, V <- V J
+            for (int64_t e = tid; e < (int64_t)half * m; e += nth) {
+                const int k = (int)(e / m), i = (int)(e % m);
+                const int2 pq = pr[k];
+                if (pq.y >= m) continue;
+                const double2 cs = rot[k];
+                const double ap = A[(int64_t)i * m + pq.x], aq = A[(int64_t)i * m + pq.y];
+                A[(int64_t)i * m + pq.x] = cs.x * ap - cs.y * aq;
+                A[(int64_t)i * m + pq.y] = cs.y * ap + cs.x * aq;
+                const double vp = V[(int64_t)i * m + pq.x], vq = V[(int64_t)i * m + pq.y];
+                V[(int64_t)i * m + pq.x] = cs.x * vp - cs.y * vq;
+                V[(int64_t)i * m + pq.y] = cs.y * vp + cs.x * vq;
+            }
+            grid.sync();
+        }
+    }
+    if (tid == 0) *sweeps_out = sweep;
+}
+
+// P rows = eigenvectors of the r largest eigenvalues (ties by index), FP32,
+// padded to r_pad x m_pad with zeros.  Single block.
+__global__ void k_pick_basis(const double* A, const double* V, int m, int r, int r_pad, int m_pad,
+                             float* P, double* evals) {
+    extern __shared__ int order[];
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        const double di = A[(int64_t)i * m + i];
+        int rank = 0;
+        for (int j = 0; j < m; ++j) {
+            const double dj = A[(int64_t)j * m + j];
+            rank += (dj > di) || (dj == di && j < i);
+        }
+        order[rank] = i;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < r_pad * m_pad; e += blockDim.x) {
+        const int k = e / m_pad, j = e % m_pad;
+        float v = 0.f;
+        if (k < r && j < m) v = (float)V[(int64_t)j * m + order[k]];
+        P[e] = v;
+    }
+    for (int i = threadIdx.x; i < m; i += blockDim.x) evals[i] = A[(int64_t)order[i] * m + order[i]];
+}
+
+// Pc[n][r_pad] = X P^T: CTA of 64 nodes x 64 outputs, k-chunks of 32
+__global__ void __launch_bounds__(256) k_node_proj(const float* X, int64_t n, int m_pad,
+                                                   const float* P, int r_pad, float* Pc) {
+    __shared__ float Xs[32][65];
+    __shared__ float Ps[32][65];
+    const int64_t n0 = (int64_t)blockIdx.x * 64;
+    const int r0 = blockIdx.y * 64;
+    const int t = threadIdx.x;
+    const int on = (t >> 4) * 4, orr = (t & 15) * 4;
+    float acc[4][4] = {};
+    for (int k0 = 0; k0 < m_pad; k0 += 32) {
+        __syncthreads();
+        for (int e = t; e < 64 * 32; e += 256) {
+            const int i = e / 32, k = e % 32;
+            const int64_t gn = n0 + i;
+            const int gk = k0 + k;
+            Xs[k][i] = (gn < n && gk < m_pad) ? X[gn * m_pad + gk] : 0.f;
+            const int gr = r0 + i;
+            Ps[k][i] = (gr < r_pad && gk < m_pad) ? P[(int64_t)gr * m_pad + gk] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int k = 0; k < 32; ++k) {
+            float a[4], b[4];
+#pragma unroll
+            for (int x = 0; x < 4; ++x) {
+                a[x] = Xs[k][on + x];
+                b[x] = Ps[k][orr + x];
+            }
+#pragma unroll
+            for (int x = 0; x < 4; ++x)
+#pragma unroll
+                for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(a[x], b[y], acc[x][y]);
+        }
+    }
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) {
+            const int64_t gn = n0 + on + x;
+            const int gr = r0 + orr + y;
+            if (gn < n && gr < r_pad) Pc[gn * r_pad + gr] = acc[x][y];
+        }
+}
+
+// per layer-0 edge (c, d): warp per node c
+__global__ void k_edge(const float4* X, int m4, const float* xn2, const uint32_t* adj0,
+                       int64_t n, int deg0, const float* Pc, int r_pad, float* edge_u,
+                       float2* edge_s) {
+    const int lane = threadIdx.x & 31;
+    const int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (c >= n) return;
+    float4 xc[8];
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+        const int k = lane + 32 * v;
+        xc[v] = k < m4 ? X[c * m4 + k] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    const float cc = xn2[c];
+    const float pc0 = lane < r_pad ? Pc[c * r_pad + lane] : 0.f;
+    const float pc1 = lane + 32 < r_pad ? Pc[c * r_pad + lane + 32] : 0.f;
+    for (int j = 0; j < deg0; ++j) {
+        const int64_t e = c * deg0 + j;
+        const uint32_t d = adj0[e];
+        if (d == PAD) {
+            if (lane < r_pad) edge_u[e * r_pad + lane] = 0.f;
+            if (lane + 32 < r_pad) edge_u[e * r_pad + lane + 32] = 0.f;
+            if (lane == 0) edge_s[e] = make_float2(0.f, 0.f);
+            continue;
+        }
+        float4 xd[8];
+        float dot = 0.f;
+#pragma unroll
+        for (int v = 0; v < 8; ++v) {
+            const int k = lane + 32 * v;
+            xd[v] = k < m4 ? X[(int64_t)d * m4 + k] : make_float4(0.f, 0.f, 0.f, 0.f);
+            dot = fmaf(xc[v].x, xd[v].x, dot);
+            dot = fmaf(xc[v].y, xd[v].y, dot);
+            dot = fmaf(xc[v].z, xd[v].z, dot);
+            dot = fmaf(xc[v].w, xd[v].w, dot);
+        }
+        dot = wsum(dot);
+        const float b = cc > 0.f ? dot / cc : 0.f;
+        float rn = 0.f;
+#pragma unroll
+        for (int v = 0; v < 8; ++v) {
+            float t;
+            t = xd[v].x - b * xc[v].x; rn = fmaf(t, t, rn);
+            t = xd[v].y - b * xc[v].y; rn = fmaf(t, t, rn);
+            t = xd[v].z - b * xc[v].z; rn = fmaf(t, t, rn);
+            t = xd[v].w - b * xc[v].w; rn = fmaf(t, t, rn);
+        }
+        rn = wsum(rn);
+        const float u0 = lane < r_pad ? Pc[(int64_t)d * r_pad + lane] - b * pc0 : 0.f;
+        const float u1 = lane + 32 < r_pad ? Pc[(int64_t)d * r_pad + lane + 32] - b * pc1 : 0.f;
+        const float nu = wsum(u0 * u0 + u1 * u1);
+        const float inv = nu > 0.f ? rsqrtf(nu) : 0.f;
+        if (lane < r_pad) edge_u[e * r_pad + lane] = u0 * inv;
+        if (lane + 32 < r_pad) edge_u[e * r_pad + lane + 32] = u1 * inv;
+        if (lane == 0) edge_s[e] = make_float2(sqrtf(rn), b);
+    }
+}
+
+// X_i, Y_i for every drawn pair (warp per pair); invalid pairs get NaN
+__global__ void k_pair_cos(const float4* X, int m4, const uint32_t* adj0, int deg0,
+                           const int3* pairs, int64_t np, const float* edge_u, const float2* edge_s,
+                           int r_pad, double* Xc, double* Yc) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (w >= np) return;
+    const int3 p = pairs[w];
+    if (p.x < 0) {
+        if (lane == 0) {
+            Xc[w] = NAN;
+            Yc[w] = NAN;
+        }
+        return;
+    }
+    const int64_t e1 = (int64_t)p.x * deg0 + p.y, e2 = (int64_t)p.x * deg0 + p.z;
+    const uint32_t d1 = adj0[e1], d2 = adj0[e2];
+    const float b1 = edge_s[e1].y, b2 = edge_s[e2].y;
+    float s12 = 0.f, s11 = 0.f, s22 = 0.f;
+    for (int k = lane; k < m4; k += 32) {
+        const float4 c = X[(int64_t)p.x * m4 + k];
+        const float4 x = X[(int64_t)d1 * m4 + k];
+        const float4 y = X[(int64_t)d2 * m4 + k];
+        const float r1[4] = {x.x - b1 * c.x, x.y - b1 * c.y, x.z - b1 * c.z, x.w - b1 * c.w};
+        const float r2[4] = {y.x - b2 * c.x, y.y - b2 * c.y, y.z - b2 * c.z, y.w - b2 * c.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            s12 = fmaf(r1[i], r2[i], s12);
+            s11 = fmaf(r1[i], r1[i], s11);
+            s22 = fmaf(r2[i], r2[i], s22);
+        }
+    }
+    s12 = wsum(s12);
+    s11 = wsum(s11);
+    s22 = wsum(s22);
+    float uu = 0.f;
+    for (int k = lane; k < r_pad; k += 32) uu = fmaf(edge_u[e1 * r_pad + k], edge_u[e2 * r_pad + k], uu);
+    uu = wsum(uu);
+    if (lane == 0) {
+        const double den = sqrt((double)s11) * sqrt((double)s22);
+        Xc[w] = den > 0 ? (double)s12 / den : 0.0;
+        Yc[w] = (double)uu;
+    }
+}
+
+// deterministic reductions: per-block partial sums, then one block sums them
+// mode 0: sum X, sum Y, count;  mode 1: sum (X-mu)^2, sum (Y-muh)^2;
+// mode 2: sum |(Y - muh) ratio + mu - X|
+__global__ void k_sum_part(const double* Xc, const double* Yc, int64_t np, int mode, double mu,
+                           double muh, double ratio, double* part) {
+    __shared__ double s[3][256];
+    double a = 0, b = 0, c = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < np;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double x = Xc[i], y = Yc[i];
+        if (x != x) continue;
+        if (mode == 0) {
+            a += x;
+            b += y;
+            c += 1.0;
+        } else if (mode == 1) {
+            a += (x - mu) * (x - mu);
+            b += (y - muh) * (y - muh);
+        } else {
+            a += fabs((y - muh) * ratio + mu - x);
+        }
+    }
+    s[0][threadIdx.x] = a;
+    s[1][threadIdx.x] = b;
+    s[2][threadIdx.x] = c;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o)
+            for (int k = 0; k < 3; ++k) s[k][threadIdx.x] += s[k][threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 3; ++k) part[blockIdx.x * 3 + k] = s[k][0];
+}
+
+__global__ void k_sum_final(const double* part, int nb, double* out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double a = 0, b = 0, c = 0;
+    for (int i = 0; i < nb; ++i) {
+        a += part[3 * i];
+        b += part[3 * i + 1];
+        c += part[3 * i + 2];
+    }
+    out[0] = a;
+    out[1] = b;
+    out[2] = c;
+}
+
+__global__ void k_lp_codes(const float* edge_u, int64_t ne, int r_pad, int r16b, float scale,
+                           uint8_t* out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ne * r16b) return;
+    const int64_t e = i / r16b;
+    const int k = (int)(i % r16b);
+    const float v = k < r_pad ? edge_u[e * r_pad + k] * scale : 0.f;
+    out[i] = (uint8_t)__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
+}
+
+template <class T>
+T* dalloc(size_t count) {
+    void* p = nullptr;
+    if (cudaMalloc(&p, count * sizeof(T) + 16) != cudaSuccess) return nullptr;
+    return static_cast<T*>(p);
+}
+
+}  // namespace
+
+cudaError_t launch_xnorm2(const float4* X, int64_t n, int m4, float* out, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    k_xnorm2<<<(unsigned)((n * 32 + 255) / 256), 256, 0, s>>>(X, n, m4, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_to_bf16(const float* X, int64_t n, int m_pad, int m8, __nv_bfloat16* out,
+                           cudaStream_t s) {
+    const int64_t tot = n * m8 * 8;
+    if (tot == 0) return cudaSuccess;
+    k_to_bf16<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(X, n, m_pad, m8, out);
+    return cudaGetLastError();
+}
+
+}  // namespace fg
+
+// BF16 rows and FP8-e4m3 residual codes from the FP32 tables (mode LP)
+cudaError_t lp_rebuild(finger_index* ix) {
+    using namespace fg;
+    cudaFree(ix->Xh);
+    cudaFree(ix->edge_q);
+    ix->Xh = nullptr;
+    ix->edge_q = nullptr;
+    const int64_t n = ix->n, ne = n * ix->deg0;
+    const int r16b = ((ix->r_pad + 15) / 16) * 16;
+    cudaError_t e = cudaMalloc(&ix->Xh, sizeof(__nv_bfloat16) * (size_t)n * ix->m8 * 8 + 16);
+    if (e != cudaSuccess) return e;
+    e = cudaMalloc(&ix->edge_q, (size_t)ne * r16b + 16);
+    if (e != cudaSuccess) return e;
+    e = launch_to_bf16(ix->X, n, ix->m_pad, ix->m8, ix->Xh, 0);
+    if (e != cudaSuccess) return e;
+    k_lp_codes<<<(unsigned)((ne * r16b + 255) / 256), 256>>>(ix->edge_u, ne, ix->r_pad, r16b,
+                                                             ix->code_scale, ix->edge_q);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    ix->r16 = r16b / 16;
+    return cudaDeviceSynchronize();
+}
+
+namespace fg {
+
+#define CKT(x)                        \
+    do {                              \
+        if ((x) != cudaSuccess) {     \
+            status = FINGER_ERR_CUDA; \
+            goto done;                \
+        }                             \
+    } while (0)
+
+finger_status build_tables(finger_index* ix, const finger_build_params* p, cudaStream_t s) {
+    const auto t0 = std::chrono::steady_clock::now();
+    if (!ix->adj0) return FINGER_ERR_NOT_BUILT;
+    const int r = p->r;
+    if (r < 1 || r > MAX_R || r > ix->m) return FINGER_ERR_INVALID_ARG;
+    const int spn = p->samples_per_node > 0 ? p->samples_per_node : 1;
+    const int64_t n = ix->n;
+    const int m = ix->m, m_pad = ix->m_pad, m4 = ix->m4, deg0 = ix->deg0;
+    const int r_pad = (r + 3) & ~3;
+    const int64_t np = n * spn;
+    const int64_t ne = n * deg0;
+    finger_status status = FINGER_OK;
+    int3* pairs = nullptr;
+    float* bq = nullptr;
+    double *G = nullptr, *V = nullptr, *red = nullptr, *evals = nullptr;
+    double2* rot = nullptr;
+    int2* pr = nullptr;
+    int* sweeps = nullptr;
+    double *Xc = nullptr, *Yc = nullptr, *part = nullptr, *sums = nullptr;
+    float* P = dalloc<float>((size_t)r_pad * m_pad);
+    float* Pc = dalloc<float>((size_t)n * r_pad);
+    float* edge_u = dalloc<float>((size_t)ne * r_pad);
+    float2* edge_s = dalloc<float2>((size_t)ne);
+    double st[5] = {0, 0, 0, 0, 0};
+    double h[3];
+    const int nbp = 512;
+    if (!P || !Pc || !edge_u || !edge_s) {
+        status = FINGER_ERR_OOM;
+        goto done;
+    }
+    pairs = dalloc<int3>((size_t)np);
+    bq = dalloc<float>((size_t)np);
+    Xc = dalloc<double>((size_t)np);
+    Yc = dalloc<double>((size_t)np);
+    part = dalloc<double>(3 * nbp);
+    sums = dalloc<double>(3);
+    if (!pairs || !bq || !Xc || !Yc || !part || !sums) {
+        status = FINGER_ERR_OOM;
+        goto done;
+    }
+    k_sample<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(ix->adj0, n, deg0, p->seed, spn, pairs);
+    CKT(cudaGetLastError());
+    if (p->basis_host) {
+        std::vector<float> hp((size_t)r_pad * m_pad, 0.f);
+        for (int k = 0; k < r; ++k)
+            for (int j = 0; j < m; ++j) hp[(size_t)k * m_pad + j] = p->basis_host[(size_t)k * m + j];
+        CKT(cudaMemcpyAsync(P, hp.data(), sizeof(float) * hp.size(), cudaMemcpyHostToDevice, s));
+        CKT(cudaStreamSynchronize(s));
+    } else {
+        // D_res Gram matrix and its eigenvectors
+        G = dalloc<double>((size_t)m * m);
+        V = dalloc<double>((size_t)m * m);
+        const int jb = std::max(1, std::min(ix->num_sms, (m + 63) / 64 * 4));
+        red = dalloc<double>(2 * (size_t)jb);
+        rot = dalloc<double2>((size_t)m);
+        pr = dalloc<int2>((size_t)m);
+        sweeps = dalloc<int>(1);
+        evals = dalloc<double>((size_t)m);
+        if (!G || !V || !red || !rot || !pr || !sweeps || !evals) {
+            status = FINGER_ERR_OOM;
+            goto done;
+        }
+        k_pair_b<<<(unsigned)((np * 32 + 255) / 256), 256, 0, s>>>(
+            reinterpret_cast<const float4*>(ix->X), m4, ix->xnorm2, ix->adj0, deg0, pairs, np, bq);
+        CKT(cudaGetLastError());
+        CKT(cudaMemsetAsync(G, 0, sizeof(double) * m * m, s));
+        {
+            const dim3 grid((m + GT - 1) / GT, (m + GT - 1) / GT, (unsigned)((np + GCHUNK - 1) / GCHUNK));
+            k_gram<<<grid, 256, 0, s>>>(ix->X, m_pad, m, ix->adj0, deg0, pairs, bq, np, G);
+            CKT(cudaGetLastError());
+        }
+        {
+            std::vector<double> I((size_t)m * m, 0.0);
+            for (int i = 0; i < m; ++i) I[(size_t)i * m + i] = 1.0;
+            CKT(cudaMemcpyAsync(V, I.data(), sizeof(double) * I.size(), cudaMemcpyHostToDevice, s));
+            int max_sweeps = 40;
+            double tol = 1e-15;
+            void* args[] = {&G, &V, (void*)&m, &rot, &pr, &red, &max_sweeps, &tol, &sweeps};
+            CKT(cudaLaunchCooperativeKernel((void*)k_jacobi, dim3(jb), dim3(256), args, 0, s));
+            k_pick_basis<<<1, 256, sizeof(int) * m, s>>>(G, V, m, r, r_pad, m_pad, P, evals);
+            CKT(cudaGetLastError());
+            CKT(cudaStreamSynchronize(s));
+        }
+    }
+    {
+        const dim3 grid((unsigned)((n + 63) / 64), (r_pad + 63) / 64);
+        k_node_proj<<<grid, 256, 0, s>>>(ix->X, n, m_pad, P, r_pad, Pc);
+        CKT(cudaGetLastError());
+    }
+    k_edge<<<(unsigned)((n * 32 + 127) / 128), 128, 0, s>>>(reinterpret_cast<const float4*>(ix->X),
+                                                            m4, ix->xnorm2, ix->adj0, n, deg0, Pc,
+                                                            r_pad, edge_u, edge_s);
+    CKT(cudaGetLastError());
+    if (p->stats_host) {
+        for (int i = 0; i < 5; ++i) st[i] = p->stats_host[i];
+    } else {
+        k_pair_cos<<<(unsigned)((np * 32 + 255) / 256), 256, 0, s>>>(
+            reinterpret_cast<const float4*>(ix->X), m4, ix->adj0, deg0, pairs, np, edge_u, edge_s,
+            r_pad, Xc, Yc);
+        CKT(cudaGetLastError());
+        k_sum_part<<<nbp, 256, 0, s>>>(Xc, Yc, np, 0, 0, 0, 0, part);
+        k_sum_final<<<1, 32, 0, s>>>(part, nbp, sums);
+        CKT(cudaMemcpyAsync(h, sums, sizeof(h), cudaMemcpyDeviceToHost, s));
+        CKT(cudaStreamSynchronize(s));
+        const double N = h[2] > 0 ? h[2] : 1.0;
+        const double mu = h[0] / N, muh = h[1] / N;
+        k_sum_part<<<nbp, 256, 0, s>>>(Xc, Yc, np, 1, mu, muh, 0, part);
+        k_sum_final<<<1, 32, 0, s>>>(part, nbp, sums);
+        CKT(cudaMemcpyAsync(h, sums, sizeof(h), cudaMemcpyDeviceToHost, s));
+        CKT(cudaStreamSynchronize(s));
+        const double sigma = sqrt(h[0] / N), sigmah = sqrt(h[1] / N);
+        const double ratio = sigmah > 0 ? sigma / sigmah : 0.0;
+        k_sum_part<<<nbp, 256, 0, s>>>(Xc, Yc, np, 2, mu, muh, ratio, part);
+        k_sum_final<<<1, 32, 0, s>>>(part, nbp, sums);
+        CKT(cudaMemcpyAsync(h, sums, sizeof(h), cudaMemcpyDeviceToHost, s));
+        CKT(cudaStreamSynchronize(s));
+        st[0] = mu;
+        st[1] = sigma;
+        st[2] = muh;
+        st[3] = sigmah;
+        st[4] = h[0] / N;
+    }
+    CKT(cudaStreamSynchronize(s));
+    // reduced-precision tables
+    cudaFree(ix->Xh);
+    cudaFree(ix->edge_q);
+    ix->Xh = nullptr;
+    ix->edge_q = nullptr;
+done:
+    cudaFree(pairs);
+    cudaFree(bq);
+    cudaFree(G);
+    cudaFree(V);
+    cudaFree(red);
+    cudaFree(rot);
+    cudaFree(pr);
+    cudaFree(sweeps);
+    cudaFree(evals);
+    cudaFree(Xc);
+    cudaFree(Yc);
+    cudaFree(part);
+    cudaFree(sums);
+    if (status != FINGER_OK) {
+        cudaFree(P);
+        cudaFree(Pc);
+        cudaFree(edge_u);
+        cudaFree(edge_s);
+        return status;
+    }
+    cudaFree(ix->P);
+    cudaFree(ix->Pc);
+    cudaFree(ix->edge_u);
+    cudaFree(ix->edge_s);
+    ix->P = P;
+    ix->Pc = Pc;
+    ix->edge_u = edge_u;
+    ix->edge_s = edge_s;
+    ix->r = r;
+    ix->r_pad = r_pad;
+    for (int i = 0; i < 5; ++i) ix->stats[i] = st[i];
+    if (p->build_lp && lp_rebuild(ix) != cudaSuccess) {
+        cudaGetLastError();
+        return FINGER_ERR_CUDA;
+    }
+    ix->build_ms =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return FINGER_OK;
+}
+
+}  // namespace fg

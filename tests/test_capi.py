@@ -1,0 +1,47 @@
+"""Host-side checks of the C ABI: the library loads without a GPU, exports
+every entry point include/finger.h declares, and its pure-host helpers follow
+the paper's memory formula.  No compute call is made here."""
+import ctypes
+import os
+import re
+
+import paper_2206_11408_gb300 as fg
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include",
+                      "finger.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(finger_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("finger_index_load", "finger_build_tables", "finger_search"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol():
+    L = ctypes.CDLL(fg._build.build())
+    missing = [n for n in declared_functions() if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_declared_symbol():
+    assert set(declared_functions()) <= set(fg.SIGNATURES)
+
+
+def test_table_bytes_is_r_plus_2_floats_per_edge():
+    # Supplementary F: (r + 2) * |E| * sizeof(float)
+    assert fg.table_bytes(1_000_000, 32, 64) == 66 * 32_000_000 * 4
+    assert fg.table_bytes(10_000, 32, 16) == 18 * 320_000 * 4
+    # reduced precision: 16-byte aligned FP8 codes + two FP32 scalars
+    assert fg.table_bytes(1_200_000, 48, 32, lp=True) == (32 + 8) * 1_200_000 * 48
+
+
+def test_status_strings():
+    L = fg.lib()
+    for s in range(9):
+        assert L.finger_status_str(s)

@@ -1,0 +1,209 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Workload: the 10,000-point, 64-dimensional 16-cluster Gaussian mixture with
+200 queries, an HNSW graph (M = 16, efConstruction = 100) built by the oracle,
+FINGER rank 16.  Bars: result lists identical to the oracle on >= 99 % of
+queries, per-pair distances within 1e-5 relative of FP64, recall@10 within
+0.002 of the oracle's at the same ef, traversal counters identical on the
+queries whose lists match.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2206_11408_gb300 as fg  # noqa: E402
+
+REL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def cfg1():
+    X = workloads.base_vectors(1)
+    Q = workloads.query_vectors(1)
+    g = oracle.hnsw_build(X, 16, 100, 3001)
+    fp, pairs = oracle.build_tables(X, g, 16, 4001)
+    gt, gd = oracle.bruteforce(X, Q, 10)
+    ix = fg.Index(X)
+    ix.set_graph(g.adj0, g.level, g.up_off, g.up_adj, g.entry, g.maxlevel, g.M)
+    ix.build_tables(16, 4001, basis=fp.P, stats=fp.stats())
+    q = torch.from_numpy(Q).cuda()
+    yield dict(X=X, Q=Q, g=g, fp=fp, pairs=pairs, gt=gt, gd=gd, ix=ix, q=q)
+    ix.close()
+
+
+def _gpu_search(ix, q, K, ef, mode, warmup=5):
+    ix.set_mode(mode, warmup)
+    cnt = torch.zeros((q.shape[0], 8), dtype=torch.int32, device="cuda")
+    ix.set_counters(cnt)
+    ids, d = ix.search(q, K, ef)
+    torch.cuda.synchronize()
+    ix.sync()
+    ix.set_counters(None)
+    return ids.cpu().numpy(), d.cpu().numpy(), cnt.cpu().numpy()
+
+
+def _compare(gi, gd, gc, oi, od, oc, gt, K, what):
+    match = (gi == oi).all(axis=1)
+    assert match.mean() >= 0.99, f"{what}: {match.mean():.4f} of lists identical"
+    ok = oi[match] >= 0
+    rel = np.abs(gd[match][ok] - od[match][ok]) / np.maximum(od[match][ok], 1e-30)
+    assert rel.max() < REL, f"{what}: max rel distance error {rel.max():.2e}"
+    # counters: expansions, examined, estimates, skipped, exact, admitted, upper
+    assert (gc[match][:, :7] == oc[match][:, :7]).all(), f"{what}: counters differ"
+    r_g, r_o = oracle.recall(gi, gt, K), oracle.recall(oi, gt, K)
+    assert abs(r_g - r_o) <= 0.002, f"{what}: recall {r_g} vs oracle {r_o}"
+
+
+def test_bruteforce_knn_matches_oracle(cfg1):
+    ids, d = cfg1["ix"].knn(cfg1["q"], 10)
+    torch.cuda.synchronize()
+    ids, d = ids.cpu().numpy(), d.cpu().numpy()
+    assert (ids == cfg1["gt"]).mean() > 0.999
+    np.testing.assert_allclose(d, cfg1["gd"], rtol=REL)
+
+
+@pytest.mark.parametrize("ef", [10, 20, 50, 100])
+def test_plain_search_parity(cfg1, ef):
+    gi, gd, gc = _gpu_search(cfg1["ix"], cfg1["q"], 10, ef, fg.MODE_PLAIN)
+    oi, od, oc = oracle.search(cfg1["g"], cfg1["X"], cfg1["Q"], 10, ef)
+    _compare(gi, gd, gc, oi, od, oc, cfg1["gt"], 10, f"plain ef={ef}")
+
+
+@pytest.mark.parametrize("ef", [10, 20, 50, 100])
+def test_finger_search_parity(cfg1, ef):
+    gi, gd, gc = _gpu_search(cfg1["ix"], cfg1["q"], 10, ef, fg.MODE_FINGER)
+    oi, od, oc = oracle.search(cfg1["g"], cfg1["X"], cfg1["Q"], 10, ef, cfg1["fp"])
+    _compare(gi, gd, gc, oi, od, oc, cfg1["gt"], 10, f"finger ef={ef}")
+    assert gc[:, 3].sum() > 0          # the gate skipped neighbours
+
+
+def test_finger_without_skipping_equals_plain(cfg1):
+    a = _gpu_search(cfg1["ix"], cfg1["q"], 10, 50, fg.MODE_PLAIN)
+    b = _gpu_search(cfg1["ix"], cfg1["q"], 10, 50, fg.MODE_FINGER, warmup=10 ** 9)
+    assert (a[0] == b[0]).all() and (a[1] == b[1]).all()
+    assert (a[2][:, [0, 1, 4, 5, 6]] == b[2][:, [0, 1, 4, 5, 6]]).all()
+
+
+def test_search_host_equals_device(cfg1):
+    ix = cfg1["ix"]
+    ix.set_mode(fg.MODE_FINGER, 5)
+    ids, d = ix.search(cfg1["q"], 10, 50)
+    hi, hd = ix.search_host(cfg1["Q"], 10, 50)
+    assert (ids.cpu().numpy() == hi).all() and (d.cpu().numpy() == hd).all()
+
+
+def test_edge_tables_match_oracle(cfg1):
+    t = cfg1["ix"].get_tables()
+    X, g, fp = cfg1["X"], cfg1["g"], cfg1["fp"]
+    nodes = np.arange(0, X.shape[0], 7)
+    u, dn, b = oracle.edge_tables(X, g.adj0, fp.P, nodes)
+    np.testing.assert_allclose(t["b"][nodes], b, rtol=1e-5, atol=1e-6)
+    np.testing.assert_allclose(t["dres_norm"][nodes], dn, rtol=1e-4, atol=1e-5)
+    np.testing.assert_allclose(t["edge_u"][nodes], u, atol=2e-5)
+    Pc = X[nodes].astype(np.float64) @ fp.P.T
+    np.testing.assert_allclose(t["node_proj"][nodes], Pc, rtol=1e-5, atol=1e-5)
+
+
+def test_matching_stats_match_oracle(cfg1):
+    """GPU statistics from the oracle's basis vs the oracle's own (FP64)."""
+    X, g, fp = cfg1["X"], cfg1["g"], cfg1["fp"]
+    ix = fg.Index(X)
+    ix.set_graph(g.adj0, g.level, g.up_off, g.up_adj, g.entry, g.maxlevel, g.M)
+    ix.build_tables(16, 4001, basis=fp.P)
+    st = ix.get_tables()["stats"]
+    np.testing.assert_allclose(st, fp.stats(), rtol=1e-5, atol=1e-6)
+    ix.close()
+
+
+def test_device_basis_is_the_svd_basis(cfg1):
+    """P from the device Gram + Jacobi spans the top-r left singular subspace:
+    orthonormal rows, captured energy equal to the sum of the r largest
+    eigenvalues of the oracle's Gram matrix (Proposition 1)."""
+    X, g, fp, pairs = cfg1["X"], cfg1["g"], cfg1["fp"], cfg1["pairs"]
+    ix = fg.Index(X)
+    ix.set_graph(g.adj0, g.level, g.up_off, g.up_adj, g.entry, g.maxlevel, g.M)
+    ix.build_tables(16, 4001)
+    t = ix.get_tables()
+    P = t["P"].astype(np.float64)
+    np.testing.assert_allclose(P @ P.T, np.eye(16), atol=1e-5)
+    G = oracle.gram(X, pairs)
+    w = np.sort(np.linalg.eigvalsh(G))[::-1]
+    energy = np.trace(P @ G @ P.T)
+    assert energy == pytest.approx(w[:16].sum(), rel=1e-5)
+    gap = (w[15] - w[16]) / w[0]
+    if gap > 1e-3:
+        np.testing.assert_allclose(P.T @ P, fp.P.T @ fp.P, atol=1e-3)
+    np.testing.assert_allclose(t["stats"], fp.stats(), rtol=2e-3, atol=1e-4)
+    ix.close()
+
+
+def test_full_rank_finger_equals_plain(cfg1):
+    X, g = cfg1["X"], cfg1["g"]
+    fpf, _ = oracle.build_tables(X, g, 64, 4001)
+    ix = fg.Index(X)
+    ix.set_graph(g.adj0, g.level, g.up_off, g.up_adj, g.entry, g.maxlevel, g.M)
+    ix.build_tables(64, 4001, basis=fpf.P, stats=fpf.stats())
+    a = _gpu_search(ix, cfg1["q"], 10, 50, fg.MODE_PLAIN)
+    b = _gpu_search(ix, cfg1["q"], 10, 50, fg.MODE_FINGER)
+    assert (a[0] == b[0]).all(axis=1).mean() >= 0.99
+    assert b[2][:, 2].sum() > 0
+    ix.close()
+
+
+def test_limits_and_padding(cfg1):
+    ix = cfg1["ix"]
+    with pytest.raises(fg.FingerError):
+        ix.search(cfg1["q"], 10, 5)                     # K > ef
+    ids, d = ix.search(cfg1["q"][:0], 10, 20)           # empty batch
+    assert ids.shape == (0, 10)
+    small = fg.Index(cfg1["X"][:5])
+    adj = np.full((5, 4), -1, np.int32)
+    adj[:, :2] = [[1, 2], [0, 2], [0, 1], [4, -1], [3, -1]]
+    small.set_graph(adj, np.zeros(5, np.int32), np.full(5, -1, np.int64),
+                    np.zeros((0, 2), np.int32), 0, 0, 2)
+    small.set_mode(fg.MODE_PLAIN)
+    ids, d = small.search(cfg1["q"][:3], 8, 8)          # only 3 nodes reachable
+    ids = ids.cpu().numpy()
+    assert (ids[:, 3:] == -1).all() and set(ids[0, :3]) == {0, 1, 2}
+    assert torch.isinf(d[:, 3:]).all()
+    small.close()
+
+
+def test_ragged_batch_and_odd_dimension():
+    X = workloads.base_vectors(1, 1500)[:, :50].copy()      # m = 50, not a multiple of 4
+    Q = workloads.query_vectors(1, 203)[:, :50].copy()
+    g = oracle.hnsw_build(X, 12, 60, 99)                   # deg0 = 24
+    fp, _ = oracle.build_tables(X, g, 10, 5)
+    ix = fg.Index(X)
+    ix.set_graph(g.adj0, g.level, g.up_off, g.up_adj, g.entry, g.maxlevel, g.M)
+    ix.build_tables(10, 5, basis=fp.P, stats=fp.stats())
+    q = torch.from_numpy(Q).cuda()
+    for mode, f in ((fg.MODE_PLAIN, None), (fg.MODE_FINGER, fp)):
+        gi, gd, gc = _gpu_search(ix, q, 7, 33, mode)
+        oi, od, oc = oracle.search(g, X, Q, 7, 33, f)
+        gt, _ = oracle.bruteforce(X, Q, 7)
+        _compare(gi, gd, gc, oi, od, oc, gt, 7, f"m=50 mode={mode}")
+    ix.close()
+
+
+def test_two_neighbour_slots_per_lane():
+    """deg0 = 48 > 32 (two neighbour slots per lane), M = 24."""
+    X = workloads.base_vectors(1, 3000)
+    Q = workloads.query_vectors(1, 100)
+    g = oracle.hnsw_build(X, 24, 80, 11)
+    fp, _ = oracle.build_tables(X, g, 16, 12)
+    ix = fg.Index(X)
+    ix.set_graph(g.adj0, g.level, g.up_off, g.up_adj, g.entry, g.maxlevel, g.M)
+    ix.build_tables(16, 12, basis=fp.P, stats=fp.stats())
+    q = torch.from_numpy(Q).cuda()
+    gt, _ = oracle.bruteforce(X, Q, 10)
+    for mode, f in ((fg.MODE_PLAIN, None), (fg.MODE_FINGER, fp)):
+        gi, gd, gc = _gpu_search(ix, q, 10, 64, mode)
+        oi, od, oc = oracle.search(g, X, Q, 10, 64, f)
+        _compare(gi, gd, gc, oi, od, oc, gt, 10, f"deg0=48 mode={mode}")
+    ix.close()
