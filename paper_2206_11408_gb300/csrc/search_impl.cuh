@@ -122,23 +122,27 @@ __device__ __forceinline__ void exact_list(const QRegs<LP, VPL>& q, const DevInd
                                            const uint32_t* nbs, const int* lst, int nlist,
                                            float* xb, int lane) {
     constexpr int RPW = 32 / G;
+    constexpr int U = VPL >= 4 ? 2 : 4;   // rows per group in flight
     const int grp = lane / G, kin = lane % G;
-    for (int base = 0; base < nlist; base += 2 * RPW) {
-        const int i0 = base + grp, i1 = base + RPW + grp;
-        const int o0 = i0 < nlist ? lst[i0] : -1;
-        const int o1 = i1 < nlist ? lst[i1] : -1;
-        float p0 = 0.f, p1 = 0.f;
-        if (o0 >= 0) p0 = row_partial<LP, G, VPL>(q, ix, nbs[o0], kin);
-        if (o1 >= 0) p1 = row_partial<LP, G, VPL>(q, ix, nbs[o1], kin);
+    for (int base = 0; base < nlist; base += U * RPW) {
+        int o[U];
+        float p[U];
 #pragma unroll
-        for (int off = G / 2; off > 0; off >>= 1) {
-            p0 += __shfl_xor_sync(FULLMASK, p0, off);
-            p1 += __shfl_xor_sync(FULLMASK, p1, off);
+        for (int u = 0; u < U; ++u) {
+            const int i = base + u * RPW + grp;
+            o[u] = i < nlist ? lst[i] : -1;
         }
-        if (kin == 0) {
-            if (o0 >= 0) xb[o0] = p0;
-            if (o1 >= 0) xb[o1] = p1;
-        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            p[u] = o[u] >= 0 ? row_partial<LP, G, VPL>(q, ix, nbs[o[u]], kin) : 0.f;
+#pragma unroll
+        for (int off = G / 2; off > 0; off >>= 1)
+#pragma unroll
+            for (int u = 0; u < U; ++u) p[u] += __shfl_xor_sync(FULLMASK, p[u], off);
+        if (kin == 0)
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (o[u] >= 0) xb[o[u]] = p[u];
     }
     __syncwarp();
 }
@@ -265,16 +269,92 @@ __device__ __forceinline__ float edge_cos(const DevIndex& ix, size_t e, const fl
                     (__nv_fp8x2_storage_t)(w[i] >> 16), __NV_E4M3);
                 const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&lo));
                 const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&hi));
-                const float* y = uq + k * 16 + i * 4;
-                acc = fmaf(a.x, y[0], acc);
-                acc = fmaf(a.y, y[1], acc);
-                acc = fmaf(b.x, y[2], acc);
-                acc = fmaf(b.y, y[3], acc);
+                const int k0 = k * 16 + i * 4;
+                const int rp = ix.r4 * 4;
+                acc = fmaf(a.x, k0 + 0 < rp ? uq[k0 + 0] : 0.f, acc);
+                acc = fmaf(a.y, k0 + 1 < rp ? uq[k0 + 1] : 0.f, acc);
+                acc = fmaf(b.x, k0 + 2 < rp ? uq[k0 + 2] : 0.f, acc);
+                acc = fmaf(b.y, k0 + 3 < rp ? uq[k0 + 3] : 0.f, acc);
             }
         }
         acc *= ix.code_inv;
     }
     return acc;
+}
+
+// t_hat for a list of edges of one centre: edge rows (contiguous per centre)
+// are gathered by groups of GE lanes, one 16-byte chunk per lane, U rows per
+// group in flight; the partial dots are reduced inside the group and written
+// to out[o] for list entry o = lst[i] (the neighbour slot).
+template <bool LP>
+__device__ __forceinline__ void edge_cos_list(const DevIndex& ix, size_t ebase, const float* uq,
+                                              const int* lst, int nn, float* out, int lane) {
+    constexpr int U = 4;
+    constexpr int W = LP ? 16 : 4;
+    const int nch = LP ? ix.r16 : ix.r4;
+    const int r_pad = ix.r4 * 4;
+    int GE = 1;
+    while (GE < nch) GE <<= 1;
+    const int RPW = 32 / GE, grp = lane / GE, kin = lane % GE;
+    float qv[W];
+#pragma unroll
+    for (int e = 0; e < W; ++e) {
+        const int k = kin * W + e;
+        qv[e] = (kin < nch && k < r_pad) ? uq[k] : 0.f;
+    }
+    for (int base = 0; base < nn; base += U * RPW) {
+        int o[U];
+        float p[U];
+        if constexpr (!LP) {
+            float4 x[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int i = base + u * RPW + grp;
+                o[u] = i < nn ? lst[i] : -1;
+                x[u] = (o[u] >= 0 && kin < nch) ? __ldg(ix.edge_u + (ebase + o[u]) * ix.r4 + kin)
+                                               : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                p[u] = fmaf(x[u].x, qv[0], fmaf(x[u].y, qv[1], fmaf(x[u].z, qv[2], x[u].w * qv[3])));
+        } else {
+            uint4 x[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int i = base + u * RPW + grp;
+                o[u] = i < nn ? lst[i] : -1;
+                x[u] = (o[u] >= 0 && kin < nch) ? __ldg(ix.edge_q + (ebase + o[u]) * ix.r16 + kin)
+                                               : make_uint4(0u, 0u, 0u, 0u);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const uint32_t w[4] = {x[u].x, x[u].y, x[u].z, x[u].w};
+                float acc = 0.f;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const __half2_raw lo = __nv_cvt_fp8x2_to_halfraw2(
+                        (__nv_fp8x2_storage_t)(w[i] & 0xFFFFu), __NV_E4M3);
+                    const __half2_raw hi = __nv_cvt_fp8x2_to_halfraw2(
+                        (__nv_fp8x2_storage_t)(w[i] >> 16), __NV_E4M3);
+                    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&lo));
+                    const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&hi));
+                    acc = fmaf(a.x, qv[4 * i + 0], acc);
+                    acc = fmaf(a.y, qv[4 * i + 1], acc);
+                    acc = fmaf(b.x, qv[4 * i + 2], acc);
+                    acc = fmaf(b.y, qv[4 * i + 3], acc);
+                }
+                p[u] = acc * ix.code_inv;
+            }
+        }
+        for (int off = GE >> 1; off > 0; off >>= 1)
+#pragma unroll
+            for (int u = 0; u < U; ++u) p[u] += __shfl_xor_sync(FULLMASK, p[u], off);
+        if (kin == 0)
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (o[u] >= 0) out[o[u]] = p[u];
+    }
+    __syncwarp();
 }
 
 // learned predictor: t = w3 . relu(W2 relu(W1 f + b1) + b2) + b3, features f of
@@ -301,7 +381,7 @@ __device__ __forceinline__ float mlp_predict(const DevIndex& ix, const float* f,
 }
 
 template <int MODE, int G, int VPL, int NPL>
-__global__ void __launch_bounds__(256) k_search(DevIndex ix, SearchArgs a) {
+__global__ void __launch_bounds__(256, 2) k_search(DevIndex ix, SearchArgs a) {
     constexpr bool LP = MODE == FINGER_MODE_FINGER_LP;
     constexpr bool EST = MODE != FINGER_MODE_PLAIN;
     constexpr bool MLP = MODE == FINGER_MODE_FINGER_MLP;
@@ -493,6 +573,17 @@ __global__ void __launch_bounds__(256) k_search(DevIndex ix, SearchArgs a) {
             // a5: estimates of the new neighbours against ub at expansion start
             const bool full0 = sz == ef;
             const float ub0 = full0 ? Tk[ef - 1] : INFINITY;
+            if (!MLP && use_est) {
+                int nn = 0;
+#pragma unroll
+                for (int s = 0; s < NPL; ++s) {
+                    const unsigned bm = __ballot_sync(FULLMASK, isnew[s]);
+                    if (isnew[s]) lst[nn + __popc(bm & ltmask)] = s * 32 + lane;
+                    nn += __popc(bm);
+                }
+                __syncwarp();
+                edge_cos_list<LP>(ix, (size_t)c * ix.deg0, uq, lst, nn, es, lane);
+            }
             int nl = 0;
 #pragma unroll
             for (int s = 0; s < NPL; ++s) {
@@ -500,9 +591,9 @@ __global__ void __launch_bounds__(256) k_search(DevIndex ix, SearchArgs a) {
                 if (use_est && isnew[s]) {
                     const size_t e = (size_t)c * ix.deg0 + s * 32 + lane;
                     const float2 sc = __ldg(ix.edge_s + e);
-                    const float th = edge_cos<LP>(ix, e, uq);
                     float t;
                     if constexpr (MLP) {
+                        const float th = edge_cos<false>(ix, e, uq);
                         // learned predictor in place of distribution matching
                         float f[MAX_R + 8];
                         const float4* ud = ix.edge_u + e * ix.r4;
@@ -521,7 +612,7 @@ __global__ void __launch_bounds__(256) k_search(DevIndex ix, SearchArgs a) {
                         const float pred = mlp_predict(ix, f, ix.r + 4);
                         t = isfinite(pred) ? pred + ix.mlp_eps : fmaf(th, ix.alpha, ix.beta);
                     } else {
-                        t = fmaf(th, ix.alpha, ix.beta);
+                        t = fmaf(es[s * 32 + lane], ix.alpha, ix.beta);
                     }
                     const float dd = ac - sc.y;
                     est = dd * dd * cc + qres2 + sc.x * sc.x - 2.f * qres_n * sc.x * t;
