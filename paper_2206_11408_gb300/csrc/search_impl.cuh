@@ -405,6 +405,10 @@ __global__ void __launch_bounds__(256, 2) k_search(DevIndex ix, SearchArgs a) {
     float* es = reinterpret_cast<float*>(nbs + 32 * NPL);
     float* xb = es + 32 * NPL;
     int* lst = reinterpret_cast<int*>(xb + 32 * NPL);
+    float* ak = reinterpret_cast<float*>(lst + 32 * NPL);     // admitted keys (sorted)
+    uint32_t* ai = reinterpret_cast<uint32_t*>(ak + 32 * NPL);
+    int* apos = reinterpret_cast<int*>(ai + 32 * NPL);        // slot of each admission
+    float* aub = reinterpret_cast<float*>(apos + 32 * NPL);   // ub after it
 
     const int64_t slot = (int64_t)blockIdx.x * wpb + wib;
     uint32_t* bitmap = a.bitmap + slot * a.words;
@@ -585,6 +589,7 @@ __global__ void __launch_bounds__(256, 2) k_search(DevIndex ix, SearchArgs a) {
                 edge_cos_list<LP>(ix, (size_t)c * ix.deg0, uq, lst, nn, es, lane);
             }
             int nl = 0;
+            bool needr[NPL];
 #pragma unroll
             for (int s = 0; s < NPL; ++s) {
                 float est = -INFINITY;
@@ -618,6 +623,7 @@ __global__ void __launch_bounds__(256, 2) k_search(DevIndex ix, SearchArgs a) {
                     est = dd * dd * cc + qres2 + sc.x * sc.x - 2.f * qres_n * sc.x * t;
                 }
                 const bool need = isnew[s] && (!use_est || !full0 || !(est > ub0));
+                needr[s] = need;
                 es[s * 32 + lane] = est;
                 const unsigned bm = __ballot_sync(FULLMASK, need);
                 if (need) lst[nl + __popc(bm & ltmask)] = s * 32 + lane;
@@ -628,29 +634,177 @@ __global__ void __launch_bounds__(256, 2) k_search(DevIndex ix, SearchArgs a) {
             exact_list<LP, G, VPL>(q, ix, nbs, lst, nl, xb, lane);
             c_gath += nl;
 
-            // sequential gate and admission in adjacency order
+            if (full0) {
+                // T is full and stays full.  Only neighbours evaluated exactly and
+                // below the starting ub can be admitted; replay the sequential gate
+                // over them with a running model of ub (top-ef of T and the admitted
+                // set A), then merge A into T once.
+                const float u0d = Tk[ef - 1];
+                const uint32_t u0i = Ti[ef - 1] & ~EXP;
+                unsigned cb[NPL], cskip[NPL];
 #pragma unroll
-            for (int s = 0; s < NPL; ++s) {
-                unsigned bits = __ballot_sync(FULLMASK, isnew[s]);
-                c_exa += __popc(bits);
-                while (bits) {
-                    const int j = __ffs(bits) - 1;
-                    bits &= bits - 1;
-                    const int o = s * 32 + j;
-                    const bool full = sz == ef;
-                    if (use_est && full) {
-                        c_est++;
-                        if (es[o] > Tk[ef - 1]) {
-                            c_skip++;
+                for (int s = 0; s < NPL; ++s) {
+                    const int o = s * 32 + lane;
+                    const bool cand = needr[s] && key_lt(xb[o], nb[s], u0d, u0i);
+                    cb[s] = __ballot_sync(FULLMASK, cand);
+                    cskip[s] = 0u;
+                }
+                float ubd = u0d;
+                uint32_t ubi = u0i;
+                int tk = ef, na = 0, nadm = 0;
+#pragma unroll
+                for (int s = 0; s < NPL; ++s) {
+                    unsigned bits = cb[s];
+                    while (bits) {
+                        const int j = __ffs(bits) - 1;
+                        bits &= bits - 1;
+                        const int o = s * 32 + j;
+                        if (use_est && es[o] > ubd) {
+                            cskip[s] |= 1u << j;
                             continue;
                         }
+                        const float d = xb[o];
+                        const uint32_t id = nbs[o];
+                        if (!key_lt(d, id, ubd, ubi)) continue;
+                        // the current worst of the top ef leaves it
+                        if (tk == 0 || (na > 0 && key_lt(Tk[tk - 1], Ti[tk - 1] & ~EXP, ak[na - 1],
+                                                         ai[na - 1])))
+                            na--;
+                        else
+                            tk--;
+                        // insert (d, id) into the sorted admitted list
+                        int p = 0;
+                        for (int b = 0; b < na; b += 32) {
+                            const int i = b + lane;
+                            p += __popc(__ballot_sync(FULLMASK, i < na && key_lt(ak[i], ai[i], d, id)));
+                        }
+                        for (int top = na - 1; top >= p; top -= 32) {
+                            const int i = top - lane;
+                            float kd = 0.f;
+                            uint32_t ki = 0;
+                            if (i >= p) {
+                                kd = ak[i];
+                                ki = ai[i];
+                            }
+                            __syncwarp();
+                            if (i >= p) {
+                                ak[i + 1] = kd;
+                                ai[i + 1] = ki;
+                            }
+                            __syncwarp();
+                        }
+                        if (lane == 0) {
+                            ak[p] = d;
+                            ai[p] = id;
+                        }
+                        __syncwarp();
+                        na++;
+                        // new ub: the larger of T[tk-1] and max(A)
+                        ubd = ak[na - 1];
+                        ubi = ai[na - 1];
+                        if (tk > 0 && key_lt(ubd, ubi, Tk[tk - 1], Ti[tk - 1] & ~EXP)) {
+                            ubd = Tk[tk - 1];
+                            ubi = Ti[tk - 1] & ~EXP;
+                        }
+                        if (lane == 0) {
+                            apos[nadm] = o;
+                            aub[nadm] = ubd;
+                        }
+                        __syncwarp();
+                        nadm++;
                     }
-                    const float d = xb[o];
-                    const uint32_t id = nbs[o];
-                    c_exact++;
-                    if (!full || key_lt(d, id, Tk[sz - 1], Ti[sz - 1] & ~EXP)) {
-                        t_insert(Tk, Ti, sz, ef, d, id, cursor, lane);
-                        c_adm++;
+                }
+                // counters of every new neighbour under the sequential semantics
+#pragma unroll
+                for (int s = 0; s < NPL; ++s) {
+                    const int o = s * 32 + lane;
+                    bool skipped = false;
+                    if (isnew[s]) {
+                        if ((cb[s] >> lane) & 1u) {
+                            skipped = (cskip[s] >> lane) & 1u;
+                        } else if (use_est) {
+                            float ubt = u0d;
+                            for (int k = 0; k < nadm; ++k)
+                                if (apos[k] < o) ubt = aub[k];
+                            skipped = es[o] > ubt;
+                        }
+                    }
+                    const int nnew = __popc(__ballot_sync(FULLMASK, isnew[s]));
+                    const int nsk = __popc(__ballot_sync(FULLMASK, skipped));
+                    c_exa += nnew;
+                    if (use_est) c_est += nnew;
+                    c_skip += nsk;
+                    c_exact += nnew - nsk;
+                }
+                c_adm += nadm;
+                // merge A (sorted, na entries) into T[0..tk) -> T[0..ef)
+                if (na > 0) {
+                    int apos_t = 0;   // rank of this lane's admitted key among T[0..tk)
+                    float akd = 0.f;
+                    uint32_t aki = 0;
+                    if (lane < na) {
+                        akd = ak[lane];
+                        aki = ai[lane];
+                        int lo = 0, hi = tk;
+                        while (lo < hi) {
+                            const int mid = (lo + hi) >> 1;
+                            if (key_lt(Tk[mid], Ti[mid] & ~EXP, akd, aki)) lo = mid + 1;
+                            else hi = mid;
+                        }
+                        apos_t = lo;
+                    }
+                    const int pmin = __shfl_sync(FULLMASK, apos_t, 0);
+                    for (int top = tk - 1; top >= pmin; top -= 32) {
+                        const int i = top - lane;
+                        const bool act = i >= pmin;
+                        float kd = 0.f;
+                        uint32_t ki = 0;
+                        int sh = 0;
+                        if (act) {
+                            kd = Tk[i];
+                            ki = Ti[i];
+                            for (int k = 0; k < na; ++k) sh += key_lt(ak[k], ai[k], kd, ki & ~EXP);
+                        }
+                        __syncwarp();
+                        if (act && sh) {
+                            Tk[i + sh] = kd;
+                            Ti[i + sh] = ki;
+                        }
+                        __syncwarp();
+                    }
+                    if (lane < na) {
+                        Tk[apos_t + lane] = akd;
+                        Ti[apos_t + lane] = aki;
+                    }
+                    __syncwarp();
+                    const int newpos = pmin;   // smallest new entry (A is sorted)
+                    if (newpos < cursor) cursor = newpos;
+                }
+            } else {
+                // T not full at the start of this expansion: plain sequential replay
+#pragma unroll
+                for (int s = 0; s < NPL; ++s) {
+                    unsigned bits = __ballot_sync(FULLMASK, isnew[s]);
+                    c_exa += __popc(bits);
+                    while (bits) {
+                        const int j = __ffs(bits) - 1;
+                        bits &= bits - 1;
+                        const int o = s * 32 + j;
+                        const bool full = sz == ef;
+                        if (use_est && full) {
+                            c_est++;
+                            if (es[o] > Tk[ef - 1]) {
+                                c_skip++;
+                                continue;
+                            }
+                        }
+                        const float d = xb[o];
+                        const uint32_t id = nbs[o];
+                        c_exact++;
+                        if (!full || key_lt(d, id, Tk[sz - 1], Ti[sz - 1] & ~EXP)) {
+                            t_insert(Tk, Ti, sz, ef, d, id, cursor, lane);
+                            c_adm++;
+                        }
                     }
                 }
             }
