@@ -94,7 +94,11 @@ def lib(build: bool = True):
     """Load libfinger.so (building it first when stale).  Raises if it cannot."""
     global _lib
     if _lib is None:
-        path = _build.build() if build else _build.LIB
+        checked = os.environ.get("FINGER_CHECKED", "0") == "1"
+        if build:
+            path = _build.build(checked=checked)
+        else:
+            path = _build.LIB_CHECKED if checked else _build.LIB
         if not os.path.exists(path):
             raise RuntimeError(f"libfinger.so is missing at {path}; build it with _build.build()")
         L = ctypes.CDLL(path)

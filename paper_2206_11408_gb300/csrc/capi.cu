@@ -37,7 +37,7 @@ void choose_groups(int nchunks, int* G, int* VPL) {
 int search_smem_per_warp(const DevIndex& ix, int mode, int ef_cap, int H, int NPL) {
     const int r_pad = ix.r4 * 4;
     const int qs_len = mode == FINGER_MODE_FINGER_LP ? ix.m8 * 8 : ix.m4 * 4;
-    int b = 8 * ef_cap + 4 * H + 8 * r_pad + 4 * ((qs_len + 3) & ~3) + 32 * 32 * NPL;
+    int b = 8 * ef_cap + 4 * H + 8 * r_pad + 4 * ((qs_len + 3) & ~3) + 32 * 32 * NPL + 32;
     return (b + 15) & ~15;
 }
 

@@ -36,6 +36,23 @@ namespace fg {
 
 #define FULLMASK 0xffffffffu
 
+// Debug builds (-DFG_CHECKED=1) validate every shared/global index of the
+// search kernel: the first violation's site code is latched into the status
+// word and the index is clamped to 0, so a faulty traversal reports instead of
+// faulting.  Release builds compile the checks away.
+#ifndef FG_CHECKED
+#define FG_CHECKED 0
+#endif
+__device__ int* g_chk_err;
+__device__ __forceinline__ int64_t chk(int64_t i, int64_t lim, int code) {
+    if (FG_CHECKED && (i < 0 || i >= lim)) {
+        atomicCAS(g_chk_err, 0, code);
+        return 0;
+    }
+    return i;
+}
+#define CK(i, lim, code) chk((int64_t)(i), (int64_t)(lim), (code))
+
 __device__ __forceinline__ bool key_lt(float da, uint32_t ia, float db, uint32_t ib) {
     return da < db || (da == db && ia < ib);
 }
@@ -134,7 +151,7 @@ __device__ __forceinline__ void exact_list(const QRegs<LP, VPL>& q, const DevInd
         }
 #pragma unroll
         for (int u = 0; u < U; ++u)
-            p[u] = o[u] >= 0 ? row_partial<LP, G, VPL>(q, ix, nbs[o[u]], kin) : 0.f;
+            p[u] = o[u] >= 0 ? row_partial<LP, G, VPL>(q, ix, (uint32_t)CK(nbs[CK(o[u], 64, 1018)], ix.n, 1019), kin) : 0.f;
 #pragma unroll
         for (int off = G / 2; off > 0; off >>= 1)
 #pragma unroll
@@ -409,7 +426,9 @@ __global__ void __launch_bounds__(256, 2) k_search(DevIndex ix, SearchArgs a) {
     uint32_t* ai = reinterpret_cast<uint32_t*>(ak + 32 * NPL);
     int* apos = reinterpret_cast<int*>(ai + 32 * NPL);        // slot of each admission
     float* aub = reinterpret_cast<float*>(apos + 32 * NPL);   // ub after it
+    int* meta = reinterpret_cast<int*>(aub + 32 * NPL);       // replay results (8 ints)
 
+    if (FG_CHECKED) g_chk_err = a.err;   // same value from every thread
     const int64_t slot = (int64_t)blockIdx.x * wpb + wib;
     uint32_t* bitmap = a.bitmap + slot * a.words;
     uint32_t* spl = a.spill + slot * a.spill_cap;
@@ -472,7 +491,7 @@ __global__ void __launch_bounds__(256, 2) k_search(DevIndex ix, SearchArgs a) {
                     fail = true;
                     break;
                 }
-                const uint32_t* row = ix.up_adj + (size_t)(ix.up_off[cur] + l - 1) * ix.Mup;
+                const uint32_t* row = ix.up_adj + (size_t)CK(ix.up_off[CK(cur, ix.n, 1006)] + l - 1, 1LL << 40, 1007) * ix.Mup;
                 const uint32_t id = lane < ix.Mup ? row[lane] : PAD;
                 const bool v = id != PAD;
                 const unsigned bm = __ballot_sync(FULLMASK, v);
@@ -524,8 +543,8 @@ __global__ void __launch_bounds__(256, 2) k_search(DevIndex ix, SearchArgs a) {
                 fail = true;
                 break;
             }
-            const uint32_t c = Ti[cursor];
-            const float dc = Tk[cursor];
+            const uint32_t c = Ti[CK(cursor, ef, 1001)];
+            const float dc = Tk[CK(cursor, ef, 1002)];
             __syncwarp();
             if (lane == 0) Ti[cursor] = c | EXP;
             expansions++;
@@ -535,7 +554,7 @@ __global__ void __launch_bounds__(256, 2) k_search(DevIndex ix, SearchArgs a) {
 #pragma unroll
             for (int s = 0; s < NPL; ++s) {
                 const int j = s * 32 + lane;
-                nb[s] = j < ix.deg0 ? __ldg(ix.adj0 + (size_t)c * ix.deg0 + j) : PAD;
+                nb[s] = j < ix.deg0 ? __ldg(ix.adj0 + CK((size_t)c * ix.deg0 + j, ix.n * ix.deg0, 1003)) : PAD;
             }
             float cc = 0.f, pc0 = 0.f, pc1 = 0.f;
             if (use_est) {
@@ -548,10 +567,10 @@ __global__ void __launch_bounds__(256, 2) k_search(DevIndex ix, SearchArgs a) {
 #pragma unroll
             for (int s = 0; s < NPL; ++s) {
                 int res = V_SEEN;
-                if (nb[s] != PAD) res = visit(hash, a.H, logH, nb[s], spill_mode, bitmap);
+                if (nb[s] != PAD) res = visit(hash, a.H, logH, (uint32_t)CK(nb[s], ix.n, 1004), spill_mode, bitmap);
                 isnew[s] = res != V_SEEN;
                 const unsigned sb = __ballot_sync(FULLMASK, res == V_NEW_SPILL);
-                if (res == V_NEW_SPILL) spl[nspill + __popc(sb & ltmask)] = nb[s];
+                if (res == V_NEW_SPILL) spl[CK(nspill + __popc(sb & ltmask), a.spill_cap, 1005)] = nb[s];
                 nspill += __popc(sb);
                 hcount += __popc(__ballot_sync(FULLMASK, res == V_NEW));
                 nbs[s * 32 + lane] = nb[s];
@@ -626,7 +645,7 @@ __global__ void __launch_bounds__(256, 2) k_search(DevIndex ix, SearchArgs a) {
                 needr[s] = need;
                 es[s * 32 + lane] = est;
                 const unsigned bm = __ballot_sync(FULLMASK, need);
-                if (need) lst[nl + __popc(bm & ltmask)] = s * 32 + lane;
+                if (need) lst[CK(nl + __popc(bm & ltmask), 32 * NPL, 1017)] = s * 32 + lane;
                 nl += __popc(bm);
             }
             __syncwarp();
@@ -649,71 +668,64 @@ __global__ void __launch_bounds__(256, 2) k_search(DevIndex ix, SearchArgs a) {
                     cb[s] = __ballot_sync(FULLMASK, cand);
                     cskip[s] = 0u;
                 }
-                float ubd = u0d;
-                uint32_t ubi = u0i;
-                int tk = ef, na = 0, nadm = 0;
+                // the serial replay runs on lane 0 only; results go through smem
+                if (lane == 0) {
+                    float ubd = u0d;
+                    uint32_t ubi = u0i;
+                    int tk = ef, na = 0, nadm = 0;
 #pragma unroll
-                for (int s = 0; s < NPL; ++s) {
-                    unsigned bits = cb[s];
-                    while (bits) {
-                        const int j = __ffs(bits) - 1;
-                        bits &= bits - 1;
-                        const int o = s * 32 + j;
-                        if (use_est && es[o] > ubd) {
-                            cskip[s] |= 1u << j;
-                            continue;
-                        }
-                        const float d = xb[o];
-                        const uint32_t id = nbs[o];
-                        if (!key_lt(d, id, ubd, ubi)) continue;
-                        // the current worst of the top ef leaves it
-                        if (tk == 0 || (na > 0 && key_lt(Tk[tk - 1], Ti[tk - 1] & ~EXP, ak[na - 1],
-                                                         ai[na - 1])))
-                            na--;
-                        else
-                            tk--;
-                        // insert (d, id) into the sorted admitted list
-                        int p = 0;
-                        for (int b = 0; b < na; b += 32) {
-                            const int i = b + lane;
-                            p += __popc(__ballot_sync(FULLMASK, i < na && key_lt(ak[i], ai[i], d, id)));
-                        }
-                        for (int top = na - 1; top >= p; top -= 32) {
-                            const int i = top - lane;
-                            float kd = 0.f;
-                            uint32_t ki = 0;
-                            if (i >= p) {
-                                kd = ak[i];
-                                ki = ai[i];
+                    for (int s = 0; s < NPL; ++s) {
+                        unsigned bits = cb[s];
+                        unsigned skm = 0u;
+                        while (bits) {
+                            const int j = __ffs(bits) - 1;
+                            bits &= bits - 1;
+                            const int o = s * 32 + j;
+                            if (use_est && es[o] > ubd) {
+                                skm |= 1u << j;
+                                continue;
                             }
-                            __syncwarp();
-                            if (i >= p) {
-                                ak[i + 1] = kd;
-                                ai[i + 1] = ki;
+                            const float d = xb[CK(o, 32 * NPL, 1008)];
+                            const uint32_t id = nbs[o];
+                            if (!key_lt(d, id, ubd, ubi)) continue;
+                            // the current worst of the top ef leaves it
+                            if (tk == 0 ||
+                                (na > 0 && key_lt(Tk[CK(tk - 1, ef, 1009)], Ti[tk - 1] & ~EXP,
+                                                  ak[CK(na - 1, 32 * NPL, 1010)], ai[na - 1])))
+                                na--;
+                            else
+                                tk--;
+                            // insert (d, id) into the sorted admitted list
+                            int p = na;
+                            while (p > 0 && key_lt(d, id, ak[p - 1], ai[p - 1])) {
+                                ak[CK(p, 32 * NPL, 1011)] = ak[p - 1];
+                                ai[p] = ai[p - 1];
+                                --p;
                             }
-                            __syncwarp();
-                        }
-                        if (lane == 0) {
-                            ak[p] = d;
+                            ak[CK(p, 32 * NPL, 1012)] = d;
                             ai[p] = id;
-                        }
-                        __syncwarp();
-                        na++;
-                        // new ub: the larger of T[tk-1] and max(A)
-                        ubd = ak[na - 1];
-                        ubi = ai[na - 1];
-                        if (tk > 0 && key_lt(ubd, ubi, Tk[tk - 1], Ti[tk - 1] & ~EXP)) {
-                            ubd = Tk[tk - 1];
-                            ubi = Ti[tk - 1] & ~EXP;
-                        }
-                        if (lane == 0) {
-                            apos[nadm] = o;
+                            na++;
+                            // new ub: the larger of T[tk-1] and max(A)
+                            ubd = ak[na - 1];
+                            ubi = ai[na - 1];
+                            if (tk > 0 && key_lt(ubd, ubi, Tk[tk - 1], Ti[tk - 1] & ~EXP)) {
+                                ubd = Tk[tk - 1];
+                                ubi = Ti[tk - 1] & ~EXP;
+                            }
+                            apos[CK(nadm, 32 * NPL, 1013)] = o;
                             aub[nadm] = ubd;
+                            nadm++;
                         }
-                        __syncwarp();
-                        nadm++;
+                        meta[3 + s] = (int)skm;
                     }
+                    meta[0] = tk;
+                    meta[1] = na;
+                    meta[2] = nadm;
                 }
+                __syncwarp();
+                const int tk = meta[0], na = meta[1], nadm = meta[2];
+#pragma unroll
+                for (int s = 0; s < NPL; ++s) cskip[s] = (unsigned)meta[3 + s];
                 // counters of every new neighbour under the sequential semantics
 #pragma unroll
                 for (int s = 0; s < NPL; ++s) {
@@ -739,21 +751,28 @@ __global__ void __launch_bounds__(256, 2) k_search(DevIndex ix, SearchArgs a) {
                 c_adm += nadm;
                 // merge A (sorted, na entries) into T[0..tk) -> T[0..ef)
                 if (na > 0) {
-                    int apos_t = 0;   // rank of this lane's admitted key among T[0..tk)
-                    float akd = 0.f;
-                    uint32_t aki = 0;
-                    if (lane < na) {
-                        akd = ak[lane];
-                        aki = ai[lane];
-                        int lo = 0, hi = tk;
-                        while (lo < hi) {
-                            const int mid = (lo + hi) >> 1;
-                            if (key_lt(Tk[mid], Ti[mid] & ~EXP, akd, aki)) lo = mid + 1;
-                            else hi = mid;
+                    int apt[NPL];         // rank of each admitted key among T[0..tk)
+                    float akd[NPL];
+                    uint32_t aki[NPL];
+#pragma unroll
+                    for (int t = 0; t < NPL; ++t) {
+                        const int k = lane + 32 * t;
+                        apt[t] = 0;
+                        akd[t] = 0.f;
+                        aki[t] = 0u;
+                        if (k < na) {
+                            akd[t] = ak[k];
+                            aki[t] = ai[k];
+                            int lo = 0, hi = tk;
+                            while (lo < hi) {
+                                const int mid = (lo + hi) >> 1;
+                                if (key_lt(Tk[mid], Ti[mid] & ~EXP, akd[t], aki[t])) lo = mid + 1;
+                                else hi = mid;
+                            }
+                            apt[t] = lo;
                         }
-                        apos_t = lo;
                     }
-                    const int pmin = __shfl_sync(FULLMASK, apos_t, 0);
+                    const int pmin = __shfl_sync(FULLMASK, apt[0], 0);   // A is sorted
                     for (int top = tk - 1; top >= pmin; top -= 32) {
                         const int i = top - lane;
                         const bool act = i >= pmin;
@@ -767,18 +786,21 @@ __global__ void __launch_bounds__(256, 2) k_search(DevIndex ix, SearchArgs a) {
                         }
                         __syncwarp();
                         if (act && sh) {
-                            Tk[i + sh] = kd;
+                            Tk[CK(i + sh, ef, 1014)] = kd;
                             Ti[i + sh] = ki;
                         }
                         __syncwarp();
                     }
-                    if (lane < na) {
-                        Tk[apos_t + lane] = akd;
-                        Ti[apos_t + lane] = aki;
+#pragma unroll
+                    for (int t = 0; t < NPL; ++t) {
+                        const int k = lane + 32 * t;
+                        if (k < na) {
+                            Tk[CK(apt[t] + k, ef, 1015)] = akd[t];
+                            Ti[apt[t] + k] = aki[t];
+                        }
                     }
                     __syncwarp();
-                    const int newpos = pmin;   // smallest new entry (A is sorted)
-                    if (newpos < cursor) cursor = newpos;
+                    if (pmin < cursor) cursor = pmin;
                 }
             } else {
                 // T not full at the start of this expansion: plain sequential replay
@@ -802,6 +824,7 @@ __global__ void __launch_bounds__(256, 2) k_search(DevIndex ix, SearchArgs a) {
                         const uint32_t id = nbs[o];
                         c_exact++;
                         if (!full || key_lt(d, id, Tk[sz - 1], Ti[sz - 1] & ~EXP)) {
+                            CK(sz, ef + 1, 1016);
                             t_insert(Tk, Ti, sz, ef, d, id, cursor, lane);
                             c_adm++;
                         }
