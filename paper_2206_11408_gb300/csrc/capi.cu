@@ -155,7 +155,7 @@ finger_status make_plan(finger_index* ix, int mode, int ef_max, int64_t nq, Sear
     choose_groups(mode == FINGER_MODE_FINGER_LP ? ix->m8 : ix->m4, &p->G, &p->VPL);
     p->NPL = ix->deg0 > 32 ? 2 : 1;
     p->ef_cap = (ef_max + 3) & ~3;
-    if (H <= 0) H = pow2ceil(std::min(std::max(16 * ef_max, 512), 4096));
+    if (H <= 0) H = pow2ceil(std::min(std::max(16 * ef_max, 512), 2048));
     if (mode == FINGER_MODE_FINGER_LP) H = std::max(H, pow2ceil(2 * p->ef_cap));
     p->H = H;
     p->wpb = wpb;

@@ -164,6 +164,17 @@ __device__ __forceinline__ void exact_list(const QRegs<LP, VPL>& q, const DevInd
     __syncwarp();
 }
 
+// L2 prefetch of one full row (issued by the lane that owns the neighbour, so
+// every row of an expansion is requested at once)
+template <bool LP>
+__device__ __forceinline__ void prefetch_row(const DevIndex& ix, uint32_t id) {
+    const char* base = LP ? reinterpret_cast<const char*>(ix.Xh + (size_t)id * ix.m8)
+                          : reinterpret_cast<const char*>(ix.X + (size_t)id * ix.m4);
+    const int bytes = LP ? ix.m8 * 16 : ix.m4 * 16;
+    for (int off = 0; off < bytes; off += 128)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(base + off));
+}
+
 // exact FP32 distance of one row, whole warp (used for the FP32 re-rank)
 __device__ __forceinline__ float exact_f32_row(const float* qs, const DevIndex& ix, uint32_t id,
                                                int lane) {
@@ -596,17 +607,6 @@ __global__ void __launch_bounds__(256, 2) k_search(DevIndex ix, SearchArgs a) {
             // a5: estimates of the new neighbours against ub at expansion start
             const bool full0 = sz == ef;
             const float ub0 = full0 ? Tk[ef - 1] : INFINITY;
-            if (!MLP && use_est) {
-                int nn = 0;
-#pragma unroll
-                for (int s = 0; s < NPL; ++s) {
-                    const unsigned bm = __ballot_sync(FULLMASK, isnew[s]);
-                    if (isnew[s]) lst[nn + __popc(bm & ltmask)] = s * 32 + lane;
-                    nn += __popc(bm);
-                }
-                __syncwarp();
-                edge_cos_list<LP>(ix, (size_t)c * ix.deg0, uq, lst, nn, es, lane);
-            }
             int nl = 0;
             bool needr[NPL];
 #pragma unroll
@@ -636,13 +636,14 @@ __global__ void __launch_bounds__(256, 2) k_search(DevIndex ix, SearchArgs a) {
                         const float pred = mlp_predict(ix, f, ix.r + 4);
                         t = isfinite(pred) ? pred + ix.mlp_eps : fmaf(th, ix.alpha, ix.beta);
                     } else {
-                        t = fmaf(es[s * 32 + lane], ix.alpha, ix.beta);
+                        t = fmaf(edge_cos<LP>(ix, e, uq), ix.alpha, ix.beta);
                     }
                     const float dd = ac - sc.y;
                     est = dd * dd * cc + qres2 + sc.x * sc.x - 2.f * qres_n * sc.x * t;
                 }
                 const bool need = isnew[s] && (!use_est || !full0 || !(est > ub0));
                 needr[s] = need;
+                if (need) prefetch_row<LP>(ix, nb[s]);
                 es[s * 32 + lane] = est;
                 const unsigned bm = __ballot_sync(FULLMASK, need);
                 if (need) lst[CK(nl + __popc(bm & ltmask), 32 * NPL, 1017)] = s * 32 + lane;
