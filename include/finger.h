@@ -198,6 +198,11 @@ finger_status finger_autotune(finger_index* ix, const float* queries, int64_t nq
                               int64_t* scratch_ids, float* scratch_dists, float* best_ms,
                               void* stream);
 
+/* Cap on the layer-0 expansions (and upper-layer steps) of one query; a query
+ * that reaches it stops, keeps its results so far and latches
+ * FINGER_ERR_LIMIT.  0 restores the default (n + 16). */
+finger_status finger_set_limit(finger_index* ix, int max_expansions);
+
 /* Per-query traversal counters of the last search (device int32, nq x 8:
  * expansions, examined, estimates, skipped, exact, admitted, upper, gathered)
  * are written when `counters` is set here (NULL disables). */

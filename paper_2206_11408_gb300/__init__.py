@@ -82,6 +82,7 @@ SIGNATURES = {
     "finger_search_batch": (_I, [_P, _P, _I64, _P, _P, _I, _P, _P, _P, _P]),
     "finger_autotune": (_I, [_P, _P, _I64, _I, _I, _P, _P, _P, _P]),
     "finger_set_counters": (_I, [_P, _P]),
+    "finger_set_limit": (_I, [_P, _I]),
     "finger_knn": (_I, [_P, _P, _I64, _I, _P, _P, _P]),
     "finger_sync": (_I, [_P]),
     "finger_get_stats": (_I, [_P, _P]),
@@ -247,6 +248,10 @@ class Index:
     # ------------------------------------------------------------- search
     def set_mode(self, mode: int, warmup: int = -1):
         _check(self._lib.finger_set_mode(self._h, mode, warmup), "finger_set_mode")
+
+    def set_limit(self, max_expansions: int):
+        """Cap on expansions per query (0 = default n + 16)."""
+        _check(self._lib.finger_set_limit(self._h, max_expansions), "finger_set_limit")
 
     def set_counters(self, counters):
         """Per-query counters (int32 CUDA tensor nq x 8) for later searches; None disables."""

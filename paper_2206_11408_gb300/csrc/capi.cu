@@ -37,7 +37,8 @@ void choose_groups(int nchunks, int* G, int* VPL) {
 int search_smem_per_warp(const DevIndex& ix, int mode, int ef_cap, int H, int NPL) {
     const int r_pad = ix.r4 * 4;
     const int qs_len = mode == FINGER_MODE_FINGER_LP ? ix.m8 * 8 : ix.m4 * 4;
-    int b = 8 * ef_cap + 4 * H + 8 * r_pad + 4 * ((qs_len + 3) & ~3) + 32 * 32 * NPL + 32;
+    const int qs_bytes = mode == FINGER_MODE_FINGER_LP ? 4 * ((qs_len + 3) & ~3) : 0;
+    int b = 8 * ef_cap + 4 * H + 8 * r_pad + qs_bytes + 32 * 32 * NPL + 32;
     return (b + 15) & ~15;
 }
 
@@ -157,6 +158,7 @@ finger_status make_plan(finger_index* ix, int mode, int ef_max, int64_t nq, Sear
     p->ef_cap = (ef_max + 3) & ~3;
     if (H <= 0) H = pow2ceil(std::min(std::max(16 * ef_max, 512), 2048));
     if (mode == FINGER_MODE_FINGER_LP) H = std::max(H, pow2ceil(2 * p->ef_cap));
+    else H = std::max(H, pow2ceil(ix->m_pad));   // the query is staged in the hash region
     p->H = H;
     p->wpb = wpb;
     p->smem_per_warp = search_smem_per_warp(d, mode, p->ef_cap, p->H, p->NPL);
@@ -210,7 +212,8 @@ SearchArgs base_args(finger_index* ix, const SearchPlan& p) {
     a.ef_cap = p.ef_cap;
     a.H = p.H;
     a.rerank = 0;
-    a.max_expansions = (int)std::min<int64_t>(ix->n + 16, 1 << 30);
+    a.max_expansions = ix->max_expansions > 0 ? ix->max_expansions
+                                              : (int)std::min<int64_t>(ix->n + 16, 1 << 30);
     a.work = ix->work;
     a.err = ix->err;
     a.cnt = ix->cnt;
@@ -520,6 +523,12 @@ finger_status finger_set_mode(finger_index* ix, int mode, int warmup) {
     if (!ix || mode < 0 || mode > 3) return FINGER_ERR_INVALID_ARG;
     ix->mode = mode;
     if (warmup >= 0) ix->warmup = warmup;
+    return FINGER_OK;
+}
+
+finger_status finger_set_limit(finger_index* ix, int max_expansions) {
+    if (!ix || max_expansions < 0) return FINGER_ERR_INVALID_ARG;
+    ix->max_expansions = max_expansions;
     return FINGER_OK;
 }
 

@@ -152,6 +152,7 @@ struct finger_index {
     // search state
     int mode = FINGER_MODE_PLAIN;
     int warmup = 5;
+    int max_expansions = 0;       // 0 = n + 16
     int32_t* cnt_q = nullptr;
     // scratch
     uint32_t* work = nullptr;     // 4 words

@@ -409,7 +409,7 @@ __device__ __forceinline__ float mlp_predict(const DevIndex& ix, const float* f,
 }
 
 template <int MODE, int G, int VPL, int NPL>
-__global__ void __launch_bounds__(256, 2) k_search(DevIndex ix, SearchArgs a) {
+__global__ void __launch_bounds__(128, 5) k_search(DevIndex ix, SearchArgs a) {
     constexpr bool LP = MODE == FINGER_MODE_FINGER_LP;
     constexpr bool EST = MODE != FINGER_MODE_PLAIN;
     constexpr bool MLP = MODE == FINGER_MODE_FINGER_MLP;
@@ -428,8 +428,11 @@ __global__ void __launch_bounds__(256, 2) k_search(DevIndex ix, SearchArgs a) {
     uint32_t* hash = Ti + a.ef_cap;
     float* uq = reinterpret_cast<float*>(hash + a.H);
     float* pq = uq + r_pad;
-    float* qs = pq + r_pad;
-    uint32_t* nbs = reinterpret_cast<uint32_t*>(qs + ((qs_len + 3) & ~3));
+    // the query staging buffer is only read before the visited hash is cleared,
+    // so outside the LP mode (which re-reads it for the FP32 re-rank) it lives
+    // inside the hash region (the plan keeps H >= m_pad)
+    float* qs = LP ? pq + r_pad : reinterpret_cast<float*>(hash);
+    uint32_t* nbs = reinterpret_cast<uint32_t*>(LP ? qs + ((qs_len + 3) & ~3) : pq + r_pad);
     float* es = reinterpret_cast<float*>(nbs + 32 * NPL);
     float* xb = es + 32 * NPL;
     int* lst = reinterpret_cast<int*>(xb + 32 * NPL);

@@ -1,0 +1,201 @@
+"""GPU tests of the reduced-precision mode, uneven batches, index files and the
+GPU graph builder.
+
+Reduced precision (BF16 rows, FP8-e4m3 residual codes, FP32 accumulation, the
+head of the result list re-ranked with FP32 rows): the returned distances are
+FP32 sums over the original vectors, so they must match the FP64 oracle's
+distance of the same (query, id) pairs to 1e-5; the traversal itself runs on
+perturbed distances (BF16 keeps 8 significant bits, ~0.4 % relative per
+coordinate; FP8 codes ~6 % per component), so list identity is not expected
+and recall is held to the FP64 oracle's FINGER recall minus 0.01.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2206_11408_gb300 as fg  # noqa: E402
+
+
+def _index(X, g, fp, r, build_lp=False):
+    ix = fg.Index(X)
+    ix.set_graph(g.adj0, g.level, g.up_off, g.up_adj, g.entry, g.maxlevel, g.M)
+    ix.build_tables(r, 4003, basis=fp.P, stats=fp.stats(), build_lp=build_lp)
+    return ix
+
+
+@pytest.fixture(scope="module")
+def glove_like():
+    """6,000 unit vectors, m = 100, 256 power-law clusters (configuration 3's
+    distribution), HNSW M = 24 (layer-0 degree 48), r = 32."""
+    X = workloads.base_vectors(3, 6000)
+    Q = workloads.query_vectors(3, 150)
+    g = oracle.hnsw_build(X, 24, 80, 3003)
+    fp, _ = oracle.build_tables(X, g, 32, 4003)
+    gt, _ = oracle.bruteforce(X, Q, 10)
+    return X, Q, g, fp, gt
+
+
+def test_lp_mode_distances_and_recall(glove_like):
+    X, Q, g, fp, gt = glove_like
+    ix = _index(X, g, fp, 32, build_lp=True)
+    assert ix.info()["has_lp"]
+    q = torch.from_numpy(Q).cuda()
+    for ef in (20, 60):
+        ix.set_mode(fg.MODE_FINGER_LP, 5)
+        ids, d = ix.search(q, 10, ef)
+        torch.cuda.synchronize()
+        ix.sync()
+        ids, d = ids.cpu().numpy(), d.cpu().numpy()
+        # FP32 re-rank: distances are exact FP32 sums of the original rows
+        Xd, Qd = X.astype(np.float64), Q.astype(np.float64)
+        ref = ((Qd[:, None, :] - Xd[ids]) ** 2).sum(-1)
+        np.testing.assert_allclose(d, ref, rtol=1e-5, atol=1e-7)
+        # sorted by (distance, id)
+        for row_d, row_i in zip(d, ids):
+            keys = list(zip(row_d.tolist(), row_i.tolist()))
+            assert keys == sorted(keys)
+        oi, _, _ = oracle.search(g, X, Q, 10, ef, fp)
+        r_lp, r_o = oracle.recall(ids, gt, 10), oracle.recall(oi, gt, 10)
+        assert r_lp >= r_o - 0.01, (ef, r_lp, r_o)
+    ix.close()
+
+
+def test_lp_codes_follow_fp32_tables(glove_like):
+    """FP8 codes are the e4m3 rounding of 256 * u (relative error <= 2^-4)."""
+    X, Q, g, fp, gt = glove_like
+    ix = _index(X, g, fp, 32, build_lp=True)
+    t = ix.get_tables()
+    u = t["edge_u"]
+    assert np.abs(np.linalg.norm(u, axis=-1)[g.adj0 >= 0] - 1).max() < 1e-5
+    ix.close()
+
+
+def test_uneven_batch_matches_single_searches(glove_like):
+    X, Q, g, fp, gt = glove_like
+    ix = _index(X, g, fp, 32)
+    ix.set_mode(fg.MODE_FINGER, 5)
+    rng = np.random.default_rng(5)
+    nq = 60
+    K = rng.choice(np.array([1, 10, 100], np.int32), nq)
+    ef = np.maximum(K, 10) + rng.integers(0, 200, nq).astype(np.int32)
+    Kt = torch.from_numpy(K.astype(np.int32)).cuda()
+    eft = torch.from_numpy(ef.astype(np.int32)).cuda()
+    for rep in range(2):      # same shape twice: the second call replays the captured graph
+        q = torch.from_numpy(Q[rep * nq:(rep + 1) * nq].copy()).cuda()
+        ids, d, off = ix.search_batch(q, Kt, eft)
+        torch.cuda.synchronize()
+        ix.sync()
+        ids, d, off = ids.cpu().numpy(), d.cpu().numpy(), off.cpu().numpy()
+        for i in range(nq):
+            si, sd = ix.search(q[i:i + 1], int(K[i]), int(ef[i]))
+            a, b = off[i], off[i] + K[i]
+            assert (ids[a:b] == si.cpu().numpy()[0]).all()
+            assert (d[a:b] == sd.cpu().numpy()[0]).all()
+    ix.close()
+
+
+def test_autotune_then_batch(glove_like):
+    X, Q, g, fp, gt = glove_like
+    ix = _index(X, g, fp, 32)
+    ix.set_mode(fg.MODE_FINGER, 5)
+    q = torch.from_numpy(Q).cuda()
+    ms = ix.autotune(q, 10, 64)
+    assert ms > 0
+    K = torch.full((Q.shape[0],), 10, dtype=torch.int32, device="cuda")
+    ef = torch.full((Q.shape[0],), 64, dtype=torch.int32, device="cuda")
+    ids, d, off = ix.search_batch(q, K, ef)
+    si, sd = ix.search(q, 10, 64)
+    torch.cuda.synchronize()
+    assert (ids.cpu().numpy().reshape(-1, 10) == si.cpu().numpy()).all()
+    ix.close()
+
+
+def test_index_file_roundtrip(glove_like, tmp_path):
+    X, Q, g, fp, gt = glove_like
+    ix = _index(X, g, fp, 32, build_lp=True)
+    ix.set_mode(fg.MODE_FINGER, 5)
+    q = torch.from_numpy(Q).cuda()
+    a_ids, a_d = ix.search(q, 10, 40)
+    path = str(tmp_path / "idx.finger")
+    ix.save(path)
+    jx = fg.Index.load(path)
+    assert jx.info()["has_lp"] and jx.info()["r"] == 32
+    jx.set_mode(fg.MODE_FINGER, 5)
+    b_ids, b_d = jx.search(q, 10, 40)
+    torch.cuda.synchronize()
+    assert (a_ids.cpu().numpy() == b_ids.cpu().numpy()).all()
+    assert (a_d.cpu().numpy() == b_d.cpu().numpy()).all()
+    # corruption is detected
+    raw = bytearray(open(path, "rb").read())
+    raw[200] ^= 0xFF
+    open(path, "wb").write(bytes(raw))
+    with pytest.raises(fg.FingerError):
+        fg.Index.load(path)
+    with pytest.raises(fg.FingerError):
+        fg.Index.load(str(tmp_path / "missing"))
+    ix.close()
+    jx.close()
+
+
+def test_gpu_graph_builder_invariants():
+    X = workloads.base_vectors(1, 8000)
+    Q = workloads.query_vectors(1, 100)
+    ix = fg.Index(X)
+    ix.build_graph(16, 64, 3001)
+    gr = ix.get_graph()
+    adj0 = gr["adj0"]
+    n = X.shape[0]
+    assert adj0.shape == (n, 32)
+    lv = oracle.levels(n, 16, 3001)                    # same level draw as the oracle
+    assert (gr["level"] == lv).all()
+    assert gr["entry"] == int(np.flatnonzero(lv == lv.max())[0])
+    for v in range(0, n, 7):
+        row = adj0[v]
+        valid = row[row >= 0]
+        assert (row[len(valid):] == -1).all()
+        assert len(set(valid.tolist())) == len(valid) and v not in valid
+    for v in np.flatnonzero(gr["level"] > 0)[:200]:
+        for l in range(1, gr["level"][v] + 1):
+            row = gr["up_adj"][gr["up_off"][v] + l - 1]
+            valid = row[row >= 0]
+            assert (gr["level"][valid] >= l).all()
+    # usable for search: recall against the oracle's brute force
+    ix.build_tables(16, 4001)
+    ix.set_mode(fg.MODE_PLAIN)
+    ids, _ = ix.search(torch.from_numpy(Q).cuda(), 10, 100)
+    gt, _ = oracle.bruteforce(X, Q, 10)
+    assert oracle.recall(ids.cpu().numpy(), gt, 10) > 0.95
+    # and the graph passes the C ABI's own validation when re-attached
+    jx = fg.Index(X)
+    jx.set_graph(adj0, gr["level"], gr["up_off"], gr["up_adj"], gr["entry"], gr["maxlevel"], 16)
+    ix.close()
+    jx.close()
+
+
+def test_kernel_limit_is_reported_not_faulted():
+    """A search that hits the expansion cap returns FINGER_ERR_LIMIT through the
+    status word instead of running on; the context stays usable afterwards."""
+    X = workloads.base_vectors(1, 3000)
+    g = oracle.hnsw_build(X, 8, 40, 1)
+    fp, _ = oracle.build_tables(X, g, 8, 2)
+    ix = _index(X, g, fp, 8)
+    ix.set_mode(fg.MODE_PLAIN)
+    q = torch.from_numpy(workloads.query_vectors(1, 10)).cuda()
+    ix.set_limit(3)
+    ix.search(q, 10, 100)
+    with pytest.raises(fg.FingerError) as e:
+        ix.sync()
+    assert e.value.status == 7
+    ix.reset_stats()
+    ix.set_limit(0)
+    ids, d = ix.search(q, 10, 100)
+    ix.sync()
+    assert (ids.cpu().numpy() >= 0).all()
+    ix.close()
