@@ -86,7 +86,8 @@ typedef struct {
 
 /* Build an HNSW-style graph on the device: levels drawn as in HNSW from a
  * counter-based generator, then for every level the exact k nearest neighbours
- * among that level's nodes (brute force on the GPU), heuristic neighbour
+ * among that level's nodes (brute force on the GPU; k = `candidates` on layer 0,
+ * up to 256 on the upper layers), heuristic neighbour
  * selection (keep a candidate only if it is closer to the node than to every
  * neighbour kept so far, as in HNSW), reverse edges, and a second heuristic
  * pass to the degree cap.  Synchronous (returns when the graph is built). */

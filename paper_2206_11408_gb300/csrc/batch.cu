@@ -112,7 +112,7 @@ finger_status finger_search_batch(finger_index* ix, const float* queries, int64_
             cudaGetLastError();
             ret = FINGER_ERR_CUDA;
         } else {
-            bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+            bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed) == cudaSuccess;
             ok = ok && cudaMemsetAsync(ix->work, 0, sizeof(uint32_t), cs) == cudaSuccess;
             ok = ok && launch_search(d, a, p, cs) == cudaSuccess;
             ok = (cudaStreamEndCapture(cs, &graph) == cudaSuccess) && ok;

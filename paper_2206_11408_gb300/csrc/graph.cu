@@ -5,7 +5,7 @@
 // the counter-based generator splitmix64(seed ^ v).  For every level l the
 // nodes with level >= l form a layer; its edges come from
 //   1. the exact `candidates` nearest neighbours among the layer's nodes
-//      (brute force, knn.cu);
+//      (brute force, knn.cu; up to 256 on the small upper layers);
 //   2. the HNSW neighbour-selection heuristic over those candidates, sorted by
 //      (distance, id): keep a candidate only if it is strictly closer to the
 //      node than to every neighbour kept so far, up to M forward links;
@@ -403,8 +403,10 @@ finger_status build_graph(finger_index* ix, const finger_graph_params* p, cudaSt
             CK(cudaMemcpy(d_nodes, nodes.data(), sizeof(int32_t) * cnt, cudaMemcpyHostToDevice));
             CK(cudaMemcpy(d_rows, orow.data(), sizeof(int64_t) * cnt, cudaMemcpyHostToDevice));
             CK(cudaMemcpy(d_cmap, cmap.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice));
-            status = build_layer(ix, d_nodes, cnt, std::min(kc, 2 * M), M, M, up_adj, M, d_rows,
-                                 d_cmap, s);
+            // upper layers are small: offer up to 256 exact candidates so that the
+            // selection sees beyond a node's own cluster and keeps long links
+            status = build_layer(ix, d_nodes, cnt, (int)std::min<int64_t>(cnt - 1, 256), M, M,
+                                 up_adj, M, d_rows, d_cmap, s);
             if (status != FINGER_OK) goto done;
         }
     }
