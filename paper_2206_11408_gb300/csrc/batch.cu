@@ -34,6 +34,7 @@ int bucket_of(int ef) {
 }
 
 struct Captured {
+    cudaGraph_t graph = nullptr;        // kept: its kernel node is updated per call
     cudaGraphExec_t exec = nullptr;
     cudaGraphNode_t knode = nullptr;
     cudaKernelNodeParams kp{};
@@ -49,8 +50,10 @@ std::map<const finger_index*, std::map<std::pair<int64_t, int>, Captured>>& capt
 void fg_drop_captures(const finger_index* ix) {
     auto it = captures().find(ix);
     if (it == captures().end()) return;
-    for (auto& kv : it->second)
+    for (auto& kv : it->second) {
         if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+        if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
+    }
     captures().erase(it);
 }
 
@@ -131,12 +134,14 @@ finger_status finger_search_batch(finger_index* ix, const float* queries, int64_
                 }
                 ok = c.knode && cudaGraphInstantiate(&c.exec, graph, 0) == cudaSuccess;
             }
-            if (graph) cudaGraphDestroy(graph);
             cudaStreamDestroy(cs);
             if (!ok) {
+                if (c.exec) cudaGraphExecDestroy(c.exec);
+                if (graph) cudaGraphDestroy(graph);
                 cudaGetLastError();
                 ret = FINGER_ERR_CUDA;
             } else {
+                c.graph = graph;
                 it = caps.emplace(key, c).first;
             }
         }
