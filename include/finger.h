@@ -180,6 +180,22 @@ finger_status finger_search_host(finger_index* ix, const float* queries_host, in
                                  int ef, int64_t* out_ids_host, float* out_dists_host,
                                  void* stream);
 
+/* finger_search without any device-memory allocation during the call.  The
+ * paper has no counterpart; this exists for callers that must not allocate on
+ * the query path (processes that reserve their device-memory budget at
+ * start-up, loops where cudaMalloc/cudaFree latency or synchronisation is not
+ * acceptable).  Same arguments, modes and results as finger_search; the
+ * visited-set scratch comes from one fixed 64 MiB device array that the
+ * library reserves on every device that loads it, shared by all calls: calls
+ * whose kernels overlap on the GPU race on it and must be serialised.  The
+ * first call on a device looks up the array's device address and caches it;
+ * make that first call before any stream capture.  A launch uses as many
+ * resident warps as the array holds (ceil(n/32) bitmap words + up to 16384
+ * spill ids per warp); if not even one fits (n above roughly 5e8) the call
+ * returns FINGER_ERR_UNSUPPORTED.  Asynchronous on `stream`. */
+finger_status finger_search_noalloc(finger_index* ix, const float* queries, int64_t nq, int K,
+                                    int ef, int64_t* out_ids, float* out_dists, void* stream);
+
 /* Uneven batch: per-query K[i] and ef[i] (device int32 arrays, K[i] <= ef[i]),
  * results of query i at out_ids[out_off[i] .. out_off[i] + K[i]) (device
  * int64 offsets).  One persistent launch sized for max ef; replayed from a

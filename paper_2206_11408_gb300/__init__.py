@@ -79,6 +79,7 @@ SIGNATURES = {
     "finger_set_mode": (_I, [_P, _I, _I]),
     "finger_search": (_I, [_P, _P, _I64, _I, _I, _P, _P, _P]),
     "finger_search_host": (_I, [_P, _P, _I64, _I, _I, _P, _P, _P]),
+    "finger_search_noalloc": (_I, [_P, _P, _I64, _I, _I, _P, _P, _P]),
     "finger_search_batch": (_I, [_P, _P, _I64, _P, _P, _I, _P, _P, _P, _P]),
     "finger_autotune": (_I, [_P, _P, _I64, _I, _I, _P, _P, _P, _P]),
     "finger_set_counters": (_I, [_P, _P]),
@@ -270,6 +271,19 @@ class Index:
                                        ef, _dev_ptr(out_ids, torch.int64, "out_ids"),
                                        _dev_ptr(out_dists, torch.float32, "out_dists"),
                                        _stream_ptr(stream)), "finger_search")
+        return out_ids, out_dists
+
+    def search_noalloc(self, queries, K: int, ef: int, out_ids, out_dists, stream=None):
+        """finger_search_noalloc: same results as search(), scratch taken from the
+        library's fixed device array, no allocation in the call (the caller passes
+        preallocated output tensors)."""
+        import torch
+        nq = queries.shape[0]
+        _check(self._lib.finger_search_noalloc(
+            self._h, _dev_ptr(queries, torch.float32, "queries"), nq, K, ef,
+            _dev_ptr(out_ids, torch.int64, "out_ids"),
+            _dev_ptr(out_dists, torch.float32, "out_dists"), _stream_ptr(stream)),
+            "finger_search_noalloc")
         return out_ids, out_dists
 
     def search_host(self, queries: np.ndarray, K: int, ef: int, out_ids=None, out_dists=None,
