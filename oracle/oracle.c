@@ -310,6 +310,42 @@ typedef struct {
     int expanded;
 } tent_t;
 
+/* round to the nearest bfloat16 (ties to even) through FP32 */
+static double bf16r(double x) {
+    float f = (float)x;
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    u = (u + 0x7FFFu + ((u >> 16) & 1u)) & 0xFFFF0000u;
+    memcpy(&f, &u, 4);
+    return (double)f;
+}
+
+/* learned angle predictor r+4 -> 64 -> 64 -> 1 (weights already BF16/FP32
+ * valued; W1 64 x nf, b1, W2 64 x 64, b2, w3, b3), hidden-layer inputs rounded
+ * to BF16 as a tensor-core operand would be */
+static double mlp_predict(const double* w, int nf, const double* f) {
+    const double* W1 = w;
+    const double* b1 = W1 + 64 * nf;
+    const double* W2 = b1 + 64;
+    const double* b2 = W2 + 64 * 64;
+    const double* w3 = b2 + 64;
+    double b3 = w3[64];
+    double x[80], h1[64];
+    for (int i = 0; i < nf; ++i) x[i] = bf16r(f[i]);
+    for (int j = 0; j < 64; ++j) {
+        double z = b1[j];
+        for (int i = 0; i < nf; ++i) z += W1[j * nf + i] * x[i];
+        h1[j] = bf16r(z > 0 ? z : 0.0);
+    }
+    double y = b3;
+    for (int j = 0; j < 64; ++j) {
+        double z = b2[j];
+        for (int i = 0; i < 64; ++i) z += W2[j * 64 + i] * h1[i];
+        y += w3[j] * (z > 0 ? z : 0.0);
+    }
+    return y;
+}
+
 /* Algorithm 3 for one neighbour d of centre c, given the per-centre parts
  * q_proj, q_res (Eq. 1), ||q_res||^2 and P q_res.  Returns the distance
  * estimate of Eq. (2) with q_res^T d_res replaced by ||q_res|| ||d_res|| t,
@@ -317,7 +353,7 @@ typedef struct {
 static double appx_dist(const double* xc, const double* xd, int m, double cc, const double* q_proj,
                         const double* q_res, double qres_n2, const double* Pq, const double* P,
                         int r, const double* st, double* d_proj, double* d_res, double* diff,
-                        double* Pd) {
+                        double* Pd, const double* q, const double* mlp, double mlp_eps) {
     double mu = st[0], sigma = st[1], muh = st[2], sigmah = st[3], eps = st[4];
     double ratio = sigmah > 0 ? sigma / sigmah : 0.0;
     double b = cc > 0 ? dot(xc, xd, m) / cc : 0.0;
@@ -332,6 +368,20 @@ static double appx_dist(const double* xc, const double* xd, int m, double cc, co
     double that = (nq_ > 0 && nd_ > 0) ? dot(Pq, Pd, r) / (nq_ * nd_) : 0.0;
     double t = (that - muh) * ratio + mu;
     t = t + eps;
+    if (mlp) {
+        /* learned predictor in place of distribution matching (extension) */
+        double f[80];
+        double a = cc > 0 ? dot(xc, q, m) / cc : 0.0;
+        for (int k = 0; k < r; ++k)
+            f[k] = (nq_ > 0 && nd_ > 0) ? (Pq[k] / nq_) * (Pd[k] / nd_) : 0.0;
+        double nqn = sqrt(dot(q, q, m)), ndn = sqrt(dot(xd, xd, m));
+        f[r] = that;
+        f[r + 1] = nqn > 0 ? sqrt(qres_n2) / nqn : 0.0;
+        f[r + 2] = ndn > 0 ? sqrt(dres_n2) / ndn : 0.0;
+        f[r + 3] = a / (fabs(a) + fabs(b) + 1e-6);
+        double y = mlp_predict(mlp, r + 4, f);
+        if (isfinite(y)) t = y + mlp_eps;
+    }
     (void)q_res;
     return dot(diff, diff, m) + qres_n2 + dres_n2 - 2.0 * sqrt(qres_n2) * sqrt(dres_n2) * t;
 }
@@ -364,7 +414,7 @@ double orc_estimate(const double* q, const double* xc, const double* xd, int m, 
     double qres_n2;
     double cc = centre_parts(xc, q, m, P, r, q_proj, q_res, &qres_n2, Pq);
     double e = appx_dist(xc, xd, m, cc, q_proj, q_res, qres_n2, Pq, P, r, stats, d_proj, d_res,
-                         diff, Pd);
+                         diff, Pd, q, NULL, 0.0);
     free(w);
     return e;
 }
@@ -375,7 +425,8 @@ static void search_one(const double* X, int m, const int32_t* adj0, int deg0, co
                        const int32_t* up_adj, int Mup, int entry, int maxlevel, const double* q,
                        int K, int ef, const double* P, int r, const double* st, int warmup,
                        int finger, int64_t* out_ids, double* out_d, int64_t* cnt, char* visited,
-                       int32_t* touched, tent_t* T, double* work) {
+                       int32_t* touched, tent_t* T, double* work, const double* mlp,
+                       double mlp_eps) {
     for (int i = 0; i < CNT_N; ++i) cnt[i] = 0;
     /* ---- upper layers: greedy descent (search-layer with ef = 1) */
     int32_t cur = entry;
@@ -443,7 +494,7 @@ static void search_one(const double* X, int m, const int32_t* adj0, int deg0, co
             int full = tlen == ef;
             if (use_est && full) {
                 double est = appx_dist(xc, xd, m, cc, q_proj, q_res, qres_n2, Pq, P, r, st,
-                                       d_proj, d_res, diff, Pd);
+                                       d_proj, d_res, diff, Pd, q, mlp, mlp_eps);
                 cnt[CNT_ESTIMATES]++;
                 double ub = T[tlen - 1].kv.d;
                 if (est > ub) {
@@ -478,7 +529,7 @@ int orc_search(const double* X, int64_t n, int m, const int32_t* adj0, int deg0,
                const int64_t* up_off, const int32_t* up_adj, int Mup, int entry, int maxlevel,
                const double* Q, int64_t nq, int K, int ef, const double* P, int r,
                const double* stats, int warmup, int finger, int64_t* ids, double* dists,
-               int64_t* counters, int nthreads) {
+               int64_t* counters, int nthreads, const double* mlp, double mlp_eps) {
     if (ef < 1 || K < 1) return -1;
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
@@ -496,7 +547,8 @@ int orc_search(const double* X, int64_t n, int m, const int32_t* adj0, int deg0,
         for (int64_t qi = 0; qi < nq; ++qi) {
             search_one(X, m, adj0, deg0, up_off, up_adj, Mup, entry, maxlevel, Q + (size_t)qi * m,
                        K, ef, P, r, stats, warmup, finger, ids + qi * K, dists + qi * K,
-                       counters ? counters + qi * CNT_N : cnt_local, visited, touched, T, work);
+                       counters ? counters + qi * CNT_N : cnt_local, visited, touched, T, work,
+                       mlp, mlp_eps);
         }
         free(visited);
         free(touched);

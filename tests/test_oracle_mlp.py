@@ -1,0 +1,100 @@
+"""Pins of the oracle's learned angle predictor (an extension; the paper has no
+learned predictor): BF16 rounding against the IEEE definition and torch's
+conversion, analytic gradients against central finite differences, the
+features against their defining identities, and the predictor hook of the
+oracle search against predictors whose effect is known in closed form."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from oracle import mlp
+
+
+def test_bf16_round_to_nearest_even():
+    # spacing of bfloat16 at 1.0 is 2^-7
+    assert mlp.bf16(1.0) == 1.0
+    assert mlp.bf16(1 + 2 ** -8) == 1.0                       # tie -> even mantissa
+    assert mlp.bf16(1 + 3 * 2 ** -8) == 1 + 2 ** -6           # tie -> even mantissa
+    assert mlp.bf16(1 + 2 ** -8 + 2 ** -20) == 1 + 2 ** -7    # above the tie
+    assert mlp.bf16(-2.5) == -2.5 and mlp.bf16(0.0) == 0.0
+    torch = pytest.importorskip("torch")
+    x = np.random.default_rng(0).standard_normal(10000) * 10.0 ** np.random.default_rng(1).uniform(-6, 6, 10000)
+    ref = torch.tensor(x, dtype=torch.float32).to(torch.bfloat16).to(torch.float64).numpy()
+    np.testing.assert_array_equal(mlp.bf16(x), ref)
+
+
+def test_gradient_matches_finite_differences():
+    rng = np.random.default_rng(2)
+    nf = 12
+    w = mlp.init(nf, 3) + rng.normal(0, 0.05, mlp.n_weights(nf))
+    w[mlp.H * nf:mlp.H * nf + mlp.H] = rng.normal(0, 0.5, mlp.H)     # non-zero b1
+    X = rng.standard_normal((40, nf))
+    t = rng.standard_normal(40)
+    loss, g = mlp.loss_and_grad(w, X, t, nf, round_act=False)
+    idx = rng.choice(len(w), 120, replace=False)
+    h = 1e-6
+    for i in idx:
+        wp, wm = w.copy(), w.copy()
+        wp[i] += h
+        wm[i] -= h
+        fd = (mlp.loss_and_grad(wp, X, t, nf, False)[0] - mlp.loss_and_grad(wm, X, t, nf, False)[0]) / (2 * h)
+        assert fd == pytest.approx(g[i], rel=1e-5, abs=1e-9)
+
+
+def test_features_identities():
+    rng = np.random.default_rng(4)
+    m, r = 16, 5
+    P = np.linalg.qr(rng.standard_normal((m, m)))[0][:r]
+    for _ in range(20):
+        q, c, d = rng.standard_normal((3, m))
+        f, target = mlp.features(q, c, d, P)
+        assert f[:r].sum() == pytest.approx(f[r], abs=1e-12)      # sum of products = t_hat
+        cc = c @ c
+        qr, dr = q - (c @ q) / cc * c, d - (c @ d) / cc * c
+        assert target == pytest.approx(qr @ dr / np.linalg.norm(qr) / np.linalg.norm(dr))
+        assert f[r + 1] == pytest.approx(np.linalg.norm(qr) / np.linalg.norm(q))
+    # full rank: cos(P q_res, P d_res) = cos(q_res, d_res), i.e. t_hat = target
+    Pf = np.linalg.qr(rng.standard_normal((m, m)))[0]
+    f, target = mlp.features(q, c, d, Pf)
+    assert f[m] == pytest.approx(target, abs=1e-12)
+
+
+@pytest.fixture(scope="module")
+def small():
+    X = workloads.base_vectors(4, 2000)
+    Q = workloads.query_vectors(4, 40)
+    g = oracle.hnsw_build(X, 8, 60, 3004)
+    fp, _ = oracle.build_tables(X, g, 8, 4004)
+    return X, Q, g, fp
+
+
+def _const_predictor(nf, value):
+    w = np.zeros(mlp.n_weights(nf))
+    w[-1] = value                           # b3: the output is this constant
+    return w
+
+
+def test_predictor_hook_large_cosine_is_no_skip(small):
+    """A predictor that always says cos = +1e6 makes every estimate -inf-like:
+    nothing is skipped and the search is Algorithm 1."""
+    X, Q, g, fp = small
+    nf = fp.P.shape[0] + 4
+    i1, d1, c1 = oracle.search(g, X, Q, 10, 30)
+    i2, d2, c2 = oracle.search(g, X, Q, 10, 30, fp, mlp_weights=_const_predictor(nf, 1e6))
+    assert (i1 == i2).all() and (d1 == d2).all()
+    assert c2[:, 3].sum() == 0 and c2[:, 2].sum() > 0
+
+
+def test_predictor_hook_constant_equals_matching(small):
+    """A constant predictor c0 with eps' = e0 gives t = c0 + e0, the same t as
+    distribution matching with sigma = 0, mu = c0, eps = e0."""
+    X, Q, g, fp = small
+    nf = fp.P.shape[0] + 4
+    c0, e0 = -0.5, 0.05
+    flat = oracle.FingerParams(fp.P, c0, 0.0, 0.0, 1.0, e0)
+    i1, d1, c1 = oracle.search(g, X, Q, 10, 30, flat)
+    i2, d2, c2 = oracle.search(g, X, Q, 10, 30, fp, mlp_weights=_const_predictor(nf, c0),
+                               mlp_eps=e0)
+    assert (i1 == i2).all() and (c1 == c2).all()
+    assert c1[:, 3].sum() > 0
