@@ -225,6 +225,66 @@ finger_status finger_set_limit(finger_index* ix, int max_expansions);
  * are written when `counters` is set here (NULL disables). */
 finger_status finger_set_counters(finger_index* ix, int32_t* counters_device);
 
+/* ------------------------------------ learned angle predictor (extension)
+ * The paper matches the low-rank cosine's distribution to the true one
+ * (Sec. 3.3).  This extension replaces that step by a small MLP trained on
+ * (q, c, d) triples harvested from FINGER's own traversals: inputs are the
+ * r + 4 features [u_q * u_d (r values), t_hat, ||q_res||/||q||,
+ * ||d_res||/||d||, a/(|a|+|b|+1e-6)] (u = unit P-projected residuals,
+ * a = c^T q / c^T c, b = c^T d / c^T c), target cos(q_res, d_res); network
+ * r+4 -> 64 -> 64 -> 1 with ReLU, BF16 weights, FP32 accumulation, the inputs
+ * of both hidden layers rounded to BF16.  Flat FP32 weight order: W1 (64 x
+ * (r+4), row = hidden unit), b1 (64), W2 (64 x 64), b2 (64), w3 (64), b3.
+ * In FINGER_MODE_FINGER_MLP the estimate uses t = prediction + eps', eps' the
+ * mean absolute error on held-out triples; a non-finite prediction falls back
+ * to the distribution-matched t. */
+
+/* number of floats of the flat predictor for rank r (64 (r+4) + 64 + 4096 + 64 + 64 + 1) */
+int64_t finger_mlp_size(int r);
+
+/* Run FINGER searches (mode FINGER semantics, warm-up as set) over nq device
+ * queries with the given ef and record, for every estimate made while the
+ * result list is full, the features (cap x (r+4) FP32, device), the target
+ * cos(q_res, d_res) computed from the exact distance (cap FP32, device) and the
+ * triple (query index, centre id, neighbour id) (cap x 3 int32, device).
+ * *count (host) receives the number of records written (<= cap). Synchronous. */
+finger_status finger_harvest(finger_index* ix, const float* queries, int64_t nq, int ef,
+                             int64_t cap, float* feat, float* target, int32_t* triples,
+                             int64_t* count, void* stream);
+
+typedef struct {
+    const float* feat;     /* device, (n_train + n_val) x (r + 4) */
+    const float* target;   /* device, n_train + n_val */
+    int64_t n_train;       /* first n_train rows train, the next n_val give eps' */
+    int64_t n_val;
+    int epochs;
+    int batch;             /* rows per Adam step */
+    float lr;
+    uint64_t seed;         /* weight initialisation and shuffling */
+} finger_train_params;
+
+/* Train the predictor on the device (hand-written forward, backward and Adam
+ * kernels; MSE loss) and install it in the index.  losses (host, may be NULL)
+ * receives the mean training loss of each epoch.  Synchronous. */
+finger_status finger_train_predictor(finger_index* ix, const finger_train_params* p,
+                                     float* losses, void* stream);
+
+/* Install / read a predictor as flat FP32 weights (host) with its eps'. */
+finger_status finger_set_predictor(finger_index* ix, const float* weights, int64_t count,
+                                   float eps);
+finger_status finger_get_predictor(const finger_index* ix, float* weights, float* eps);
+
+/* Mean squared error and its gradient (host, finger_mlp_size floats) of the
+ * predictor with the given flat weights (host, nf = r + 4 inputs) on n device
+ * rows, computed by the training kernels (gradient checks). Synchronous. */
+finger_status finger_mlp_loss_grad(finger_index* ix, int nf, const float* weights,
+                                   const float* feat, const float* target, int64_t n, float* grad,
+                                   double* loss, void* stream);
+
+/* Predictions of the installed predictor for n device feature rows. */
+finger_status finger_mlp_predict(finger_index* ix, const float* feat, int64_t n, float* out,
+                                 void* stream);
+
 /* ------------------------------------------------------- ground truth */
 
 /* Exact K nearest neighbours of nq queries (device, nq x m) over all n base

@@ -46,6 +46,12 @@ class BuildParams(ctypes.Structure):
                 ("build_lp", ctypes.c_int)]
 
 
+class TrainParams(ctypes.Structure):
+    _fields_ = [("feat", ctypes.c_void_p), ("target", ctypes.c_void_p),
+                ("n_train", ctypes.c_int64), ("n_val", ctypes.c_int64), ("epochs", ctypes.c_int),
+                ("batch", ctypes.c_int), ("lr", ctypes.c_float), ("seed", ctypes.c_uint64)]
+
+
 class Info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("m", ctypes.c_int), ("deg0", ctypes.c_int),
                 ("M", ctypes.c_int), ("maxlevel", ctypes.c_int), ("entry", ctypes.c_int),
@@ -89,6 +95,13 @@ SIGNATURES = {
     "finger_get_stats": (_I, [_P, _P]),
     "finger_reset_stats": (_I, [_P]),
     "finger_status_str": (ctypes.c_char_p, [_I]),
+    "finger_mlp_size": (_I64, [_I]),
+    "finger_harvest": (_I, [_P, _P, _I64, _I, _I64, _P, _P, _P, _P, _P]),
+    "finger_train_predictor": (_I, [_P, _P, _P, _P]),
+    "finger_set_predictor": (_I, [_P, _P, _I64, _F]),
+    "finger_get_predictor": (_I, [_P, _P, _P]),
+    "finger_mlp_loss_grad": (_I, [_P, _I, _P, _P, _P, _I64, _P, _P, _P]),
+    "finger_mlp_predict": (_I, [_P, _P, _I64, _P, _P]),
 }
 
 
@@ -341,6 +354,71 @@ class Index:
                                     _dev_ptr(d, torch.float32, "dists"), _stream_ptr(stream)),
                "finger_knn")
         return ids, d
+
+    # ------------------------------------------ learned predictor (extension)
+    def mlp_size(self) -> int:
+        return int(self._lib.finger_mlp_size(self.info()["r"]))
+
+    def harvest(self, queries, ef: int, cap: int, stream=None):
+        """Training triples from FINGER traversals: (features, targets, triples)
+        as CUDA tensors trimmed to the number of records."""
+        import torch
+        nf = self.info()["r"] + 4
+        feat = torch.empty((cap, nf), dtype=torch.float32, device=queries.device)
+        tgt = torch.empty(cap, dtype=torch.float32, device=queries.device)
+        trip = torch.empty((cap, 3), dtype=torch.int32, device=queries.device)
+        cnt = ctypes.c_int64()
+        _check(self._lib.finger_harvest(self._h, _dev_ptr(queries, torch.float32, "queries"),
+                                        queries.shape[0], ef, cap, _dev_ptr(feat, torch.float32, "feat"),
+                                        _dev_ptr(tgt, torch.float32, "target"),
+                                        _dev_ptr(trip, torch.int32, "triples"), ctypes.byref(cnt),
+                                        _stream_ptr(stream)), "finger_harvest")
+        n = cnt.value
+        return feat[:n], tgt[:n], trip[:n]
+
+    def train_predictor(self, feat, target, n_val: int, epochs: int = 8, batch: int = 4096,
+                        lr: float = 2e-3, seed: int = 5004, stream=None):
+        import torch
+        n = feat.shape[0]
+        p = TrainParams(_dev_ptr(feat, torch.float32, "feat").value,
+                        _dev_ptr(target, torch.float32, "target").value, n - n_val, n_val,
+                        epochs, batch, lr, seed)
+        losses = np.zeros(epochs, np.float32)
+        _check(self._lib.finger_train_predictor(self._h, ctypes.byref(p), _np_ptr(losses),
+                                                _stream_ptr(stream)), "finger_train_predictor")
+        return losses
+
+    def set_predictor(self, weights: np.ndarray, eps: float):
+        w = np.ascontiguousarray(weights, dtype=np.float32)
+        _check(self._lib.finger_set_predictor(self._h, _np_ptr(w), w.size, eps),
+               "finger_set_predictor")
+
+    def get_predictor(self):
+        w = np.empty(self.mlp_size(), np.float32)
+        eps = ctypes.c_float()
+        _check(self._lib.finger_get_predictor(self._h, _np_ptr(w), ctypes.byref(eps)),
+               "finger_get_predictor")
+        return w, eps.value
+
+    def mlp_loss_grad(self, weights: np.ndarray, feat, target, stream=None):
+        import torch
+        w = np.ascontiguousarray(weights, dtype=np.float32)
+        g = np.empty_like(w)
+        loss = ctypes.c_double()
+        _check(self._lib.finger_mlp_loss_grad(self._h, feat.shape[1], _np_ptr(w),
+                                              _dev_ptr(feat, torch.float32, "feat"),
+                                              _dev_ptr(target, torch.float32, "target"),
+                                              feat.shape[0], _np_ptr(g), ctypes.byref(loss),
+                                              _stream_ptr(stream)), "finger_mlp_loss_grad")
+        return loss.value, g
+
+    def mlp_predict(self, feat, stream=None):
+        import torch
+        out = torch.empty(feat.shape[0], dtype=torch.float32, device=feat.device)
+        _check(self._lib.finger_mlp_predict(self._h, _dev_ptr(feat, torch.float32, "feat"),
+                                            feat.shape[0], _dev_ptr(out, torch.float32, "out"),
+                                            _stream_ptr(stream)), "finger_mlp_predict")
+        return out
 
     # -------------------------------------------------------------- status
     def sync(self):

@@ -19,6 +19,8 @@ cudaError_t occupancy_mode0(const SearchPlan&, int*);
 cudaError_t occupancy_mode1(const SearchPlan&, int*);
 cudaError_t occupancy_mode2(const SearchPlan&, int*);
 cudaError_t occupancy_mode3(const SearchPlan&, int*);
+cudaError_t launch_mode4(const DevIndex&, const SearchArgs&, const SearchPlan&, cudaStream_t);
+cudaError_t occupancy_mode4(const SearchPlan&, int*);
 
 void choose_groups(int nchunks, int* G, int* VPL) {
     if (nchunks <= 8) {
@@ -38,7 +40,8 @@ int search_smem_per_warp(const DevIndex& ix, int mode, int ef_cap, int H, int NP
     const int r_pad = ix.r4 * 4;
     const int qs_len = mode == FINGER_MODE_FINGER_LP ? ix.m8 * 8 : ix.m4 * 4;
     const int qs_bytes = mode == FINGER_MODE_FINGER_LP ? 4 * ((qs_len + 3) & ~3) : 0;
-    int b = 8 * ef_cap + 4 * H + 8 * r_pad + qs_bytes + 32 * 32 * NPL + 32;
+    const int tile = mode == FINGER_MODE_FINGER_MLP ? 2 * 32 * NPL * ix.mlp_kp : 0;
+    int b = 8 * ef_cap + 4 * H + 8 * r_pad + qs_bytes + 32 * 32 * NPL + 32 + tile;
     return (b + 15) & ~15;
 }
 
@@ -49,6 +52,7 @@ cudaError_t launch_search(const DevIndex& ix, const SearchArgs& a, const SearchP
         case 1: return launch_mode1(ix, a, p, s);
         case 2: return launch_mode2(ix, a, p, s);
         case 3: return launch_mode3(ix, a, p, s);
+        case MODE_HARVEST: return launch_mode4(ix, a, p, s);
     }
     return cudaErrorInvalidValue;
 }
@@ -59,6 +63,7 @@ cudaError_t search_occupancy(const DevIndex&, const SearchPlan& p, int* bps) {
         case 1: return occupancy_mode1(p, bps);
         case 2: return occupancy_mode2(p, bps);
         case 3: return occupancy_mode3(p, bps);
+        case MODE_HARVEST: return occupancy_mode4(p, bps);
     }
     return cudaErrorInvalidValue;
 }
@@ -106,6 +111,7 @@ fg::DevIndex make_dev(const finger_index* ix) {
     d.b2 = ix->b2;
     d.b3 = ix->b3;
     d.mlp_eps = ix->mlp_eps;
+    d.mlp_kp = ix->mlp_kp;
     return d;
 }
 
@@ -162,7 +168,8 @@ finger_status make_plan(finger_index* ix, int mode, int ef_max, int64_t nq, Sear
     p->H = H;
     p->wpb = wpb;
     p->smem_per_warp = search_smem_per_warp(d, mode, p->ef_cap, p->H, p->NPL);
-    if ((int64_t)p->smem_per_warp * wpb > 227 * 1024) return FINGER_ERR_UNSUPPORTED;
+    p->blk_smem = mode == FINGER_MODE_FINGER_MLP ? 2 * 64 * ix->mlp_kp + 2 * 64 * 64 + 3 * 64 * 4 : 0;
+    if (p->blk_smem + (int64_t)p->smem_per_warp * wpb > 227 * 1024) return FINGER_ERR_UNSUPPORTED;
     int bps = 0;
     if (search_occupancy(d, *p, &bps) != cudaSuccess || bps < 1) {
         cudaGetLastError();
@@ -223,6 +230,7 @@ SearchArgs base_args(finger_index* ix, const SearchPlan& p) {
     a.spill = ix->spill;
     a.spill_cap = ix->spill_cap;
     a.warp_smem = p.smem_per_warp;
+    a.blk_smem = p.blk_smem;
     return a;
 }
 
@@ -362,8 +370,8 @@ static void drop_tables(finger_index* ix) {
     ix->edge_s = nullptr;
     ix->Xh = nullptr;
     ix->edge_q = nullptr;
-    ix->W1 = ix->W2 = ix->w3 = nullptr;
-    ix->b1 = ix->b2 = nullptr;
+    ix->W1 = ix->W2 = nullptr;
+    ix->w3 = ix->b1 = ix->b2 = nullptr;
     ix->r = ix->r_pad = ix->r16 = 0;
     ix->has_mlp = 0;
     ix->h_mlp.clear();

@@ -44,13 +44,15 @@ struct DevIndex {
     const uint4* Xh;        // n x m8 (BF16)
     const uint4* edge_q;    // (n*deg0) x r16 FP8-e4m3 codes of edge_u * code_scale
     float code_inv;         // 1 / code_scale
-    // learned predictor: BF16 weights W1 (H x (r+4)), W2 (H x H), w3 (H); FP32 biases
+    // learned predictor: BF16 W1 (H x kp, zero padded beyond r+4), BF16 W2 (H x H),
+    // w3 (H, BF16-valued FP32), FP32 biases
     const __nv_bfloat16* W1;
     const __nv_bfloat16* W2;
-    const __nv_bfloat16* w3;
+    const float* w3;
     const float* b1;
     const float* b2;
     float b3, mlp_eps;
+    int mlp_kp;
 };
 
 struct SearchArgs {
@@ -74,12 +76,16 @@ struct SearchArgs {
     uint32_t* spill;           // slots x spill_cap
     int spill_cap;
     int warp_smem;             // bytes per warp
-    // harvest (learned predictor training data); null when off
+    int blk_smem;              // bytes at the start of the block's smem (predictor weights)
+    // harvest (learned predictor training data); used by the harvest mode only
     float* hv_feat;            // cap x (r+4)
     float* hv_target;          // cap
+    int32_t* hv_trip;          // cap x 3: query, centre, neighbour
     unsigned long long* hv_count;
     int64_t hv_cap;
 };
+
+constexpr int MODE_HARVEST = 4;     // FINGER traversal that records predictor training data
 
 struct SearchPlan {
     int mode;
@@ -88,6 +94,7 @@ struct SearchPlan {
     int blocks;
     int ef_cap, H;
     int smem_per_warp;
+    int blk_smem;       // per-block shared memory before the warp regions
 };
 
 // kernels / launchers (search.cu)
@@ -142,9 +149,10 @@ struct finger_index {
     float code_scale = 256.0f;
     // learned predictor
     int has_mlp = 0;
+    int mlp_kp = 0;
     __nv_bfloat16* W1 = nullptr;
     __nv_bfloat16* W2 = nullptr;
-    __nv_bfloat16* w3 = nullptr;
+    float* w3 = nullptr;
     float* b1 = nullptr;
     float* b2 = nullptr;
     float b3 = 0.f, mlp_eps = 0.f;

@@ -385,27 +385,132 @@ __device__ __forceinline__ void edge_cos_list(const DevIndex& ix, size_t ebase, 
     __syncwarp();
 }
 
-// learned predictor: t = w3 . relu(W2 relu(W1 f + b1) + b2) + b3, features f of
-// length r+4 (uq*ud elementwise, t_hat, ||q_res||/||q||, ||d_res||/||d||,
-// a/(|a|+|b|+1e-6)); BF16 weights, FP32 accumulation.
-__device__ __forceinline__ float mlp_predict(const DevIndex& ix, const float* f, int nf) {
-    float h1[MLP_H];
-#pragma unroll 4
-    for (int j = 0; j < MLP_H; ++j) {
-        float acc = ix.b1[j];
-        const __nv_bfloat16* w = ix.W1 + (size_t)j * nf;
-        for (int i = 0; i < nf; ++i) acc = fmaf(__bfloat162float(w[i]), f[i], acc);
-        h1[j] = fmaxf(acc, 0.f);
+// Features of one (q, c, d) triple for the learned angle predictor (an
+// extension; the paper has no learned predictor): f = [u_q * u_d (r values),
+// t_hat, ||q_res|| / ||q||, ||d_res|| / ||d||, a / (|a| + |b| + 1e-6)], with
+// ||d||^2 = b^2 ||c||^2 + ||d_res||^2.  Written as BF16 into a shared-memory
+// tile row (inference) or as FP32 into a global row (harvest).  Returns t_hat,
+// summed in the same order as edge_cos.
+template <bool TO_GLOBAL>
+__device__ __forceinline__ float features_row(const DevIndex& ix, size_t e, const float* uq,
+                                              float2 sc, float cc, float ac, float qres_n,
+                                              float qn2, __nv_bfloat16* xrow, float* grow) {
+    const float4* ud = ix.edge_u + e * ix.r4;
+    float th = 0.f;
+    for (int k = 0; k < ix.r4; ++k) {
+        const float4 x = __ldg(ud + k);
+        const float p[4] = {x.x * uq[4 * k], x.y * uq[4 * k + 1], x.z * uq[4 * k + 2],
+                            x.w * uq[4 * k + 3]};
+        th = fmaf(x.x, uq[4 * k], th);
+        th = fmaf(x.y, uq[4 * k + 1], th);
+        th = fmaf(x.z, uq[4 * k + 2], th);
+        th = fmaf(x.w, uq[4 * k + 3], th);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int j = 4 * k + i;
+            if (j < ix.r) {
+                if constexpr (TO_GLOBAL) grow[j] = p[i];
+                else xrow[j] = __float2bfloat16_rn(p[i]);
+            }
+        }
     }
-    float out = ix.b3;
-    for (int j = 0; j < MLP_H; ++j) {
-        float acc = ix.b2[j];
-        const __nv_bfloat16* w = ix.W2 + (size_t)j * MLP_H;
-#pragma unroll 8
-        for (int i = 0; i < MLP_H; ++i) acc = fmaf(__bfloat162float(w[i]), h1[i], acc);
-        out = fmaf(__bfloat162float(ix.w3[j]), fmaxf(acc, 0.f), out);
+    const float dnorm = sqrtf(sc.y * sc.y * cc + sc.x * sc.x);
+    const float tail[4] = {th, qn2 > 0.f ? qres_n * rsqrtf(qn2) : 0.f,
+                           dnorm > 0.f ? sc.x / dnorm : 0.f,
+                           ac / (fabsf(ac) + fabsf(sc.y) + 1e-6f)};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        if constexpr (TO_GLOBAL) grow[ix.r + i] = tail[i];
+        else xrow[ix.r + i] = __float2bfloat16_rn(tail[i]);
     }
-    return out;
+    if constexpr (!TO_GLOBAL)
+        for (int j = ix.r + 4; j < ix.mlp_kp; ++j) xrow[j] = __float2bfloat16_rn(0.f);
+    return th;
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&v);
+}
+
+// D += A B for one m16n8k16 tile, BF16 operands, FP32 accumulators
+__device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// The predictor r+4 -> 64 -> 64 -> 1 on the 32*NPL feature rows of one
+// expansion (one row per neighbour slot) with warp-level BF16 tensor-core MMAs
+// (m16n8k16, FP32 accumulation).  Layer 1's accumulators are turned into the
+// A operand of layer 2 in registers (the C layout of two n8 tiles is the A
+// layout of one k16 step); layer 3 is an FP32 dot reduced over the lane quad.
+// W1s: 64 x kp BF16 (row = hidden unit), W2s: 64 x 64 BF16, b1s/b2s/w3s FP32.
+template <int NPL>
+__device__ __forceinline__ void mlp_batch(const __nv_bfloat16* xt, int kp,
+                                          const __nv_bfloat16* W1s, const __nv_bfloat16* W2s,
+                                          const float* b1s, const float* b2s, const float* w3s,
+                                          float b3, float* yout, int lane) {
+    const int g = lane >> 2, t = lane & 3;
+    const int nks = kp >> 4;
+    for (int mt = 0; mt < 2 * NPL; ++mt) {
+        const int r0 = mt * 16 + g, r1 = r0 + 8;
+        float acc[8][4];
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+            const float c0 = b1s[8 * nt + 2 * t], c1 = b1s[8 * nt + 2 * t + 1];
+            acc[nt][0] = c0;
+            acc[nt][1] = c1;
+            acc[nt][2] = c0;
+            acc[nt][3] = c1;
+        }
+        for (int ks = 0; ks < nks; ++ks) {
+            const uint32_t* X0 = reinterpret_cast<const uint32_t*>(xt + r0 * kp + 16 * ks);
+            const uint32_t* X1 = reinterpret_cast<const uint32_t*>(xt + r1 * kp + 16 * ks);
+            const uint32_t a[4] = {X0[t], X1[t], X0[t + 4], X1[t + 4]};
+#pragma unroll
+            for (int nt = 0; nt < 8; ++nt) {
+                const uint32_t* Wr =
+                    reinterpret_cast<const uint32_t*>(W1s + (8 * nt + g) * kp + 16 * ks);
+                mma_bf16(acc[nt], a, Wr[t], Wr[t + 4]);
+            }
+        }
+        uint32_t h[4][4];
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+            h[kk][0] = pack_bf16x2(fmaxf(acc[2 * kk][0], 0.f), fmaxf(acc[2 * kk][1], 0.f));
+            h[kk][1] = pack_bf16x2(fmaxf(acc[2 * kk][2], 0.f), fmaxf(acc[2 * kk][3], 0.f));
+            h[kk][2] = pack_bf16x2(fmaxf(acc[2 * kk + 1][0], 0.f), fmaxf(acc[2 * kk + 1][1], 0.f));
+            h[kk][3] = pack_bf16x2(fmaxf(acc[2 * kk + 1][2], 0.f), fmaxf(acc[2 * kk + 1][3], 0.f));
+        }
+        float p0 = 0.f, p1 = 0.f;
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+            float cacc[4];
+            cacc[0] = cacc[2] = b2s[8 * nt + 2 * t];
+            cacc[1] = cacc[3] = b2s[8 * nt + 2 * t + 1];
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+                const uint32_t* Wr =
+                    reinterpret_cast<const uint32_t*>(W2s + (8 * nt + g) * 64 + 16 * kk);
+                mma_bf16(cacc, h[kk], Wr[t], Wr[t + 4]);
+            }
+            const float wa = w3s[8 * nt + 2 * t], wb = w3s[8 * nt + 2 * t + 1];
+            p0 = fmaf(fmaxf(cacc[0], 0.f), wa, fmaf(fmaxf(cacc[1], 0.f), wb, p0));
+            p1 = fmaf(fmaxf(cacc[2], 0.f), wa, fmaf(fmaxf(cacc[3], 0.f), wb, p1));
+        }
+        p0 += __shfl_xor_sync(FULLMASK, p0, 1);
+        p0 += __shfl_xor_sync(FULLMASK, p0, 2);
+        p1 += __shfl_xor_sync(FULLMASK, p1, 1);
+        p1 += __shfl_xor_sync(FULLMASK, p1, 2);
+        if (t == 0) {
+            yout[r0] = p0 + b3;
+            yout[r1] = p1 + b3;
+        }
+    }
+    __syncwarp();
 }
 
 template <int MODE, int G, int VPL, int NPL>
@@ -413,6 +518,7 @@ __global__ void __launch_bounds__(128, 5) k_search(DevIndex ix, SearchArgs a) {
     constexpr bool LP = MODE == FINGER_MODE_FINGER_LP;
     constexpr bool EST = MODE != FINGER_MODE_PLAIN;
     constexpr bool MLP = MODE == FINGER_MODE_FINGER_MLP;
+    constexpr bool HARV = MODE == MODE_HARVEST;
     extern __shared__ __align__(16) unsigned char sm[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
@@ -422,7 +528,7 @@ __global__ void __launch_bounds__(128, 5) k_search(DevIndex ix, SearchArgs a) {
     const int nchunks = LP ? ix.m8 : ix.m4;
     const int qs_len = LP ? ix.m8 * 8 : ix.m4 * 4;
 
-    unsigned char* wb = sm + (size_t)wib * a.warp_smem;
+    unsigned char* wb = sm + a.blk_smem + (size_t)wib * a.warp_smem;
     float* Tk = reinterpret_cast<float*>(wb);
     uint32_t* Ti = reinterpret_cast<uint32_t*>(Tk + a.ef_cap);
     uint32_t* hash = Ti + a.ef_cap;
@@ -441,6 +547,23 @@ __global__ void __launch_bounds__(128, 5) k_search(DevIndex ix, SearchArgs a) {
     int* apos = reinterpret_cast<int*>(ai + 32 * NPL);        // slot of each admission
     float* aub = reinterpret_cast<float*>(apos + 32 * NPL);   // ub after it
     int* meta = reinterpret_cast<int*>(aub + 32 * NPL);       // replay results (8 ints)
+    __nv_bfloat16* xt = reinterpret_cast<__nv_bfloat16*>(meta + 8);   // predictor input tile
+    // predictor weights, staged once per block at the start of shared memory
+    __nv_bfloat16* W1s = reinterpret_cast<__nv_bfloat16*>(sm);
+    __nv_bfloat16* W2s = W1s + 64 * ix.mlp_kp;
+    float* b1s = reinterpret_cast<float*>(W2s + 64 * 64);
+    float* b2s = b1s + 64;
+    float* w3s = b2s + 64;
+    if constexpr (MLP) {
+        for (int i = threadIdx.x; i < 64 * ix.mlp_kp; i += blockDim.x) W1s[i] = ix.W1[i];
+        for (int i = threadIdx.x; i < 64 * 64; i += blockDim.x) W2s[i] = ix.W2[i];
+        for (int i = threadIdx.x; i < 64; i += blockDim.x) {
+            b1s[i] = ix.b1[i];
+            b2s[i] = ix.b2[i];
+            w3s[i] = ix.w3[i];
+        }
+        __syncthreads();
+    }
 
     if (FG_CHECKED) g_chk_err = a.err;   // same value from every thread
     const int64_t slot = (int64_t)blockIdx.x * wpb + wib;
@@ -610,6 +733,55 @@ __global__ void __launch_bounds__(128, 5) k_search(DevIndex ix, SearchArgs a) {
             // a5: estimates of the new neighbours against ub at expansion start
             const bool full0 = sz == ef;
             const float ub0 = full0 ? Tk[ef - 1] : INFINITY;
+            float tr[NPL];          // distribution-matched cosine per slot
+            int64_t hpos[NPL];      // harvest record of each slot (-1: none)
+#pragma unroll
+            for (int s = 0; s < NPL; ++s) {
+                tr[s] = 0.f;
+                hpos[s] = -1;
+            }
+            if constexpr (MLP || HARV) {
+                if (use_est) {
+#pragma unroll
+                    for (int s = 0; s < NPL; ++s) {
+                        const int o = s * 32 + lane;
+                        int64_t pos = -1;
+                        if constexpr (HARV) {
+                            const bool rec = isnew[s] && full0;
+                            const unsigned bm = __ballot_sync(FULLMASK, rec);
+                            unsigned long long base = 0;
+                            if (lane == 0 && bm) base = atomicAdd(a.hv_count, (unsigned long long)__popc(bm));
+                            base = __shfl_sync(FULLMASK, base, 0);
+                            if (rec) pos = (int64_t)base + __popc(bm & ltmask);
+                            if (pos >= a.hv_cap) pos = -1;
+                            hpos[s] = pos;
+                        }
+                        if (isnew[s]) {
+                            const size_t e = (size_t)c * ix.deg0 + o;
+                            const float2 sc = __ldg(ix.edge_s + e);
+                            float th;
+                            if constexpr (HARV) {
+                                if (pos >= 0)
+                                    th = features_row<true>(ix, e, uq, sc, cc, ac, qres_n, qn2,
+                                                            nullptr, a.hv_feat + pos * (ix.r + 4));
+                                else
+                                    th = edge_cos<false>(ix, e, uq);
+                            } else {
+                                th = features_row<false>(ix, e, uq, sc, cc, ac, qres_n, qn2,
+                                                         xt + (size_t)o * ix.mlp_kp, nullptr);
+                            }
+                            tr[s] = fmaf(th, ix.alpha, ix.beta);
+                        } else if constexpr (MLP) {
+                            for (int j = 0; j < ix.mlp_kp; ++j)
+                                xt[(size_t)o * ix.mlp_kp + j] = __float2bfloat16_rn(0.f);
+                        }
+                    }
+                    if constexpr (MLP) {
+                        __syncwarp();
+                        mlp_batch<NPL>(xt, ix.mlp_kp, W1s, W2s, b1s, b2s, w3s, ix.b3, es, lane);
+                    }
+                }
+            }
             int nl = 0;
             bool needr[NPL];
 #pragma unroll
@@ -620,31 +792,20 @@ __global__ void __launch_bounds__(128, 5) k_search(DevIndex ix, SearchArgs a) {
                     const float2 sc = __ldg(ix.edge_s + e);
                     float t;
                     if constexpr (MLP) {
-                        const float th = edge_cos<false>(ix, e, uq);
-                        // learned predictor in place of distribution matching
-                        float f[MAX_R + 8];
-                        const float4* ud = ix.edge_u + e * ix.r4;
-                        for (int k = 0; k < ix.r4; ++k) {
-                            const float4 x = __ldg(ud + k);
-                            f[4 * k + 0] = x.x * uq[4 * k + 0];
-                            f[4 * k + 1] = x.y * uq[4 * k + 1];
-                            f[4 * k + 2] = x.z * uq[4 * k + 2];
-                            f[4 * k + 3] = x.w * uq[4 * k + 3];
-                        }
-                        const float dnorm = sqrtf(sc.y * sc.y * cc + sc.x * sc.x);
-                        f[ix.r] = th;
-                        f[ix.r + 1] = qn2 > 0.f ? qres_n * rsqrtf(qn2) : 0.f;
-                        f[ix.r + 2] = dnorm > 0.f ? sc.x / dnorm : 0.f;
-                        f[ix.r + 3] = ac / (fabsf(ac) + fabsf(sc.y) + 1e-6f);
-                        const float pred = mlp_predict(ix, f, ix.r + 4);
-                        t = isfinite(pred) ? pred + ix.mlp_eps : fmaf(th, ix.alpha, ix.beta);
+                        // learned predictor in place of distribution matching;
+                        // the matched cosine is the fallback for a non-finite output
+                        const float y = es[s * 32 + lane];
+                        t = isfinite(y) ? y + ix.mlp_eps : tr[s];
+                    } else if constexpr (HARV) {
+                        t = tr[s];
                     } else {
                         t = fmaf(edge_cos<LP>(ix, e, uq), ix.alpha, ix.beta);
                     }
                     const float dd = ac - sc.y;
                     est = dd * dd * cc + qres2 + sc.x * sc.x - 2.f * qres_n * sc.x * t;
                 }
-                const bool need = isnew[s] && (!use_est || !full0 || !(est > ub0));
+                bool need = isnew[s] && (!use_est || !full0 || !(est > ub0));
+                if (HARV && hpos[s] >= 0) need = true;   // the record needs the exact distance
                 needr[s] = need;
                 if (need) prefetch_row<LP>(ix, nb[s]);
                 es[s * 32 + lane] = est;
@@ -656,6 +817,24 @@ __global__ void __launch_bounds__(128, 5) k_search(DevIndex ix, SearchArgs a) {
             // a6: exact distances of the survivors
             exact_list<LP, G, VPL>(q, ix, nbs, lst, nl, xb, lane);
             c_gath += nl;
+            if constexpr (HARV) {
+                // target cos(q_res, d_res) = (q^T d - a b ||c||^2) / (||q_res|| ||d_res||),
+                // q^T d from the exact distance, ||d||^2 = b^2 ||c||^2 + ||d_res||^2
+#pragma unroll
+                for (int s = 0; s < NPL; ++s) {
+                    if (hpos[s] < 0) continue;
+                    const int o = s * 32 + lane;
+                    const float2 sc = __ldg(ix.edge_s + (size_t)c * ix.deg0 + o);
+                    const float dn2 = sc.y * sc.y * cc + sc.x * sc.x;
+                    const float qd = 0.5f * (qn2 + dn2 - xb[o]);
+                    const float den = qres_n * sc.x;
+                    a.hv_target[hpos[s]] = den > 0.f ? (qd - ac * sc.y * cc) / den : 0.f;
+                    int32_t* tp = a.hv_trip + hpos[s] * 3;
+                    tp[0] = qi;
+                    tp[1] = (int32_t)c;
+                    tp[2] = (int32_t)nb[s];
+                }
+            }
 
             if (full0) {
                 // T is full and stays full.  Only neighbours evaluated exactly and
@@ -902,7 +1081,7 @@ __global__ void __launch_bounds__(128, 5) k_search(DevIndex ix, SearchArgs a) {
 template <int MODE>
 cudaError_t launch_mode(const DevIndex& ix, const SearchArgs& a, const SearchPlan& p,
                         cudaStream_t s) {
-    const int smem = p.smem_per_warp * p.wpb;
+    const int smem = p.blk_smem + p.smem_per_warp * p.wpb;
     const dim3 grid(p.blocks), block(p.wpb * 32);
 #define FG_CASE(G_, V_, N_)                                                                    \
     if (p.G == G_ && p.VPL == V_ && p.NPL == N_) {                                           \
@@ -924,7 +1103,7 @@ cudaError_t launch_mode(const DevIndex& ix, const SearchArgs& a, const SearchPla
 
 template <int MODE>
 cudaError_t occupancy_mode(const SearchPlan& p, int* blocks) {
-    const int smem = p.smem_per_warp * p.wpb;
+    const int smem = p.blk_smem + p.smem_per_warp * p.wpb;
 #define FG_CASE(G_, V_, N_)                                                                    \
     if (p.G == G_ && p.VPL == V_ && p.NPL == N_) {                                           \
         auto k = k_search<MODE, G_, V_, N_>;                                                   \
