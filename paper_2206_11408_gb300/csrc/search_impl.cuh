@@ -239,15 +239,18 @@ __device__ __forceinline__ void t_insert(float* Tk, uint32_t* Ti, int& sz, int e
     if (p < cursor) cursor = p;
 }
 
-enum { V_SEEN = 0, V_NEW = 1, V_NEW_SPILL = 2 };
+enum { V_SEEN = 0, V_NEW = 1, V_NEW_SPILL = 2, V_PENDING = 3 };
 
 __device__ __forceinline__ uint32_t hslot(uint32_t id, int logH) {
     return (id * 2654435769u) >> (32 - logH);
 }
 
-// exact test-and-set of the visited set
+// exact test-and-set of the visited set.  Once the shared-memory table is half
+// full (spill mode) ids not found in it are test-and-set in the warp's global
+// bitmap; the call then returns V_PENDING with the old bitmap word in `oldw`
+// (its value is only waited for where the caller first reads it).
 __device__ __forceinline__ int visit(uint32_t* hash, int H, int logH, uint32_t id, bool spill_mode,
-                                     uint32_t* bitmap) {
+                                     uint32_t* bitmap, uint32_t& oldw) {
     uint32_t h = hslot(id, logH);
     for (int probe = 0; probe < H; ++probe) {
         if (!spill_mode) {
@@ -258,9 +261,8 @@ __device__ __forceinline__ int visit(uint32_t* hash, int H, int logH, uint32_t i
             const uint32_t v = hash[h];
             if (v == id) return V_SEEN;
             if (v == PAD) {
-                const uint32_t bit = 1u << (id & 31);
-                const uint32_t old = atomicOr(&bitmap[id >> 5], bit);
-                return (old & bit) ? V_SEEN : V_NEW_SPILL;
+                oldw = atomicOr(&bitmap[id >> 5], 1u << (id & 31));
+                return V_PENDING;
             }
         }
         h = (h + 1) & (H - 1);
@@ -700,15 +702,29 @@ __global__ void __launch_bounds__(128, 5) k_search(DevIndex ix, SearchArgs a) {
                 if (lane < r_pad) pc0 = __ldg(pcr + lane);
                 if (lane + 32 < r_pad) pc1 = __ldg(pcr + lane + 32);
             }
-            bool isnew[NPL];
+            // In FINGER mode a bitmap test-and-set is resolved only after the
+            // neighbour's edge row has been requested, so the two round trips
+            // overlap; a neighbour that turns out visited just drops its estimate.
+            constexpr bool DEFER = MODE == FINGER_MODE_FINGER;
+            bool isnew[NPL], pend[NPL];
+            uint32_t pold[NPL];
 #pragma unroll
             for (int s = 0; s < NPL; ++s) {
                 int res = V_SEEN;
-                if (nb[s] != PAD) res = visit(hash, a.H, logH, (uint32_t)CK(nb[s], ix.n, 1004), spill_mode, bitmap);
+                uint32_t oldw = 0u;
+                if (nb[s] != PAD)
+                    res = visit(hash, a.H, logH, (uint32_t)CK(nb[s], ix.n, 1004), spill_mode, bitmap,
+                                oldw);
+                if (!DEFER && res == V_PENDING)
+                    res = (oldw & (1u << (nb[s] & 31))) ? V_SEEN : V_NEW_SPILL;
+                pend[s] = res == V_PENDING;
+                pold[s] = oldw;
                 isnew[s] = res != V_SEEN;
-                const unsigned sb = __ballot_sync(FULLMASK, res == V_NEW_SPILL);
-                if (res == V_NEW_SPILL) spl[CK(nspill + __popc(sb & ltmask), a.spill_cap, 1005)] = nb[s];
-                nspill += __popc(sb);
+                if (!DEFER) {
+                    const unsigned sb = __ballot_sync(FULLMASK, res == V_NEW_SPILL);
+                    if (res == V_NEW_SPILL) spl[CK(nspill + __popc(sb & ltmask), a.spill_cap, 1005)] = nb[s];
+                    nspill += __popc(sb);
+                }
                 hcount += __popc(__ballot_sync(FULLMASK, res == V_NEW));
                 nbs[s * 32 + lane] = nb[s];
             }
@@ -803,6 +819,14 @@ __global__ void __launch_bounds__(128, 5) k_search(DevIndex ix, SearchArgs a) {
                     }
                     const float dd = ac - sc.y;
                     est = dd * dd * cc + qres2 + sc.x * sc.x - 2.f * qres_n * sc.x * t;
+                }
+                if (DEFER) {
+                    // resolve the deferred bitmap test-and-set of this slot
+                    if (pend[s]) isnew[s] = !(pold[s] & (1u << (nb[s] & 31)));
+                    const bool sp = pend[s] && isnew[s];
+                    const unsigned sb = __ballot_sync(FULLMASK, sp);
+                    if (sp) spl[CK(nspill + __popc(sb & ltmask), a.spill_cap, 1005)] = nb[s];
+                    nspill += __popc(sb);
                 }
                 bool need = isnew[s] && (!use_est || !full0 || !(est > ub0));
                 if (HARV && hpos[s] >= 0) need = true;   // the record needs the exact distance
