@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--candidates", type=int, default=64)
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--save-curves", default="")
+    ap.add_argument("--profile-ef", type=int, default=0,
+                    help="profiling run: set up, then only --warmup + 1 FINGER searches at this ef")
     return ap.parse_args()
 
 
@@ -155,22 +157,56 @@ def profiled_traffic(workload: str, per_query_scale: float):
 
 
 def algorithmic_bytes(cnt: dict, nq: int, m: int, r: int, deg0: int, M: int, K: int,
-                      warmup: int, finger: bool) -> float:
-    """Bytes the method must move per launch (SURVEY-style accounting):
-    adjacency rows of every expansion, per-centre D5 rows (||c||^2, Pc) after
-    warm-up, one D6 row (r+2 floats) per estimate, one full row per exact
-    distance (layer 0 and upper layers, plus the upper adjacency rows), the
-    queries and the results."""
+                      warmup: int, finger: bool, lp: bool = False, rerank: int = 0,
+                      sector: int = 0) -> float:
+    """Bytes the method must move per launch: the adjacency row of every
+    layer-0 expansion (deg0 u32), the per-centre row (||c||^2 and P c, r+1
+    floats) of every post-warm-up expansion, one edge row (r+2 floats; LP:
+    r one-byte codes + 2 floats) per estimate, one vector row per exact distance
+    (m floats; LP: m BF16) on layer 0 and on the upper levels, the FP32 rows of
+    the re-ranked entries (LP), the queries and the results.  ``sector`` > 0
+    rounds every row up to whole sectors of that many bytes."""
+    def row(nbytes):
+        return -(-nbytes // sector) * sector if sector else nbytes
+
     E = cnt["expansions"]
-    b = E * 4 * deg0
-    b += cnt["exact"] * 4 * m
-    b += cnt["upper"] * 4 * m + cnt["upper"] * 4 * M / max(M, 1) * 0
+    wv = 2 if lp else 4
+    b = E * row(4 * deg0)
+    b += cnt["exact"] * row(wv * m)
+    b += cnt["upper"] * row(4 * m)
     if finger:
         post = max(E - warmup * nq, 0)
-        b += post * 4 * (r + 1)
-        b += cnt["estimates"] * 4 * (r + 2)
+        b += post * (row(4 * r) + row(4))
+        b += cnt["estimates"] * ((row(r) if lp else row(4 * r)) + row(8))
+    if lp:
+        b += nq * rerank * row(4 * m)
     b += nq * 4 * m + nq * K * 12
     return float(b)
+
+
+def qps_at(curve, target=TARGET_RECALL):
+    """QPS at the target recall by linear interpolation on the (recall, QPS)
+    Pareto frontier of an ef sweep; None if the target is not reached."""
+    pts = [(rec, qps) for _, rec, qps in curve]
+    front = sorted(p for p in pts
+                   if not any((o[0] >= p[0] and o[1] > p[1]) or (o[0] > p[0] and o[1] >= p[1])
+                              for o in pts))
+    if not front or front[-1][0] < target:
+        return None
+    if front[0][0] >= target:
+        return front[0][1]
+    for (r0, q0), (r1, q1) in zip(front, front[1:]):
+        if r0 <= target <= r1:
+            return q0 + (q1 - q0) * (target - r0) / (r1 - r0) if r1 > r0 else max(q0, q1)
+    return None
+
+
+def tie_recall(ids: np.ndarray, dists: np.ndarray, gt_d: np.ndarray, K: int) -> float:
+    """Recall that counts a result as a hit when its distance is at most the
+    K-th exact distance (ties at the K-th distance all count)."""
+    kth = gt_d[:, K - 1:K]
+    ok = (dists[:, :K] <= kth) & (ids[:, :K] >= 0)
+    return float(np.minimum(ok.sum(1), K).sum() / (K * len(ids)))
 
 
 # ---------------------------------------------------------------- reference
@@ -235,10 +271,271 @@ def cpu_baseline(X, Q, K, budget_s=12.0):
 
 # ---------------------------------------------------------------------- ours
 
+# ------------------------------------------------------------ extension legs
+
+def _ext_setup(args, cfg, build_lp=False):
+    import torch
+
+    import paper_2206_11408_gb300 as fg
+    c = workloads.config(cfg)
+    n = args.n or c.n
+    nq = args.nq or c.nq
+    t0 = time.perf_counter()
+    X = workloads.base_vectors(cfg, n)
+    Q = workloads.query_vectors(cfg, nq)
+    ix = fg.Index(X)
+    tg = time.perf_counter()
+    ix.build_graph(c.M, candidates=max(args.candidates, 2 * c.M), level_seed=3000 + cfg)
+    torch.cuda.synchronize()
+    tg = time.perf_counter() - tg
+    tt = time.perf_counter()
+    ix.build_tables(c.r, 4000 + cfg, build_lp=build_lp)
+    torch.cuda.synchronize()
+    tt = time.perf_counter() - tt
+    q = torch.from_numpy(Q).cuda()
+    return c, n, nq, X, Q, ix, q, {"graph": tg, "tables": tt, "total": time.perf_counter() - t0}
+
+
+def _sweep(ix, q, gt, K, modes, ef_grid, nq):
+    import torch
+    stream = torch.cuda.current_stream()
+    curves, choice = {}, {}
+    for name, mode in modes.items():
+        ix.set_mode(mode, 5)
+        pts = []
+        for ef in ef_grid:
+            if ef < K:
+                continue
+            ids, d = ix.search(q, K, ef)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ix.search(q, K, ef, ids, d)
+            e1.record(stream)
+            e1.synchronize()
+            ix.sync()
+            rec = recall_at(ids.cpu().numpy(), gt, K)
+            pts.append((ef, rec, nq / (e0.elapsed_time(e1) / 1000)))
+            if rec >= TARGET_RECALL and name not in choice:
+                choice[name] = (ef, rec)
+            if name in choice and ef >= choice[name][0] + 40:
+                break
+        curves[name] = pts
+        if name not in choice:
+            best = max(pts, key=lambda p_: p_[1])
+            choice[name] = (best[0], best[1])
+    return curves, choice
+
+
+def _timed(ix, q, K, ef, mode, steps, warmup, nq, clocks=None):
+    import torch
+    stream = torch.cuda.current_stream()
+    ix.set_mode(mode, 5)
+    ids, d = ix.search(q, K, ef)
+    for _ in range(warmup):
+        ix.search(q, K, ef, ids, d)
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.start()
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    for _ in range(steps):
+        ix.search(q, K, ef, ids, d)
+    g1.record(stream)
+    torch.cuda.synchronize()
+    ck = clocks.stop() if clocks else None
+    ix.sync()
+    ms = g0.elapsed_time(g1) / steps
+    return nq / (ms / 1000), ms, ids, ck
+
+
+def _line(c, n, nq, value, ms, steps, warmup, extra, clocks):
+    line = {"metric": "queries/sec at recall@10=0.95, FINGER vs plain greedy search",
+            "value": value, "unit": "queries/s", "n_gpus": 1, "steps": steps, "warmup": warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": c.name if n == c.n else f"{c.name}[:{n}]", "n": n, "m": c.m,
+                       "nq": nq, "K": c.K, "M": c.M, "r": c.r},
+            "clocks": clocks, "gpu_launches": steps}
+    line.update(extra)
+    return line
+
+
+def leg_lp(args):
+    """Configuration 3: BF16 rows + FP8-e4m3 residual codes (mode LP) vs FP32
+    FINGER vs plain, QPS at recall@10 0.95, plus the distance error of the
+    returned (FP32 re-ranked) distances and of the BF16 rows vs FP64."""
+    import paper_2206_11408_gb300 as fg
+    c, n, nq, X, Q, ix, q, setup = _ext_setup(args, 3, build_lp=True)
+    gt_ids, _ = ix.knn(q, c.K)
+    gt = gt_ids.cpu().numpy()
+    modes = {"plain": fg.MODE_PLAIN, "finger": fg.MODE_FINGER, "finger_lp": fg.MODE_FINGER_LP}
+    curves, choice = _sweep(ix, q, gt, c.K, modes, c.ef_grid, nq)
+    res = {}
+    ck = None
+    for name, mode in modes.items():
+        v, ms, ids, k = _timed(ix, q, c.K, choice[name][0], mode, args.steps, args.warmup, nq,
+                               Clocks(0) if name == "finger_lp" else None)
+        res[name] = (v, ms, ids)
+        ck = k or ck
+    ids_t, dd = ix.search(q[:200], c.K, choice["finger_lp"][0])
+    ids = np.maximum(ids_t.cpu().numpy(), 0)
+    Xd, Qd = X.astype(np.float64), Q[:200].astype(np.float64)
+    ref = ((Qd[:, None, :] - Xd[ids]) ** 2).sum(-1)
+    rel32 = np.abs(dd.cpu().numpy() - ref) / np.maximum(ref, 1e-30)
+    import torch
+    xb = torch.from_numpy(X[ids.reshape(-1)]).to(torch.bfloat16).to(torch.float64).numpy()
+    refb = ((Qd.repeat(c.K, 0) - xb) ** 2).sum(-1).reshape(ids.shape)
+    relb = np.abs(refb - ref) / np.maximum(ref, 1e-30)
+    extra = {"impl_mode": "FINGER_LP (BF16 rows, FP8-e4m3 codes, FP32 re-rank)",
+             "finger_qps": res["finger"][0], "plain_qps": res["plain"][0],
+             "lp_over_plain": res["finger_lp"][0] / res["plain"][0],
+             "ef": {k: v[0] for k, v in choice.items()},
+             "recall": {k: v[1] for k, v in choice.items()},
+             "distance_error_vs_fp64": {"returned_fp32": {"max": float(rel32.max()),
+                                                          "mean": float(rel32.mean())},
+                                        "bf16_rows": {"max": float(relb.max()),
+                                                      "mean": float(relb.mean())}},
+             "setup_s": setup,
+             "curves": {k: [[e, round(r_, 4), round(v_, 1)] for e, r_, v_ in pts]
+                        for k, pts in curves.items()}}
+    return _line(c, n, nq, res["finger_lp"][0], res["finger_lp"][1], args.steps, args.warmup,
+                 extra, ck)
+
+
+def leg_mlp(args):
+    """Configuration 4: learned predictor (harvest on training queries, GPU
+    training) vs distribution-matched FINGER vs plain, QPS at recall@10 0.95."""
+    import torch
+
+    import paper_2206_11408_gb300 as fg
+    c, n, nq, X, Q, ix, q, setup = _ext_setup(args, 4)
+    gt_ids, _ = ix.knn(q, c.K)
+    gt = gt_ids.cpu().numpy()
+    th = time.perf_counter()
+    Qtr = torch.from_numpy(workloads.training_queries(4, 1000)).cuda()
+    ix.set_mode(fg.MODE_FINGER, 5)
+    cnt = torch.zeros((1000, 8), dtype=torch.int32, device="cuda")
+    ix.set_counters(cnt)
+    feat, tgt, _ = ix.harvest(Qtr, 100, 2_000_000)
+    ix.set_counters(None)
+    expansions = int(cnt[:, 0].sum().item())
+    harvest_s = time.perf_counter() - th
+    tt = time.perf_counter()
+    nrec = feat.shape[0]
+    n_val = nrec // 10
+    losses = ix.train_predictor(feat.contiguous(), tgt.contiguous(), n_val, epochs=6, batch=4096,
+                                lr=2e-3, seed=5004)
+    train_s = time.perf_counter() - tt
+    w, eps_mlp = ix.get_predictor()
+    fv, tv = feat[nrec - n_val:].contiguous(), tgt[nrec - n_val:].cpu().numpy()
+    pred = ix.mlp_predict(fv).cpu().numpy()
+    st = ix.stats()
+    ratio = st["sigma"] / st["sigma_hat"] if st["sigma_hat"] > 0 else 0.0
+    matched = (fv[:, c.r].cpu().numpy() - st["mu_hat"]) * ratio + st["mu"]
+    modes = {"plain": fg.MODE_PLAIN, "finger": fg.MODE_FINGER, "finger_mlp": fg.MODE_FINGER_MLP}
+    curves, choice = _sweep(ix, q, gt, c.K, modes, c.ef_grid, nq)
+    res, ck = {}, None
+    for name, mode in modes.items():
+        v, ms, ids, k = _timed(ix, q, c.K, choice[name][0], mode, args.steps, args.warmup, nq,
+                               Clocks(0) if name == "finger_mlp" else None)
+        res[name] = (v, ms)
+        ck = k or ck
+    extra = {"impl_mode": "FINGER_MLP (learned angle predictor, BF16 tensor-core inference)",
+             "finger_qps": res["finger"][0], "plain_qps": res["plain"][0],
+             "mlp_over_plain": res["finger_mlp"][0] / res["plain"][0],
+             "mlp_over_finger": res["finger_mlp"][0] / res["finger"][0],
+             "ef": {k: v[0] for k, v in choice.items()},
+             "recall": {k: v[1] for k, v in choice.items()},
+             "predictor": {"triples": int(nrec), "harvest_expansions": expansions,
+                           "epochs": len(losses), "loss_first_last": [float(losses[0]),
+                                                                      float(losses[-1])],
+                           "eps_prime": float(eps_mlp),
+                           "heldout_cos_mae": {"mlp": float(np.abs(pred - tv).mean()),
+                                               "matching": float(np.abs(matched - tv).mean())},
+                           "harvest_s": harvest_s, "train_s": train_s},
+             "setup_s": setup,
+             "curves": {k: [[e, round(r_, 4), round(v_, 1)] for e, r_, v_ in pts]
+                        for k, pts in curves.items()}}
+    return _line(c, n, nq, res["finger_mlp"][0], res["finger_mlp"][1], args.steps, args.warmup,
+                 extra, ck)
+
+
+def leg_batch(args):
+    """Configuration 5: an uneven stream of 50,000 queries in batches of 1..4096
+    with K in {1, 10, 100} and ef in [max(K,10), 400], one captured persistent
+    launch per batch (autotuned per ef bucket), FINGER vs plain: throughput,
+    p50/p99 batch latency and mean recall@K."""
+    import torch
+
+    import paper_2206_11408_gb300 as fg
+    c, n, nq, X, Q, ix, q, setup = _ext_setup(args, 5)
+    plan = workloads.uneven_batches(nq)
+    gt_ids, _ = ix.knn(q, 100)
+    gt = gt_ids.cpu().numpy()
+    stream = torch.cuda.current_stream()
+    batches = []
+    for start, size, K, ef in plan:
+        off = np.zeros(size, np.int64)
+        off[1:] = np.cumsum(K.astype(np.int64))[:-1]
+        batches.append((start, size, torch.from_numpy(K).cuda(), torch.from_numpy(ef).cuda(),
+                        int(ef.max()), K, torch.from_numpy(off).cuda(), int(K.sum())))
+    out = {}
+    ck = None
+    for name, mode in (("plain", fg.MODE_PLAIN), ("finger", fg.MODE_FINGER)):
+        ix.set_mode(mode, 5)
+        # autotune each ef bucket on a sample batch at the bucket's largest ef
+        for b in (16, 32, 64, 128, 256, 512):
+            if b >= 10:
+                ix.autotune(q[:2048], 10, min(b, 400))
+        for start, size, Kt, eft, mx, _, off, tot in batches:   # warm-up pass: captures graphs
+            ix.search_batch(q[start:start + size], Kt, eft, max_ef=mx, offsets=off, total=tot)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in batches]
+        clocks = Clocks(0) if name == "finger" else None
+        if clocks:
+            clocks.start()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        results = []
+        for (start, size, Kt, eft, mx, _, off, tot), (a, b_) in zip(batches, ev):
+            a.record(stream)
+            r_ = ix.search_batch(q[start:start + size], Kt, eft, max_ef=mx, offsets=off, total=tot)
+            b_.record(stream)
+            results.append(r_)
+        g1.record(stream)
+        torch.cuda.synchronize()
+        if clocks:
+            ck = clocks.stop()
+        ix.sync()
+        total_ms = g0.elapsed_time(g1)
+        lat = np.array([a.elapsed_time(b_) for a, b_ in ev])
+        hits, tot = 0, 0
+        for (start, size, Kt, eft, mx, K, _, _), (ids, _, off) in zip(batches, results):
+            ids, off = ids.cpu().numpy(), off.cpu().numpy()
+            for i in range(size):
+                k = int(K[i])
+                got = ids[off[i]:off[i] + k]
+                hits += len(np.intersect1d(got, gt[start + i, :k]))
+                tot += k
+        out[name] = {"qps": nq / (total_ms / 1000), "total_ms": total_ms,
+                     "p50_batch_ms": float(np.percentile(lat, 50)),
+                     "p99_batch_ms": float(np.percentile(lat, 99)), "recall": hits / tot}
+    extra = {"impl_mode": "uneven batches, graph-captured persistent launch, autotuned",
+             "batches": len(batches), "plain": out["plain"], "finger": out["finger"],
+             "finger_over_plain": out["finger"]["qps"] / out["plain"]["qps"], "setup_s": setup,
+             "gpu_launches": len(batches)}
+    return _line(c, n, nq, out["finger"]["qps"], out["finger"]["total_ms"], 1, 1, extra, ck)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.cfg in (3, 4, 5):
+        line = {3: leg_lp, 4: leg_mlp, 5: leg_batch}[args.cfg](args)
+        print(json.dumps(line), flush=True)
+        return 0
     import torch
 
     import paper_2206_11408_gb300 as fg
@@ -258,15 +555,27 @@ def main():
     ix = fg.Index(X, device=local)
     t0 = time.perf_counter()
     ix.build_graph(c.M, candidates=args.candidates, level_seed=3000 + args.cfg)
+    torch.cuda.synchronize()
     t_graph = time.perf_counter() - t0
     t0 = time.perf_counter()
     ix.build_tables(c.r, 4000 + args.cfg)
+    torch.cuda.synchronize()
     t_tables = time.perf_counter() - t0
     info = ix.info()
     q = torch.from_numpy(Q).cuda()
-    gt_ids, _ = ix.knn(q, K)
+    if args.profile_ef:
+        ix.set_mode(fg.MODE_FINGER, 5)
+        ids, d = ix.search(q, K, args.profile_ef)
+        for _ in range(args.warmup):
+            ix.search(q, K, args.profile_ef, ids, d)
+        torch.cuda.synchronize()
+        ix.sync()
+        ix.close()
+        return 0
+    gt_ids, gt_dt = ix.knn(q, K)
     torch.cuda.synchronize()
     gt = gt_ids.cpu().numpy()
+    gt_d = gt_dt.cpu().numpy()
     stream = torch.cuda.current_stream()
 
     def timed(mode, ef, reps=1):
@@ -281,10 +590,13 @@ def main():
             e1.synchronize()
             best = min(best, e0.elapsed_time(e1))
         ix.sync()
-        return ids.cpu().numpy(), best
+        last[mode] = (ids.cpu().numpy(), d.cpu().numpy())
+        return last[mode][0], best
 
     curves = {}
     choice = {}
+    tie = {}
+    last = {}
     for name, mode in (("plain", fg.MODE_PLAIN), ("finger", fg.MODE_FINGER)):
         pts = []
         for ef in c.ef_grid:
@@ -295,6 +607,7 @@ def main():
             pts.append((ef, rec, nq / (ms / 1000)))
             if rec >= TARGET_RECALL and name not in choice:
                 choice[name] = (ef, rec)
+                tie[name] = tie_recall(last[mode][0], last[mode][1], gt_d, K)
             if name in choice and ef >= choice[name][0] + 40:
                 break
         curves[name] = pts
@@ -356,6 +669,7 @@ def main():
     ix.set_counters(None)
     csum = dict(zip(fg.COUNTER_NAMES, cnt_t.sum(0).cpu().numpy().astype(np.int64).tolist()))
     algo = algorithmic_bytes(csum, nq, c.m, c.r, info["deg0"], c.M, K, 5, True)
+    algo32 = algorithmic_bytes(csum, nq, c.m, c.r, info["deg0"], c.M, K, 5, True, sector=32)
     kern_ms = statistics.median(per_f)
     peak, peak_kind = measured_peaks()
     achieved = algo / (kern_ms / 1000) / 1e9
@@ -405,7 +719,10 @@ def main():
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_kind": peak_kind, "kernel": "k_search<FINGER> (search_m1.cu)",
-                         "algorithmic_bytes_per_launch": algo, "kernel_ms": kern_ms},
+                         "algorithmic_bytes_per_launch": algo,
+                         "algorithmic_bytes_sector32": algo32, "kernel_ms": kern_ms},
+            "qps_at_recall_interp": {k: qps_at(v) for k, v in curves.items()},
+            "recall_tie_aware": tie,
             "cpu_baseline": cpu,
             "e2e": {"value": ws * nq / (e2e_ms / 1000), "unit": "queries/s",
                     "h2d_bytes_per_step": nq * c.m * 4, "d2h_bytes_per_step": nq * K * 12,

@@ -310,16 +310,22 @@ class Index:
                "finger_search_host")
         return ids, d
 
-    def search_batch(self, queries, K, ef, max_ef: int | None = None, stream=None):
+    def search_batch(self, queries, K, ef, max_ef: int | None = None, offsets=None,
+                     total: int | None = None, stream=None):
         """Uneven batch: K, ef int32 CUDA tensors (per query).  Returns flat ids,
-        dists and the int64 offsets of each query's results."""
+        dists and the int64 offsets of each query's results.  A caller that
+        already has the exclusive prefix sum of K (``offsets``, int64 CUDA) and
+        its total passes them to keep the call free of host synchronisation."""
         import torch
         nq = queries.shape[0]
-        Kc = K.to(torch.int64)
-        off = torch.zeros(nq, dtype=torch.int64, device=queries.device)
-        if nq > 1:
-            off[1:] = torch.cumsum(Kc, 0)[:-1]
-        total = int(Kc.sum().item()) if nq else 0
+        if offsets is None or total is None:
+            Kc = K.to(torch.int64)
+            off = torch.zeros(nq, dtype=torch.int64, device=queries.device)
+            if nq > 1:
+                off[1:] = torch.cumsum(Kc, 0)[:-1]
+            total = int(Kc.sum().item()) if nq else 0
+        else:
+            off = offsets
         if max_ef is None:
             max_ef = int(ef.max().item())
         ids = torch.empty(max(total, 1), dtype=torch.int64, device=queries.device)

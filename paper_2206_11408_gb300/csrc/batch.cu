@@ -5,9 +5,10 @@
 // ef arrays and output offsets.  The launch is sized for the batch's bound on
 // ef (bucketed to a power of two): result-list capacity, visited-hash size and
 // warps per block come from the tuned plan of that bucket if the autotuner ran
-// for it, else from the default heuristic.  The first call for an (nq, bucket)
-// shape captures the work-counter reset and the kernel into a CUDA graph; later
-// calls update the kernel node's arguments and replay the graph.
+// for it, else from the default heuristic.  The first call for an (nq bucket,
+// ef bucket) shape (powers of two) captures the work-counter reset and the
+// kernel into a CUDA graph; later calls of that shape update the kernel node's
+// arguments (queries, sizes, outputs) and replay the graph.
 #include <string.h>
 
 #include <algorithm>
@@ -73,13 +74,17 @@ finger_status finger_search_batch(finger_index* ix, const float* queries, int64_
     if (prev != ix->device) cudaSetDevice(ix->device);
     cudaStream_t s = (cudaStream_t)stream;
     const int bucket = std::min(bucket_of(max_ef), MAX_EF);
+    // launch shapes are keyed by power-of-two buckets of nq and ef, so one
+    // captured graph serves every batch of its bucket (surplus warps exit)
+    int64_t nqb = 1;
+    while (nqb < nq) nqb <<= 1;
     SearchPlan p;
     auto tit = ix->tuned.find(bucket);
     if (tit != ix->tuned.end() && tit->second.mode == ix->mode) {
         p = tit->second;
-        st = fg_make_plan(ix, ix->mode, bucket, nq, &p, p.wpb, p.H);
+        st = fg_make_plan(ix, ix->mode, bucket, nqb, &p, p.wpb, p.H);
     } else {
-        st = fg_make_plan(ix, ix->mode, bucket, nq, &p, 4, 0);
+        st = fg_make_plan(ix, ix->mode, bucket, nqb, &p, 4, 0);
     }
     if (st != FINGER_OK) {
         if (prev != ix->device) cudaSetDevice(prev);
@@ -102,7 +107,7 @@ finger_status finger_search_batch(finger_index* ix, const float* queries, int64_
     a.out_d = out_dists;
     a.rerank = 32;
     const DevIndex d = make_dev(ix);
-    const auto key = std::make_pair(nq, bucket * 4 + ix->mode);
+    const auto key = std::make_pair(nqb, bucket * 4 + ix->mode);
     auto& caps = captures()[ix];
     auto it = caps.find(key);
     finger_status ret = FINGER_OK;

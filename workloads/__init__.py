@@ -5,4 +5,5 @@ shapes and value distributions of the five benchmark configurations.  It holds
 none of the search or table arithmetic, so the FP64 oracle and the CUDA path
 can both take their inputs from it without sharing any method code.
 """
-from .gen import CONFIGS, WorkloadConfig, base_vectors, query_vectors, config  # noqa: F401
+from .gen import (CONFIGS, WorkloadConfig, base_vectors, config, query_vectors,  # noqa: F401
+                  training_queries, uneven_batches)

@@ -134,6 +134,12 @@ def query_vectors(cfg: int, nq: int | None = None, threads: int = 8) -> np.ndarr
     return _rows(cfg, c.nq if nq is None else int(nq), 2, 2000 + cfg, threads)
 
 
+def training_queries(cfg: int, nq: int, threads: int = 8) -> np.ndarray:
+    """Queries for harvesting predictor training data: fresh draws from the same
+    mixture with seed 5000+cfg, disjoint from the test queries (2000+cfg)."""
+    return _rows(cfg, nq, 3, 5000 + cfg, threads)
+
+
 def uneven_batches(total: int = 50_000, seed: int = 2005):
     """Batch plan of the uneven query stream (configuration 5).
 
