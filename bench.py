@@ -348,6 +348,32 @@ def _timed(ix, q, K, ef, mode, steps, warmup, nq, clocks=None):
     return nq / (ms / 1000), ms, ids, ck
 
 
+def _leg_roofline(fg, ix, q, c, ef, mode, kern_ms, lp=False):
+    """Roofline of one timed launch of a leg: counters of the same search turned
+    into algorithmic bytes, divided by the launch's CUDA-event time."""
+    import torch
+    nq = q.shape[0]
+    info = ix.info()
+    cnt = torch.zeros((nq, 8), dtype=torch.int32, device="cuda")
+    ix.set_mode(mode, 5)
+    ix.set_counters(cnt)
+    ix.search(q, c.K, ef)
+    torch.cuda.synchronize()
+    ix.set_counters(None)
+    ix.sync()
+    csum = dict(zip(fg.COUNTER_NAMES, cnt.sum(0).cpu().numpy().astype(np.int64).tolist()))
+    finger = mode != fg.MODE_PLAIN
+    rr = min(ef, 2 * c.K) if lp else 0
+    algo = algorithmic_bytes(csum, nq, c.m, c.r, info["deg0"], c.M, c.K, 5, finger, lp, rr)
+    algo32 = algorithmic_bytes(csum, nq, c.m, c.r, info["deg0"], c.M, c.K, 5, finger, lp, rr, 32)
+    peak, kind = measured_peaks()
+    ach = algo / (kern_ms / 1000) / 1e9
+    return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+            "traffic": None, "peak_kind": kind, "algorithmic_bytes_per_launch": algo,
+            "algorithmic_bytes_sector32": algo32, "kernel_ms": kern_ms}, \
+        {k: v / nq for k, v in csum.items()}
+
+
 def _line(c, n, nq, value, ms, steps, warmup, extra, clocks):
     line = {"metric": "queries/sec at recall@10=0.95, FINGER vs plain greedy search",
             "value": value, "unit": "queries/s", "n_gpus": 1, "steps": steps, "warmup": warmup,
@@ -386,7 +412,11 @@ def leg_lp(args):
     xb = torch.from_numpy(X[ids.reshape(-1)]).to(torch.bfloat16).to(torch.float64).numpy()
     refb = ((Qd.repeat(c.K, 0) - xb) ** 2).sum(-1).reshape(ids.shape)
     relb = np.abs(refb - ref) / np.maximum(ref, 1e-30)
+    roof, cpq = _leg_roofline(fg, ix, q, c, choice["finger_lp"][0], fg.MODE_FINGER_LP,
+                              res["finger_lp"][1], lp=True)
     extra = {"impl_mode": "FINGER_LP (BF16 rows, FP8-e4m3 codes, FP32 re-rank)",
+             "roofline": roof, "counters_per_query": cpq,
+             "qps_at_recall_interp": {k: qps_at(v) for k, v in curves.items()},
              "finger_qps": res["finger"][0], "plain_qps": res["plain"][0],
              "lp_over_plain": res["finger_lp"][0] / res["plain"][0],
              "ef": {k: v[0] for k, v in choice.items()},
@@ -440,7 +470,11 @@ def leg_mlp(args):
                                Clocks(0) if name == "finger_mlp" else None)
         res[name] = (v, ms)
         ck = k or ck
+    roof, cpq = _leg_roofline(fg, ix, q, c, choice["finger_mlp"][0], fg.MODE_FINGER_MLP,
+                              res["finger_mlp"][1])
     extra = {"impl_mode": "FINGER_MLP (learned angle predictor, BF16 tensor-core inference)",
+             "roofline": roof, "counters_per_query": cpq,
+             "qps_at_recall_interp": {k: qps_at(v) for k, v in curves.items()},
              "finger_qps": res["finger"][0], "plain_qps": res["plain"][0],
              "mlp_over_plain": res["finger_mlp"][0] / res["plain"][0],
              "mlp_over_finger": res["finger_mlp"][0] / res["finger"][0],
@@ -461,40 +495,57 @@ def leg_mlp(args):
 
 
 def leg_batch(args):
-    """Configuration 5: an uneven stream of 50,000 queries in batches of 1..4096
-    with K in {1, 10, 100} and ef in [max(K,10), 400], one captured persistent
-    launch per batch (autotuned per ef bucket), FINGER vs plain: throughput,
-    p50/p99 batch latency and mean recall@K."""
+    """Configuration 5.  (1) The metric on a uniform K = 10 stream: ef sweeps of
+    plain and FINGER on the first 10,000 queries, QPS at recall@10 0.95.
+    (2) The uneven stream: 50,000 queries in batches of 1..4096 with K in
+    {1, 10, 100} and ef in [max(K,10), 400], one captured persistent launch per
+    batch (autotuned per ef bucket).  Plain serves each query at its ef; FINGER
+    at ef scaled by the ratio of the two methods' ef at recall 0.95 in (1), so
+    both serve the stream at about the same recall.  Throughput, p50/p99 batch
+    latency and mean recall@K."""
     import torch
 
     import paper_2206_11408_gb300 as fg
     c, n, nq, X, Q, ix, q, setup = _ext_setup(args, 5)
-    plan = workloads.uneven_batches(nq)
+    stream = torch.cuda.current_stream()
+    nu = min(nq, 10_000)
+    qu = q[:nu]
     gt_ids, _ = ix.knn(q, 100)
     gt = gt_ids.cpu().numpy()
-    stream = torch.cuda.current_stream()
-    batches = []
-    for start, size, K, ef in plan:
-        off = np.zeros(size, np.int64)
-        off[1:] = np.cumsum(K.astype(np.int64))[:-1]
-        batches.append((start, size, torch.from_numpy(K).cuda(), torch.from_numpy(ef).cuda(),
-                        int(ef.max()), K, torch.from_numpy(off).cuda(), int(K.sum())))
-    out = {}
+    modes = {"plain": fg.MODE_PLAIN, "finger": fg.MODE_FINGER}
+    curves, choice = _sweep(ix, qu, gt[:nu], c.K, modes, c.ef_grid, nu)
+    uni = {}
     ck = None
-    for name, mode in (("plain", fg.MODE_PLAIN), ("finger", fg.MODE_FINGER)):
+    for name, mode in modes.items():
+        v, ms, _, k = _timed(ix, qu, c.K, choice[name][0], mode, args.steps, args.warmup, nu,
+                             Clocks(0) if name == "finger" else None)
+        uni[name] = (v, ms)
+        ck = k or ck
+    roof, cpq = _leg_roofline(fg, ix, qu, c, choice["finger"][0], fg.MODE_FINGER, uni["finger"][1])
+    alpha = choice["finger"][0] / choice["plain"][0]
+
+    plan = workloads.uneven_batches(nq)
+    out = {}
+    for name, mode in modes.items():
+        scale = alpha if name == "finger" else 1.0
+        batches = []
+        for start, size, K, ef in plan:
+            efm = np.minimum(np.maximum(np.ceil(ef * scale), K), 1000).astype(np.int32)
+            off = np.zeros(size, np.int64)
+            off[1:] = np.cumsum(K.astype(np.int64))[:-1]
+            batches.append((start, size, torch.from_numpy(K).cuda(), torch.from_numpy(efm).cuda(),
+                            int(efm.max()), K, torch.from_numpy(off).cuda(), int(K.sum())))
         ix.set_mode(mode, 5)
         # autotune each ef bucket on a sample batch at the bucket's largest ef
-        for b in (16, 32, 64, 128, 256, 512):
-            if b >= 10:
-                ix.autotune(q[:2048], 10, min(b, 400))
+        for bkt in (16, 32, 64, 128, 256, 512, 1024):
+            lo = bkt // 2 if bkt > 16 else 10
+            if any(lo < b[4] <= bkt for b in batches):
+                ix.autotune(q[:2048], 10, min(bkt, 1000))
         for start, size, Kt, eft, mx, _, off, tot in batches:   # warm-up pass: captures graphs
             ix.search_batch(q[start:start + size], Kt, eft, max_ef=mx, offsets=off, total=tot)
         torch.cuda.synchronize()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in batches]
-        clocks = Clocks(0) if name == "finger" else None
-        if clocks:
-            clocks.start()
         g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         g0.record(stream)
         results = []
@@ -505,27 +556,37 @@ def leg_batch(args):
             results.append(r_)
         g1.record(stream)
         torch.cuda.synchronize()
-        if clocks:
-            ck = clocks.stop()
         ix.sync()
         total_ms = g0.elapsed_time(g1)
         lat = np.array([a.elapsed_time(b_) for a, b_ in ev])
-        hits, tot = 0, 0
+        hits, tot_k = 0, 0
         for (start, size, Kt, eft, mx, K, _, _), (ids, _, off) in zip(batches, results):
             ids, off = ids.cpu().numpy(), off.cpu().numpy()
             for i in range(size):
                 k = int(K[i])
                 got = ids[off[i]:off[i] + k]
                 hits += len(np.intersect1d(got, gt[start + i, :k]))
-                tot += k
-        out[name] = {"qps": nq / (total_ms / 1000), "total_ms": total_ms,
+                tot_k += k
+        out[name] = {"qps": nq / (total_ms / 1000), "total_ms": total_ms, "ef_scale": scale,
                      "p50_batch_ms": float(np.percentile(lat, 50)),
-                     "p99_batch_ms": float(np.percentile(lat, 99)), "recall": hits / tot}
-    extra = {"impl_mode": "uneven batches, graph-captured persistent launch, autotuned",
-             "batches": len(batches), "plain": out["plain"], "finger": out["finger"],
-             "finger_over_plain": out["finger"]["qps"] / out["plain"]["qps"], "setup_s": setup,
-             "gpu_launches": len(batches)}
-    return _line(c, n, nq, out["finger"]["qps"], out["finger"]["total_ms"], 1, 1, extra, ck)
+                     "p99_batch_ms": float(np.percentile(lat, 99)), "recall": hits / tot_k}
+    extra = {"impl_mode": "FINGER; uniform K=10 sweep + uneven batches (graph-captured, "
+                          "autotuned persistent launch)",
+             "finger_qps": uni["finger"][0], "plain_qps": uni["plain"][0],
+             "finger_over_plain": uni["finger"][0] / uni["plain"][0],
+             "ef": {k: v[0] for k, v in choice.items()},
+             "recall": {k: v[1] for k, v in choice.items()},
+             "roofline": roof, "counters_per_query": cpq,
+             "qps_at_recall_interp": {k: qps_at(v) for k, v in curves.items()},
+             "stream": {"queries": nq, "batches": len(plan), "plain": out["plain"],
+                        "finger": out["finger"],
+                        "finger_over_plain": out["finger"]["qps"] / out["plain"]["qps"]},
+             "setup_s": setup,
+             "curves": {k: [[e, round(r_, 4), round(v_, 1)] for e, r_, v_ in pts]
+                        for k, pts in curves.items()}}
+    line = _line(c, n, nu, uni["finger"][0], uni["finger"][1], args.steps, args.warmup, extra, ck)
+    line["config"]["stream_nq"] = nq
+    return line
 
 
 def main():

@@ -131,7 +131,15 @@ typedef struct {
     const double* stats_host; /* optional {mu, sigma, mu_hat, sigma_hat, eps};
                                  NULL = computed from the sampled pairs */
     int build_lp;             /* also build BF16 rows and FP8-e4m3 codes (mode LP) */
+    int flags;                /* ablations of Sec. 4.4, 0 = the full method:
+                                 FINGER_BUILD_NO_MATCHING: t = t_hat + eps
+                                 (stored as mu = mu_hat = 0, sigma = sigma_hat
+                                 = 1; eps = mean |Y - X|);
+                                 FINGER_BUILD_NO_EPS: eps = 0 */
 } finger_build_params;
+
+#define FINGER_BUILD_NO_MATCHING 1
+#define FINGER_BUILD_NO_EPS 2
 
 /* Algorithm 2 and Supplementary G on the device.  For every node c with at
  * least two layer-0 neighbours a pair (d, d') is drawn with the counter rule
@@ -146,6 +154,18 @@ typedef struct {
  * deviations) and eps of Algorithm 2 over the drawn pairs, with
  * X = cos(d_res, d'_res), Y = cos(P d_res, P d'_res).  Synchronous. */
 finger_status finger_build_tables(finger_index* ix, const finger_build_params* p, void* stream);
+
+/* Rank rule of Supplementary E, then finger_build_tables at the chosen rank.
+ * The candidate ranks are r_step, 2 r_step, ... capped at r_max (<= 64 and
+ * <= m); the chosen rank is the first whose correlation of X and Y over the
+ * drawn pairs (Pearson, population moments) is >= threshold, else the last
+ * candidate.  All candidates use prefixes of the same SVD basis (p->basis_host
+ * must be NULL; p->r is ignored; the other fields apply to the final build).
+ * *r_out gets the rank; corr_trace (may be NULL) gets one correlation per
+ * candidate tried, ceil(r_max / r_step) entries at most.  Synchronous. */
+finger_status finger_select_rank(finger_index* ix, const finger_build_params* p,
+                                 double threshold, int r_step, int r_max, int* r_out,
+                                 double* corr_trace, void* stream);
 
 /* Copy FINGER tables to host buffers (any may be NULL):
  *   P r x m, stats[5] as above, node_proj n x r (P c), edge_u (n*deg0) x r,
@@ -301,6 +321,8 @@ typedef struct {
     int32_t device_error;   /* latched FINGER_ERR_* from kernels, 0 if none */
     double mu, sigma, mu_hat, sigma_hat, eps; /* matching statistics */
     double build_ms;        /* wall time of the last table build */
+    double corr;            /* correlation of X and Y over the drawn pairs
+                               (Supplementary E), NaN before a build */
 } finger_stats;
 
 /* Synchronise the index's device and return the latched kernel status. */

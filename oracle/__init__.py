@@ -159,6 +159,7 @@ class FingerParams:
     mu_hat: float
     sigma_hat: float
     eps: float
+    corr: float = float("nan")      # Pearson correlation of X and Y over S (Supp. E)
 
     def stats(self):
         return np.array([self.mu, self.sigma, self.mu_hat, self.sigma_hat, self.eps], np.float64)
@@ -266,38 +267,92 @@ def pair_cosines(X, pairs: np.ndarray, P: np.ndarray, chunk: int = 1 << 16):
     return np.concatenate(xs), np.concatenate(ys)
 
 
-def matching_stats(Xc: np.ndarray, Yc: np.ndarray):
-    """mu, sigma (std), mu_hat, sigma_hat, eps of Algorithm 2 (population 1/N)."""
-    mu, muh = float(np.mean(Xc)), float(np.mean(Yc))
-    sigma = float(np.sqrt(np.mean((Xc - mu) ** 2)))
-    sigmah = float(np.sqrt(np.mean((Yc - muh) ** 2)))
+def matching_stats(Xc: np.ndarray, Yc: np.ndarray, matching: bool = True, use_eps: bool = True):
+    """mu, sigma (std), mu_hat, sigma_hat, eps of Algorithm 2 (population 1/N).
+
+    Ablations of Sec. 4.4: ``matching=False`` keeps the low-rank cosine as it
+    is (the map becomes t = t_hat + eps, returned as mu = mu_hat = 0,
+    sigma = sigma_hat = 1) and eps is then the mean |Y - X|;
+    ``use_eps=False`` drops the error-correction term (eps = 0)."""
+    if matching:
+        mu, muh = float(np.mean(Xc)), float(np.mean(Yc))
+        sigma = float(np.sqrt(np.mean((Xc - mu) ** 2)))
+        sigmah = float(np.sqrt(np.mean((Yc - muh) ** 2)))
+    else:
+        mu, sigma, muh, sigmah = 0.0, 1.0, 0.0, 1.0
     ratio = sigma / sigmah if sigmah > 0 else 0.0
-    eps = float(np.mean(np.abs((Yc - muh) * ratio + mu - Xc)))
+    eps = float(np.mean(np.abs((Yc - muh) * ratio + mu - Xc))) if use_eps else 0.0
     return mu, sigma, muh, sigmah, eps
 
 
+def correlation(Xc: np.ndarray, Yc: np.ndarray) -> float:
+    """Pearson correlation of the true and the low-rank residual cosines over
+    the sampled pairs, the quantity of the rank rule (Supplementary E):
+    population covariance over the product of the population standard
+    deviations; 0 when either is 0."""
+    dx, dy = Xc - np.mean(Xc), Yc - np.mean(Yc)
+    den = np.sqrt(np.mean(dx * dx) * np.mean(dy * dy))
+    return float(np.mean(dx * dy) / den) if den > 0 else 0.0
+
+
+def _sorted_eigvecs(X, pairs, m, method, chunk):
+    """Left singular vectors of D_res ordered by singular value (columns)."""
+    if method == "svd":
+        D_res = residuals(X, pairs[:, 0], pairs[:, 1])
+        U, _, _ = np.linalg.svd(D_res.T, full_matrices=False)
+        return U
+    G = np.zeros((m, m), np.float64)
+    for lo in range(0, len(pairs), chunk):
+        p = pairs[lo:lo + chunk]
+        R = residuals(X, p[:, 0], p[:, 1])
+        G += R.T @ R
+    w, V = np.linalg.eigh(G)
+    return V[:, np.argsort(-w, kind="stable")]
+
+
 def build_tables(X, g: Graph, r: int, seed: int, samples_per_node: int = 1,
-                 method: str = "auto", chunk: int = 1 << 16):
-    """Algorithm 2: sample S, D_res, SVD -> P, then the matching statistics."""
+                 method: str = "auto", chunk: int = 1 << 16, basis: np.ndarray | None = None,
+                 matching: bool = True, use_eps: bool = True):
+    """Algorithm 2: sample S, D_res, SVD -> P, then the matching statistics.
+
+    ``basis`` (r x m) replaces the SVD basis (the RPLSH comparison of Sec. 4.4
+    passes a random Gaussian matrix); ``matching`` / ``use_eps`` are the
+    ablations of :func:`matching_stats`."""
     pairs = sample_pairs(g.adj0, seed, samples_per_node)
     m = np.asarray(X).shape[1]
     if method == "auto":
         method = "svd" if len(pairs) * m <= 10 ** 8 else "eigh"
-    if method == "svd":
-        D_res = residuals(X, pairs[:, 0], pairs[:, 1])
-        P = basis(D_res, r, "svd")
+    if basis is not None:
+        P = np.ascontiguousarray(_f64(basis)[:r])
     else:
-        G = np.zeros((m, m), np.float64)
-        for lo in range(0, len(pairs), chunk):
-            p = pairs[lo:lo + chunk]
-            R = residuals(X, p[:, 0], p[:, 1])
-            G += R.T @ R
-        w, V = np.linalg.eigh(G)
-        order = np.argsort(-w, kind="stable")
-        P = np.ascontiguousarray(V[:, order[:r]].T)
+        P = np.ascontiguousarray(_sorted_eigvecs(X, pairs, m, method, chunk)[:, :r].T)
     Xc, Yc = pair_cosines(X, pairs, P, chunk)
-    mu, sigma, muh, sigmah, eps = matching_stats(Xc, Yc)
-    return FingerParams(P, mu, sigma, muh, sigmah, eps), pairs
+    mu, sigma, muh, sigmah, eps = matching_stats(Xc, Yc, matching, use_eps)
+    return FingerParams(P, mu, sigma, muh, sigmah, eps, correlation(Xc, Yc)), pairs
+
+
+def select_rank(X, g: Graph, seed: int, threshold: float = 0.7, r_start: int = 8,
+                r_step: int = 8, r_max: int = 64, samples_per_node: int = 1,
+                method: str = "auto", chunk: int = 1 << 16):
+    """Rank rule of Supplementary E: start at r = 8 and add 8 while the
+    correlation of X and Y (Algorithm 2's true and low-rank residual cosines)
+    is below the threshold (0.7); stop at r_max.  The basis of every rank is
+    the top-r prefix of the same singular vectors.  Returns (r, [(r, corr)])."""
+    pairs = sample_pairs(g.adj0, seed, samples_per_node)
+    m = np.asarray(X).shape[1]
+    if method == "auto":
+        method = "svd" if len(pairs) * m <= 10 ** 8 else "eigh"
+    U = _sorted_eigvecs(X, pairs, m, method, chunk)
+    trace = []
+    r = r_start
+    while True:
+        rr = min(r, m, r_max)
+        Xc, Yc = pair_cosines(X, pairs, np.ascontiguousarray(U[:, :rr].T), chunk)
+        c = correlation(Xc, Yc)
+        trace.append((rr, c))
+        if c >= threshold or rr >= min(m, r_max):
+            return rr, trace
+        r += r_step
 
 
 def gram(X, pairs: np.ndarray, chunk: int = 1 << 16) -> np.ndarray:

@@ -43,7 +43,9 @@ class GraphParams(ctypes.Structure):
 class BuildParams(ctypes.Structure):
     _fields_ = [("r", ctypes.c_int), ("seed", ctypes.c_uint64), ("samples_per_node", ctypes.c_int),
                 ("basis_host", ctypes.c_void_p), ("stats_host", ctypes.c_void_p),
-                ("build_lp", ctypes.c_int)]
+                ("build_lp", ctypes.c_int), ("flags", ctypes.c_int)]
+
+BUILD_NO_MATCHING, BUILD_NO_EPS = 1, 2
 
 
 class TrainParams(ctypes.Structure):
@@ -64,7 +66,7 @@ class Stats(ctypes.Structure):
                 ("device_error", ctypes.c_int32), ("mu", ctypes.c_double),
                 ("sigma", ctypes.c_double), ("mu_hat", ctypes.c_double),
                 ("sigma_hat", ctypes.c_double), ("eps", ctypes.c_double),
-                ("build_ms", ctypes.c_double)]
+                ("build_ms", ctypes.c_double), ("corr", ctypes.c_double)]
 
 
 # name -> (restype, argtypes); every symbol include/finger.h declares
@@ -80,6 +82,7 @@ SIGNATURES = {
     "finger_index_load": (_I, [ctypes.c_char_p, _I, _P]),
     "finger_index_free": (None, [_P]),
     "finger_build_tables": (_I, [_P, _P, _P]),
+    "finger_select_rank": (_I, [_P, _P, ctypes.c_double, _I, _I, _P, _P, _P]),
     "finger_get_tables": (_I, [_P, _P, _P, _P, _P, _P]),
     "finger_table_bytes": (_I64, [_I64, _I, _I, _I]),
     "finger_set_mode": (_I, [_P, _I, _I]),
@@ -231,7 +234,12 @@ class Index:
 
     # ------------------------------------------------------------- tables
     def build_tables(self, r: int, seed: int, samples_per_node: int = 1, basis=None, stats=None,
-                     build_lp: bool = False, stream=None):
+                     build_lp: bool = False, matching: bool = True, use_eps: bool = True,
+                     stream=None):
+        """finger_build_tables.  ``basis`` (r x m) replaces the SVD basis (e.g.
+        a random Gaussian matrix: the RPLSH comparison of Sec. 4.4); ``matching``
+        and ``use_eps`` False are the ablations of FINGER_BUILD_NO_MATCHING and
+        FINGER_BUILD_NO_EPS."""
         keep = []
         bp = None
         sp = None
@@ -243,9 +251,22 @@ class Index:
             s = np.ascontiguousarray(stats, dtype=np.float64)
             keep.append(s)
             sp = _np_ptr(s)
-        p = BuildParams(r, seed, samples_per_node, bp, sp, int(build_lp))
+        flags = (0 if matching else BUILD_NO_MATCHING) | (0 if use_eps else BUILD_NO_EPS)
+        p = BuildParams(r, seed, samples_per_node, bp, sp, int(build_lp), flags)
         _check(self._lib.finger_build_tables(self._h, ctypes.byref(p), _stream_ptr(stream)),
                "finger_build_tables")
+
+    def select_rank(self, seed: int, threshold: float = 0.7, r_step: int = 8, r_max: int = 64,
+                    samples_per_node: int = 1, build_lp: bool = False, stream=None):
+        """finger_select_rank: rank rule of Supplementary E, then the tables at
+        that rank.  Returns (r, [correlation of each candidate tried])."""
+        p = BuildParams(0, seed, samples_per_node, None, None, int(build_lp), 0)
+        r_out = ctypes.c_int()
+        trace = np.full(-(-r_max // r_step), np.nan)
+        _check(self._lib.finger_select_rank(self._h, ctypes.byref(p), ctypes.c_double(threshold),
+                                            r_step, r_max, ctypes.byref(r_out), _np_ptr(trace),
+                                            _stream_ptr(stream)), "finger_select_rank")
+        return r_out.value, [float(x) for x in trace if x == x]
 
     def get_tables(self) -> dict:
         i = self.info()

@@ -357,15 +357,17 @@ void finger_index_free(finger_index* ix) {
     void* ptrs[] = {ix->X, ix->xnorm2, ix->adj0, ix->up_off, ix->up_adj, ix->P, ix->Pc,
                     ix->edge_u, ix->edge_s, ix->Xh, ix->edge_q, ix->W1, ix->W2, ix->w3,
                     ix->b1, ix->b2, ix->work, ix->err, ix->cnt, ix->bitmap, ix->spill,
-                    ix->stage_q, ix->stage_ids, ix->stage_d};
+                    ix->stage_q, ix->stage_ids, ix->stage_d, ix->eig_G, ix->eig_V};
     for (void* p : ptrs) cudaFree(p);
     delete ix;
 }
 
 static void drop_tables(finger_index* ix) {
     void* ptrs[] = {ix->P, ix->Pc, ix->edge_u, ix->edge_s, ix->Xh, ix->edge_q,
-                    ix->W1, ix->W2, ix->w3, ix->b1, ix->b2};
+                    ix->W1, ix->W2, ix->w3, ix->b1, ix->b2, ix->eig_G, ix->eig_V};
     for (void* p : ptrs) cudaFree(p);
+    ix->eig_G = ix->eig_V = nullptr;
+    ix->corr = 0.0 / 0.0;
     ix->P = ix->Pc = ix->edge_u = nullptr;
     ix->edge_s = nullptr;
     ix->Xh = nullptr;
@@ -502,6 +504,18 @@ finger_status finger_build_tables(finger_index* ix, const finger_build_params* p
     ix->has_mlp = 0;
     ix->h_mlp.clear();
     return build_tables(ix, p, (cudaStream_t)stream);
+}
+
+finger_status finger_select_rank(finger_index* ix, const finger_build_params* p, double threshold,
+                                 int r_step, int r_max, int* r_out, double* corr_trace,
+                                 void* stream) {
+    if (!ix || !p) return FINGER_ERR_INVALID_ARG;
+    DeviceGuard g(ix->device);
+    fg_drop_captures(ix);
+    ix->tuned.clear();
+    ix->has_mlp = 0;
+    ix->h_mlp.clear();
+    return select_rank(ix, p, threshold, r_step, r_max, r_out, corr_trace, (cudaStream_t)stream);
 }
 
 finger_status finger_get_tables(const finger_index* ix, float* P, double* stats, float* node_proj,
@@ -653,6 +667,7 @@ finger_status finger_get_stats(finger_index* ix, finger_stats* out) {
     out->sigma_hat = ix->stats[3];
     out->eps = ix->stats[4];
     out->build_ms = ix->build_ms;
+    out->corr = ix->corr;
     return FINGER_OK;
 }
 

@@ -114,6 +114,8 @@ size_t knn_smem(int K);
 finger_status build_graph(finger_index* ix, const finger_graph_params* p, cudaStream_t s);
 // FINGER tables (tables.cu)
 finger_status build_tables(finger_index* ix, const finger_build_params* p, cudaStream_t s);
+finger_status select_rank(finger_index* ix, const finger_build_params* p, double threshold,
+                          int r_step, int r_max, int* r_out, double* corr_trace, cudaStream_t s);
 cudaError_t launch_xnorm2(const float4* X, int64_t n, int m4, float* out, cudaStream_t s);
 cudaError_t launch_to_bf16(const float* X, int64_t n, int m_pad, int m8, __nv_bfloat16* out,
                            cudaStream_t s);
@@ -142,6 +144,13 @@ struct finger_index {
     float* edge_u = nullptr;
     float2* edge_s = nullptr;
     double stats[5] = {0, 0, 0, 0, 0};
+    double corr = 0.0 / 0.0;
+    // eigen-decomposition of the D_res Gram matrix (diagonalised G and its
+    // eigenvectors), kept for rebuilds at another rank with the same draw
+    double* eig_G = nullptr;
+    double* eig_V = nullptr;
+    uint64_t eig_seed = 0;
+    int eig_spn = 0;
     // LP tables
     __nv_bfloat16* Xh = nullptr;
     uint8_t* edge_q = nullptr;

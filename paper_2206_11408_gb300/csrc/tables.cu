@@ -459,9 +459,90 @@ __global__ void k_pair_cos(const float4* X, int m4, const uint32_t* adj0, int de
     }
 }
 
+// Rank rule (Supplementary E): X = cos(d_res, d'_res) and, for every
+// candidate rank r_i = min((i+1) step, r_max), Y_i = cos of the projections on
+// the first r_i basis rows, in one pass (warp per pair; both residuals staged
+// in shared memory, one warp reduction per basis row).  Y is [nr][np].
+constexpr int PREFIX_WARPS = 4;
+__global__ void __launch_bounds__(32 * PREFIX_WARPS)
+    k_pair_cos_prefix(const float4* X, int m4, const float* xn2, const uint32_t* adj0, int deg0,
+                      const int3* pairs, int64_t np, const float* P, int m_pad, int r_max,
+                      int step, double* Xc, double* Yk) {
+    extern __shared__ float4 res_s[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int64_t w = (int64_t)blockIdx.x * PREFIX_WARPS + wib;
+    if (w >= np) return;
+    const int nr = (r_max + step - 1) / step;
+    const int3 p = pairs[w];
+    if (p.x < 0) {
+        if (lane == 0) {
+            Xc[w] = NAN;
+            for (int i = 0; i < nr; ++i) Yk[(int64_t)i * np + w] = NAN;
+        }
+        return;
+    }
+    float4* r1 = res_s + (size_t)wib * 2 * m4;
+    float4* r2 = r1 + m4;
+    const uint32_t d1 = adj0[(int64_t)p.x * deg0 + p.y], d2 = adj0[(int64_t)p.x * deg0 + p.z];
+    float cd1 = 0.f, cd2 = 0.f;
+    for (int k = lane; k < m4; k += 32) {
+        const float4 c = X[(int64_t)p.x * m4 + k];
+        const float4 x = X[(int64_t)d1 * m4 + k];
+        const float4 y = X[(int64_t)d2 * m4 + k];
+        cd1 += c.x * x.x + c.y * x.y + c.z * x.z + c.w * x.w;
+        cd2 += c.x * y.x + c.y * y.y + c.z * y.z + c.w * y.w;
+    }
+    cd1 = wsum(cd1);
+    cd2 = wsum(cd2);
+    const float cc = xn2[p.x];
+    const float b1 = cc > 0.f ? cd1 / cc : 0.f, b2 = cc > 0.f ? cd2 / cc : 0.f;
+    float s12 = 0.f, s11 = 0.f, s22 = 0.f;
+    for (int k = lane; k < m4; k += 32) {
+        const float4 c = X[(int64_t)p.x * m4 + k];
+        const float4 x = X[(int64_t)d1 * m4 + k];
+        const float4 y = X[(int64_t)d2 * m4 + k];
+        const float4 a = make_float4(x.x - b1 * c.x, x.y - b1 * c.y, x.z - b1 * c.z, x.w - b1 * c.w);
+        const float4 b = make_float4(y.x - b2 * c.x, y.y - b2 * c.y, y.z - b2 * c.z, y.w - b2 * c.w);
+        r1[k] = a;
+        r2[k] = b;
+        s12 += a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w;
+        s11 += a.x * a.x + a.y * a.y + a.z * a.z + a.w * a.w;
+        s22 += b.x * b.x + b.y * b.y + b.z * b.z + b.w * b.w;
+    }
+    s12 = wsum(s12);
+    s11 = wsum(s11);
+    s22 = wsum(s22);
+    if (lane == 0) {
+        const double den = sqrt((double)s11) * sqrt((double)s22);
+        Xc[w] = den > 0 ? (double)s12 / den : 0.0;
+    }
+    __syncwarp();
+    const float4* P4 = reinterpret_cast<const float4*>(P);
+    const int mp4 = m_pad / 4;
+    double t12 = 0, t11 = 0, t22 = 0;
+    for (int k = 0; k < r_max; ++k) {
+        float u = 0.f, v = 0.f;
+        for (int j = lane; j < m4; j += 32) {
+            const float4 pk = P4[(int64_t)k * mp4 + j];
+            const float4 a = r1[j], b = r2[j];
+            u += pk.x * a.x + pk.y * a.y + pk.z * a.z + pk.w * a.w;
+            v += pk.x * b.x + pk.y * b.y + pk.z * b.z + pk.w * b.w;
+        }
+        u = wsum(u);
+        v = wsum(v);
+        t12 += (double)u * v;
+        t11 += (double)u * u;
+        t22 += (double)v * v;
+        if (lane == 0 && ((k + 1) % step == 0 || k + 1 == r_max)) {
+            const double den = sqrt(t11) * sqrt(t22);
+            Yk[(int64_t)(k / step) * np + w] = den > 0 ? t12 / den : 0.0;
+        }
+    }
+}
+
 // deterministic reductions: per-block partial sums, then one block sums them
-// mode 0: sum X, sum Y, count;  mode 1: sum (X-mu)^2, sum (Y-muh)^2;
-// mode 2: sum |(Y - muh) ratio + mu - X|
+// mode 0: sum X, sum Y, count;  mode 1: sum (X-mu)^2, sum (Y-muh)^2,
+// sum (X-mu)(Y-muh);  mode 2: sum |(Y - muh) ratio + mu - X|
 __global__ void k_sum_part(const double* Xc, const double* Yc, int64_t np, int mode, double mu,
                            double muh, double ratio, double* part) {
     __shared__ double s[3][256];
@@ -477,6 +558,7 @@ __global__ void k_sum_part(const double* Xc, const double* Yc, int64_t np, int m
         } else if (mode == 1) {
             a += (x - mu) * (x - mu);
             b += (y - muh) * (y - muh);
+            c += (x - mu) * (y - muh);
         } else {
             a += fabs((y - muh) * ratio + mu - x);
         }
@@ -575,11 +657,120 @@ namespace fg {
         }                             \
     } while (0)
 
+// Eigen-decomposition of G = sum over the drawn pairs of d_res d_res^T, kept
+// in the index (diagonalised G and eigenvectors V) for the (seed, spn) draw it
+// was computed from; a rebuild at another rank reuses it.
+static finger_status ensure_eigen(finger_index* ix, const int3* pairs, int64_t np, uint64_t seed,
+                                  int spn, cudaStream_t s) {
+    if (ix->eig_G && ix->eig_seed == seed && ix->eig_spn == spn) return FINGER_OK;
+    cudaFree(ix->eig_G);
+    cudaFree(ix->eig_V);
+    ix->eig_G = ix->eig_V = nullptr;
+    const int m = ix->m, m4 = ix->m4, deg0 = ix->deg0;
+    finger_status status = FINGER_OK;
+    double* G = dalloc<double>((size_t)m * m);
+    double* V = dalloc<double>((size_t)m * m);
+    const int jb = std::max(1, std::min(ix->num_sms, (m + 63) / 64 * 4));
+    double* red = dalloc<double>(2 * (size_t)jb);
+    double2* rot = dalloc<double2>((size_t)m);
+    int2* pr = dalloc<int2>((size_t)m);
+    int* sweeps = dalloc<int>(1);
+    float* bq = dalloc<float>((size_t)np);
+    if (!G || !V || !red || !rot || !pr || !sweeps || !bq) {
+        status = FINGER_ERR_OOM;
+        goto done;
+    }
+    k_pair_b<<<(unsigned)((np * 32 + 255) / 256), 256, 0, s>>>(
+        reinterpret_cast<const float4*>(ix->X), m4, ix->xnorm2, ix->adj0, deg0, pairs, np, bq);
+    CKT(cudaGetLastError());
+    CKT(cudaMemsetAsync(G, 0, sizeof(double) * m * m, s));
+    {
+        const dim3 grid((m + GT - 1) / GT, (m + GT - 1) / GT, (unsigned)((np + GCHUNK - 1) / GCHUNK));
+        k_gram<<<grid, 256, 0, s>>>(ix->X, ix->m_pad, m, ix->adj0, deg0, pairs, bq, np, G);
+        CKT(cudaGetLastError());
+    }
+    {
+        std::vector<double> I((size_t)m * m, 0.0);
+        for (int i = 0; i < m; ++i) I[(size_t)i * m + i] = 1.0;
+        CKT(cudaMemcpyAsync(V, I.data(), sizeof(double) * I.size(), cudaMemcpyHostToDevice, s));
+        int max_sweeps = 40;
+        double tol = 1e-15;
+        int mm = m;
+        void* args[] = {&G, &V, (void*)&mm, &rot, &pr, &red, &max_sweeps, &tol, &sweeps};
+        CKT(cudaLaunchCooperativeKernel((void*)k_jacobi, dim3(jb), dim3(256), args, 0, s));
+        CKT(cudaStreamSynchronize(s));
+    }
+    ix->eig_G = G;
+    ix->eig_V = V;
+    ix->eig_seed = seed;
+    ix->eig_spn = spn;
+    G = V = nullptr;
+done:
+    cudaFree(G);
+    cudaFree(V);
+    cudaFree(red);
+    cudaFree(rot);
+    cudaFree(pr);
+    cudaFree(sweeps);
+    cudaFree(bq);
+    return status;
+}
+
+static finger_status run_sums(const double* Xc, const double* Yc, int64_t np, int mode, double mu,
+                              double muh, double ratio, double* part, double* sums, double h[3],
+                              cudaStream_t s) {
+    const int nbp = 512;
+    k_sum_part<<<nbp, 256, 0, s>>>(Xc, Yc, np, mode, mu, muh, ratio, part);
+    k_sum_final<<<1, 32, 0, s>>>(part, nbp, sums);
+    if (cudaMemcpyAsync(h, sums, 3 * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return FINGER_ERR_CUDA;
+    return FINGER_OK;
+}
+
+// Algorithm 2's statistics over the pairs (X, Y): mu, sigma, mu_hat, sigma_hat
+// (standard deviations, 1/N), eps, and the correlation of X and Y.  flags:
+// FINGER_BUILD_NO_MATCHING keeps t_hat (mu = mu_hat = 0, sigma = sigma_hat =
+// 1, eps = mean |Y - X|); FINGER_BUILD_NO_EPS sets eps = 0.
+static finger_status pair_stats(const double* Xc, const double* Yc, int64_t np, int flags,
+                                double* part, double* sums, double st[5], double* corr,
+                                cudaStream_t s) {
+    double h[3];
+    finger_status status = run_sums(Xc, Yc, np, 0, 0, 0, 0, part, sums, h, s);
+    if (status != FINGER_OK) return status;
+    const double N = h[2] > 0 ? h[2] : 1.0;
+    const double mu = h[0] / N, muh = h[1] / N;
+    status = run_sums(Xc, Yc, np, 1, mu, muh, 0, part, sums, h, s);
+    if (status != FINGER_OK) return status;
+    const double sigma = sqrt(h[0] / N), sigmah = sqrt(h[1] / N);
+    *corr = (h[0] > 0 && h[1] > 0) ? h[2] / sqrt(h[0] * h[1]) : 0.0;
+    if (flags & FINGER_BUILD_NO_MATCHING) {
+        st[0] = 0.0;
+        st[1] = 1.0;
+        st[2] = 0.0;
+        st[3] = 1.0;
+    } else {
+        st[0] = mu;
+        st[1] = sigma;
+        st[2] = muh;
+        st[3] = sigmah;
+    }
+    st[4] = 0.0;
+    if (!(flags & FINGER_BUILD_NO_EPS)) {
+        const double ratio = st[3] > 0 ? st[1] / st[3] : 0.0;
+        status = run_sums(Xc, Yc, np, 2, st[0], st[2], ratio, part, sums, h, s);
+        if (status != FINGER_OK) return status;
+        st[4] = h[0] / N;
+    }
+    return FINGER_OK;
+}
+
 finger_status build_tables(finger_index* ix, const finger_build_params* p, cudaStream_t s) {
     const auto t0 = std::chrono::steady_clock::now();
     if (!ix->adj0) return FINGER_ERR_NOT_BUILT;
     const int r = p->r;
     if (r < 1 || r > MAX_R || r > ix->m) return FINGER_ERR_INVALID_ARG;
+    if (p->flags & ~(FINGER_BUILD_NO_MATCHING | FINGER_BUILD_NO_EPS)) return FINGER_ERR_INVALID_ARG;
     const int spn = p->samples_per_node > 0 ? p->samples_per_node : 1;
     const int64_t n = ix->n;
     const int m = ix->m, m_pad = ix->m_pad, m4 = ix->m4, deg0 = ix->deg0;
@@ -588,30 +779,25 @@ finger_status build_tables(finger_index* ix, const finger_build_params* p, cudaS
     const int64_t ne = n * deg0;
     finger_status status = FINGER_OK;
     int3* pairs = nullptr;
-    float* bq = nullptr;
-    double *G = nullptr, *V = nullptr, *red = nullptr, *evals = nullptr;
-    double2* rot = nullptr;
-    int2* pr = nullptr;
-    int* sweeps = nullptr;
+    double* evals = nullptr;
     double *Xc = nullptr, *Yc = nullptr, *part = nullptr, *sums = nullptr;
     float* P = dalloc<float>((size_t)r_pad * m_pad);
     float* Pc = dalloc<float>((size_t)n * r_pad);
     float* edge_u = dalloc<float>((size_t)ne * r_pad);
     float2* edge_s = dalloc<float2>((size_t)ne);
     double st[5] = {0, 0, 0, 0, 0};
-    double h[3];
-    const int nbp = 512;
+    double corr = 0.0;
     if (!P || !Pc || !edge_u || !edge_s) {
         status = FINGER_ERR_OOM;
         goto done;
     }
     pairs = dalloc<int3>((size_t)np);
-    bq = dalloc<float>((size_t)np);
     Xc = dalloc<double>((size_t)np);
     Yc = dalloc<double>((size_t)np);
-    part = dalloc<double>(3 * nbp);
+    part = dalloc<double>(3 * 512);
     sums = dalloc<double>(3);
-    if (!pairs || !bq || !Xc || !Yc || !part || !sums) {
+    evals = dalloc<double>((size_t)m);
+    if (!pairs || !Xc || !Yc || !part || !sums || !evals) {
         status = FINGER_ERR_OOM;
         goto done;
     }
@@ -624,40 +810,11 @@ finger_status build_tables(finger_index* ix, const finger_build_params* p, cudaS
         CKT(cudaMemcpyAsync(P, hp.data(), sizeof(float) * hp.size(), cudaMemcpyHostToDevice, s));
         CKT(cudaStreamSynchronize(s));
     } else {
-        // D_res Gram matrix and its eigenvectors
-        G = dalloc<double>((size_t)m * m);
-        V = dalloc<double>((size_t)m * m);
-        const int jb = std::max(1, std::min(ix->num_sms, (m + 63) / 64 * 4));
-        red = dalloc<double>(2 * (size_t)jb);
-        rot = dalloc<double2>((size_t)m);
-        pr = dalloc<int2>((size_t)m);
-        sweeps = dalloc<int>(1);
-        evals = dalloc<double>((size_t)m);
-        if (!G || !V || !red || !rot || !pr || !sweeps || !evals) {
-            status = FINGER_ERR_OOM;
-            goto done;
-        }
-        k_pair_b<<<(unsigned)((np * 32 + 255) / 256), 256, 0, s>>>(
-            reinterpret_cast<const float4*>(ix->X), m4, ix->xnorm2, ix->adj0, deg0, pairs, np, bq);
+        status = ensure_eigen(ix, pairs, np, p->seed, spn, s);
+        if (status != FINGER_OK) goto done;
+        k_pick_basis<<<1, 256, sizeof(int) * m, s>>>(ix->eig_G, ix->eig_V, m, r, r_pad, m_pad, P,
+                                                     evals);
         CKT(cudaGetLastError());
-        CKT(cudaMemsetAsync(G, 0, sizeof(double) * m * m, s));
-        {
-            const dim3 grid((m + GT - 1) / GT, (m + GT - 1) / GT, (unsigned)((np + GCHUNK - 1) / GCHUNK));
-            k_gram<<<grid, 256, 0, s>>>(ix->X, m_pad, m, ix->adj0, deg0, pairs, bq, np, G);
-            CKT(cudaGetLastError());
-        }
-        {
-            std::vector<double> I((size_t)m * m, 0.0);
-            for (int i = 0; i < m; ++i) I[(size_t)i * m + i] = 1.0;
-            CKT(cudaMemcpyAsync(V, I.data(), sizeof(double) * I.size(), cudaMemcpyHostToDevice, s));
-            int max_sweeps = 40;
-            double tol = 1e-15;
-            void* args[] = {&G, &V, (void*)&m, &rot, &pr, &red, &max_sweeps, &tol, &sweeps};
-            CKT(cudaLaunchCooperativeKernel((void*)k_jacobi, dim3(jb), dim3(256), args, 0, s));
-            k_pick_basis<<<1, 256, sizeof(int) * m, s>>>(G, V, m, r, r_pad, m_pad, P, evals);
-            CKT(cudaGetLastError());
-            CKT(cudaStreamSynchronize(s));
-        }
     }
     {
         const dim3 grid((unsigned)((n + 63) / 64), (r_pad + 63) / 64);
@@ -668,35 +825,14 @@ finger_status build_tables(finger_index* ix, const finger_build_params* p, cudaS
                                                             m4, ix->xnorm2, ix->adj0, n, deg0, Pc,
                                                             r_pad, edge_u, edge_s);
     CKT(cudaGetLastError());
-    if (p->stats_host) {
+    k_pair_cos<<<(unsigned)((np * 32 + 255) / 256), 256, 0, s>>>(
+        reinterpret_cast<const float4*>(ix->X), m4, ix->adj0, deg0, pairs, np, edge_u, edge_s,
+        r_pad, Xc, Yc);
+    CKT(cudaGetLastError());
+    status = pair_stats(Xc, Yc, np, p->flags, part, sums, st, &corr, s);
+    if (status != FINGER_OK) goto done;
+    if (p->stats_host)
         for (int i = 0; i < 5; ++i) st[i] = p->stats_host[i];
-    } else {
-        k_pair_cos<<<(unsigned)((np * 32 + 255) / 256), 256, 0, s>>>(
-            reinterpret_cast<const float4*>(ix->X), m4, ix->adj0, deg0, pairs, np, edge_u, edge_s,
-            r_pad, Xc, Yc);
-        CKT(cudaGetLastError());
-        k_sum_part<<<nbp, 256, 0, s>>>(Xc, Yc, np, 0, 0, 0, 0, part);
-        k_sum_final<<<1, 32, 0, s>>>(part, nbp, sums);
-        CKT(cudaMemcpyAsync(h, sums, sizeof(h), cudaMemcpyDeviceToHost, s));
-        CKT(cudaStreamSynchronize(s));
-        const double N = h[2] > 0 ? h[2] : 1.0;
-        const double mu = h[0] / N, muh = h[1] / N;
-        k_sum_part<<<nbp, 256, 0, s>>>(Xc, Yc, np, 1, mu, muh, 0, part);
-        k_sum_final<<<1, 32, 0, s>>>(part, nbp, sums);
-        CKT(cudaMemcpyAsync(h, sums, sizeof(h), cudaMemcpyDeviceToHost, s));
-        CKT(cudaStreamSynchronize(s));
-        const double sigma = sqrt(h[0] / N), sigmah = sqrt(h[1] / N);
-        const double ratio = sigmah > 0 ? sigma / sigmah : 0.0;
-        k_sum_part<<<nbp, 256, 0, s>>>(Xc, Yc, np, 2, mu, muh, ratio, part);
-        k_sum_final<<<1, 32, 0, s>>>(part, nbp, sums);
-        CKT(cudaMemcpyAsync(h, sums, sizeof(h), cudaMemcpyDeviceToHost, s));
-        CKT(cudaStreamSynchronize(s));
-        st[0] = mu;
-        st[1] = sigma;
-        st[2] = muh;
-        st[3] = sigmah;
-        st[4] = h[0] / N;
-    }
     CKT(cudaStreamSynchronize(s));
     // reduced-precision tables
     cudaFree(ix->Xh);
@@ -705,13 +841,6 @@ finger_status build_tables(finger_index* ix, const finger_build_params* p, cudaS
     ix->edge_q = nullptr;
 done:
     cudaFree(pairs);
-    cudaFree(bq);
-    cudaFree(G);
-    cudaFree(V);
-    cudaFree(red);
-    cudaFree(rot);
-    cudaFree(pr);
-    cudaFree(sweeps);
     cudaFree(evals);
     cudaFree(Xc);
     cudaFree(Yc);
@@ -735,6 +864,7 @@ done:
     ix->r = r;
     ix->r_pad = r_pad;
     for (int i = 0; i < 5; ++i) ix->stats[i] = st[i];
+    ix->corr = corr;
     if (p->build_lp && lp_rebuild(ix) != cudaSuccess) {
         cudaGetLastError();
         return FINGER_ERR_CUDA;
@@ -742,6 +872,77 @@ done:
     ix->build_ms =
         std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     return FINGER_OK;
+}
+
+// Rank rule of Supplementary E (see finger_select_rank in finger.h).
+finger_status select_rank(finger_index* ix, const finger_build_params* p, double threshold,
+                          int r_step, int r_max, int* r_out, double* corr_trace, cudaStream_t s) {
+    if (!ix->adj0) return FINGER_ERR_NOT_BUILT;
+    if (p->basis_host || r_step < 1 || r_max < 1 || r_max > MAX_R || r_max > ix->m || !r_out ||
+        !(threshold == threshold))
+        return FINGER_ERR_INVALID_ARG;
+    const int spn = p->samples_per_node > 0 ? p->samples_per_node : 1;
+    const int64_t n = ix->n, np = n * spn;
+    const int m = ix->m, m_pad = ix->m_pad, deg0 = ix->deg0;
+    const int rp_max = (r_max + 3) & ~3;
+    const int nr = (r_max + r_step - 1) / r_step;
+    finger_status status = FINGER_OK;
+    int3* pairs = dalloc<int3>((size_t)np);
+    double* Xc = dalloc<double>((size_t)np);
+    double* Yk = dalloc<double>((size_t)np * nr);
+    double* part = dalloc<double>(3 * 512);
+    double* sums = dalloc<double>(3);
+    double* evals = dalloc<double>((size_t)m);
+    float* P = dalloc<float>((size_t)rp_max * m_pad);
+    int chosen = std::min(nr * r_step, r_max);
+    const size_t smem = sizeof(float4) * 2 * (size_t)ix->m4 * PREFIX_WARPS;
+    if (!pairs || !Xc || !Yk || !part || !sums || !evals || !P) {
+        status = FINGER_ERR_OOM;
+        goto done;
+    }
+    if (smem > 200 * 1024) {
+        status = FINGER_ERR_UNSUPPORTED;
+        goto done;
+    }
+    k_sample<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(ix->adj0, n, deg0, p->seed, spn, pairs);
+    CKT(cudaGetLastError());
+    status = ensure_eigen(ix, pairs, np, p->seed, spn, s);
+    if (status != FINGER_OK) goto done;
+    k_pick_basis<<<1, 256, sizeof(int) * m, s>>>(ix->eig_G, ix->eig_V, m, r_max, rp_max, m_pad, P,
+                                                 evals);
+    CKT(cudaGetLastError());
+    if (smem > 48 * 1024)
+        CKT(cudaFuncSetAttribute(k_pair_cos_prefix, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem));
+    k_pair_cos_prefix<<<(unsigned)((np + PREFIX_WARPS - 1) / PREFIX_WARPS), 32 * PREFIX_WARPS, smem,
+                        s>>>(reinterpret_cast<const float4*>(ix->X), ix->m4, ix->xnorm2, ix->adj0,
+                             deg0, pairs, np, P, m_pad, r_max, r_step, Xc, Yk);
+    CKT(cudaGetLastError());
+    for (int i = 0; i < nr; ++i) {
+        double st[5], corr = 0.0;
+        status = pair_stats(Xc, Yk + (size_t)i * np, np, FINGER_BUILD_NO_EPS, part, sums, st, &corr,
+                            s);
+        if (status != FINGER_OK) goto done;
+        if (corr_trace) corr_trace[i] = corr;
+        if (corr >= threshold || i == nr - 1) {
+            chosen = std::min((i + 1) * r_step, r_max);
+            break;
+        }
+    }
+done:
+    cudaFree(pairs);
+    cudaFree(Xc);
+    cudaFree(Yk);
+    cudaFree(part);
+    cudaFree(sums);
+    cudaFree(evals);
+    cudaFree(P);
+    if (status != FINGER_OK) return status;
+    finger_build_params q = *p;
+    q.r = chosen;
+    status = build_tables(ix, &q, s);
+    if (status == FINGER_OK) *r_out = chosen;
+    return status;
 }
 
 }  // namespace fg

@@ -10,6 +10,14 @@ stand-in with the shape of one of them:
     4  n=1M,   m=96,  unit-normalised, 128-cluster Gaussian mixture (DEEP-like)
     5  n=1M,   m=960, per-dim lognormal magnitudes, 32 clusters (GIST-like), L2
 
+Configurations 3-5 give the within-cluster variation the decaying spectrum of
+real embedding and descriptor sets: one covariance shared by all clusters,
+R diag(lambda) R^T with a seeded random orthonormal frame R and a Zipf
+spectrum lambda_i proportional to 1/i, scaled so that the total variance is
+sigma^2 m (for configuration 5 this is the covariance of the log-magnitudes,
+so every coordinate stays lognormal).  Isotropic noise would make every
+residual direction equally likely, a structure no real embedding set has.
+
 Seeds: mixture parameters and base rows derive from 1000+cfg, queries from
 2000+cfg.  Rows are drawn in chunks of 65536 with their own child seed, so a
 smaller ``n`` gives a prefix of the full-size dataset and chunks can be drawn
@@ -60,6 +68,15 @@ def config(cfg: int) -> WorkloadConfig:
     return CONFIGS[cfg]
 
 
+def _zipf_frame(rng: np.random.Generator, m: int, sigma: float):
+    """Random orthonormal frame (m x m) and per-axis standard deviations whose
+    variances follow 1/i with total sigma^2 m."""
+    R = np.linalg.qr(rng.standard_normal((m, m)))[0]
+    lam = 1.0 / np.arange(1, m + 1, dtype=np.float64)
+    lam *= sigma ** 2 * m / lam.sum()
+    return R, np.sqrt(lam)
+
+
 def _mixture(cfg: int):
     """Mixture parameters of configuration ``cfg`` (drawn from seed 1000+cfg)."""
     c = CONFIGS[cfg]
@@ -74,13 +91,17 @@ def _mixture(cfg: int):
     if cfg == 3:
         centres = rng.standard_normal((256, c.m))
         w = np.arange(1, 257, dtype=np.float64) ** -1.5
-        return dict(kind="gauss_unit", centres=centres, weights=w / w.sum(), sigma=1.0)
+        R, sd = _zipf_frame(rng, c.m, 1.0)
+        return dict(kind="gauss_unit", centres=centres, weights=w / w.sum(), frame=R, sd=sd)
     if cfg == 4:
         centres = rng.standard_normal((128, c.m))
-        return dict(kind="gauss_unit", centres=centres, weights=np.full(128, 1 / 128), sigma=0.5)
+        R, sd = _zipf_frame(rng, c.m, 0.5)
+        return dict(kind="gauss_unit", centres=centres, weights=np.full(128, 1 / 128), frame=R,
+                    sd=sd)
     if cfg == 5:
         mu = rng.normal(-2.0, 0.5, size=(32, c.m))
-        return dict(kind="lognormal", mu=mu, weights=np.full(32, 1 / 32), sigma=0.5)
+        R, sd = _zipf_frame(rng, c.m, 0.5)
+        return dict(kind="lognormal", mu=mu, weights=np.full(32, 1 / 32), frame=R, sd=sd)
     raise KeyError(cfg)
 
 
@@ -90,12 +111,12 @@ def _draw(mix, m: int, rows: int, rng: np.random.Generator) -> np.ndarray:
     if kind == "gauss":
         x = mix["centres"][k] + mix["sigma"] * rng.standard_normal((rows, m))
     elif kind == "gauss_unit":
-        x = mix["centres"][k] + mix["sigma"] * rng.standard_normal((rows, m))
+        x = mix["centres"][k] + (rng.standard_normal((rows, m)) * mix["sd"]) @ mix["frame"].T
         x /= np.linalg.norm(x, axis=1, keepdims=True)
     elif kind == "gamma_int":
         x = np.minimum(255.0, np.round(rng.gamma(mix["shape"][k], mix["scale"][k])))
     elif kind == "lognormal":
-        x = np.exp(mix["mu"][k] + mix["sigma"] * rng.standard_normal((rows, m)))
+        x = np.exp(mix["mu"][k] + (rng.standard_normal((rows, m)) * mix["sd"]) @ mix["frame"].T)
     else:
         raise ValueError(kind)
     return np.ascontiguousarray(x, dtype=np.float32)
