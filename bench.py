@@ -52,9 +52,12 @@ def parse():
     ap.add_argument("--cfg", type=int, default=2)
     ap.add_argument("--n", type=int, default=0, help="override n (smaller runs)")
     ap.add_argument("--nq", type=int, default=0)
-    ap.add_argument("--candidates", type=int, default=64)
+    ap.add_argument("--candidates", type=int, default=0,
+                    help="graph build candidates per node (default: the workload's efConstruction)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--save-curves", default="")
+    ap.add_argument("--ablation", action="store_true",
+                    help="Sec. 4.4 ablation (basis and matching variants) on --cfg")
     ap.add_argument("--profile-ef", type=int, default=0,
                     help="profiling run: set up, then only --warmup + 1 FINGER searches at this ef")
     return ap.parse_args()
@@ -285,7 +288,7 @@ def _ext_setup(args, cfg, build_lp=False):
     Q = workloads.query_vectors(cfg, nq)
     ix = fg.Index(X)
     tg = time.perf_counter()
-    ix.build_graph(c.M, candidates=max(args.candidates, 2 * c.M), level_seed=3000 + cfg)
+    ix.build_graph(c.M, candidates=args.candidates or c.ef_construction, level_seed=3000 + cfg)
     torch.cuda.synchronize()
     tg = time.perf_counter() - tg
     tt = time.perf_counter()
@@ -589,10 +592,85 @@ def leg_batch(args):
     return line
 
 
+def leg_ablation(args):
+    """Sec. 4.4 on a synthetic stand-in: FINGER's SVD basis vs a random Gaussian
+    (RPLSH) basis, each with and without distribution matching.  Per variant:
+    the approximation error |t - t_hat| / |t| of the residual cosine on triples
+    harvested from FINGER traversals of training queries (t the true cosine,
+    t_hat the variant's estimate before the eps correction), and recall@10
+    against effective distance calls a + b r / m (a full m-dimensional
+    distances including the upper levels, b rank-r estimates) along an ef
+    sweep.  Also the rank rule of Supplementary E on the same graph."""
+    import torch
+
+    import paper_2206_11408_gb300 as fg
+    cfg = args.cfg
+    c, n, nq, X, Q, ix, q, setup = _ext_setup(args, cfg)
+    nq_s = min(nq, 2000)
+    qs = q[:nq_s]
+    gt_ids, _ = ix.knn(qs, c.K)
+    gt = gt_ids.cpu().numpy()
+    Qtr = torch.from_numpy(workloads.training_queries(cfg, 500)).cuda()
+    rank, trace = ix.select_rank(4000 + cfg, r_max=min(64, c.m))
+    G = np.random.default_rng(6000 + cfg).standard_normal((c.r, c.m))
+    variants = {"finger": (None, True), "finger_no_matching": (None, False),
+                "rplsh_matching": (G, True), "rplsh": (G, False)}
+    grid = [e for e in c.ef_grid if e % 20 == 0 or e <= 20][:12]
+    out = {}
+    for name, (basis, matching) in variants.items():
+        ix.build_tables(c.r, 4000 + cfg, basis=basis, matching=matching)
+        st = ix.stats()
+        ix.set_mode(fg.MODE_FINGER, 5)
+        feat, tgt, _ = ix.harvest(Qtr, 100, 400_000)
+        that = feat[:, c.r].double().cpu().numpy()
+        t = tgt.double().cpu().numpy()
+        ratio = st["sigma"] / st["sigma_hat"] if st["sigma_hat"] > 0 else 0.0
+        est = (that - st["mu_hat"]) * ratio + st["mu"]
+        rel = np.abs(t - est) / np.maximum(np.abs(t), 1e-12)
+        pts = []
+        for ef in grid:
+            cnt = torch.zeros((nq_s, 8), dtype=torch.int32, device="cuda")
+            ix.set_counters(cnt)
+            ids, _ = ix.search(qs, c.K, ef)
+            torch.cuda.synchronize()
+            ix.set_counters(None)
+            ix.sync()
+            cs = cnt.sum(0).cpu().numpy().astype(np.float64) / nq_s
+            full = cs[4] + cs[6]
+            pts.append([ef, round(recall_at(ids.cpu().numpy(), gt, c.K), 4),
+                        round(full + cs[2] * c.r / c.m, 1), round(full, 1), round(cs[2], 1)])
+        out[name] = {"corr": st["corr"], "eps": st["eps"], "triples": int(len(t)),
+                     "approx_error_mean": float(rel.mean()),
+                     "approx_error_median": float(np.median(rel)),
+                     "abs_error_mean": float(np.abs(t - est).mean()),
+                     "curve_ef_recall_effcalls_full_est": pts}
+    pts = []
+    ix.set_mode(fg.MODE_PLAIN, 5)
+    for ef in grid:
+        cnt = torch.zeros((nq_s, 8), dtype=torch.int32, device="cuda")
+        ix.set_counters(cnt)
+        ids, _ = ix.search(qs, c.K, ef)
+        torch.cuda.synchronize()
+        ix.set_counters(None)
+        ix.sync()
+        cs = cnt.sum(0).cpu().numpy().astype(np.float64) / nq_s
+        pts.append([ef, round(recall_at(ids.cpu().numpy(), gt, c.K), 4), round(cs[4] + cs[6], 1)])
+    out["plain"] = {"curve_ef_recall_effcalls": pts}
+    return {"metric": "Sec. 4.4 ablation: approximation error and recall@10 vs effective "
+                      "distance calls", "impl": "ours", "n_gpus": 1, "data": "synthetic",
+            "config": {"workload": c.name if n == c.n else f"{c.name}[:{n}]", "n": n, "m": c.m,
+                       "r": c.r, "M": c.M, "nq": nq_s},
+            "rank_rule": {"rank": rank, "corr_trace": trace, "threshold": 0.7},
+            "variants": out, "setup_s": setup}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.ablation:
+        print(json.dumps(leg_ablation(args)), flush=True)
+        return 0
     if args.cfg in (3, 4, 5):
         line = {3: leg_lp, 4: leg_mlp, 5: leg_batch}[args.cfg](args)
         print(json.dumps(line), flush=True)
@@ -615,7 +693,8 @@ def main():
     Q = workloads.query_vectors(args.cfg, nq)
     ix = fg.Index(X, device=local)
     t0 = time.perf_counter()
-    ix.build_graph(c.M, candidates=args.candidates, level_seed=3000 + args.cfg)
+    cands = args.candidates or c.ef_construction
+    ix.build_graph(c.M, candidates=cands, level_seed=3000 + args.cfg)
     torch.cuda.synchronize()
     t_graph = time.perf_counter() - t0
     t0 = time.perf_counter()
@@ -771,7 +850,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": workload, "n": n, "m": c.m, "nq_per_gpu": nq, "K": K,
                        "M": c.M, "deg0": info["deg0"], "r": c.r, "ef_finger": ef_f,
-                       "ef_plain": ef_p, "graph": f"GPU HNSW-style, {args.candidates} exact "
+                       "ef_plain": ef_p, "graph": f"GPU HNSW, insertion order, {cands} exact "
                                                   "candidates + heuristic selection",
                        "l2": "inputs larger than L2 (index ~9 GB), no flush",
                        "parallelism": f"replicas x{ws}, queries sharded"},

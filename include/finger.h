@@ -80,17 +80,22 @@ finger_status finger_index_set_graph(finger_index* ix, int deg0, const int32_t* 
 typedef struct {
     int M;                /* degree cap on levels >= 1; layer 0 allows 2M (<= 32) */
     int candidates;       /* exact nearest neighbours offered to the pruning step
-                             (<= 128; 0 = 2 * 2M) */
+                             (efConstruction; <= 256; 0 = 2 * 2M) */
     uint64_t level_seed;  /* seed of the level draw floor(-ln U / ln M) */
+    int symmetric;        /* 0 (default): HNSW insertion order, node i draws its
+                             candidates from the nodes j < i of its level only;
+                             1: from all nodes of its level */
 } finger_graph_params;
 
-/* Build an HNSW-style graph on the device: levels drawn as in HNSW from a
- * counter-based generator, then for every level the exact k nearest neighbours
- * among that level's nodes (brute force on the GPU; k = `candidates` on layer 0,
- * up to 256 on the upper layers), heuristic neighbour
- * selection (keep a candidate only if it is closer to the node than to every
- * neighbour kept so far, as in HNSW), reverse edges, and a second heuristic
- * pass to the degree cap.  Synchronous (returns when the graph is built). */
+/* Build an HNSW graph on the device.  Levels are drawn as in HNSW from a
+ * counter-based generator; nodes are inserted in id order.  For every level
+ * and node i: the exact `candidates` nearest among the level's nodes inserted
+ * before i (brute force on the GPU: HNSW's efConstruction beam search made
+ * exact), HNSW's heuristic selection of M forward links (keep a candidate
+ * only if it is closer to the node than to every neighbour kept so far),
+ * reverse links from later nodes, and a second heuristic pass over forward
+ * and reverse links to the level's cap (2M on layer 0, M above).  The upper
+ * levels use up to 256 candidates.  Synchronous. */
 finger_status finger_build_graph(finger_index* ix, const finger_graph_params* p, void* stream);
 
 /* Copy the graph back to host arrays of the sizes given by finger_get_info().

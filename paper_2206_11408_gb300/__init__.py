@@ -37,7 +37,8 @@ class FingerError(RuntimeError):
 
 
 class GraphParams(ctypes.Structure):
-    _fields_ = [("M", ctypes.c_int), ("candidates", ctypes.c_int), ("level_seed", ctypes.c_uint64)]
+    _fields_ = [("M", ctypes.c_int), ("candidates", ctypes.c_int), ("level_seed", ctypes.c_uint64),
+                ("symmetric", ctypes.c_int)]
 
 
 class BuildParams(ctypes.Structure):
@@ -212,8 +213,11 @@ class Index:
             up_adj.shape[0], M, _np_ptr(up_adj) if up_adj.size else None, entry, maxlevel),
             "finger_index_set_graph")
 
-    def build_graph(self, M: int, candidates: int = 0, level_seed: int = 0, stream=None):
-        p = GraphParams(M, candidates, level_seed)
+    def build_graph(self, M: int, candidates: int = 0, level_seed: int = 0,
+                    symmetric: bool = False, stream=None):
+        """finger_build_graph: HNSW on the device (insertion order by id, exact
+        candidate search); symmetric=True draws candidates from all nodes."""
+        p = GraphParams(M, candidates, level_seed, int(symmetric))
         _check(self._lib.finger_build_graph(self._h, ctypes.byref(p), _stream_ptr(stream)),
                "finger_build_graph")
 

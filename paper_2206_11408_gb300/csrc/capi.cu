@@ -40,7 +40,7 @@ int search_smem_per_warp(const DevIndex& ix, int mode, int ef_cap, int H, int NP
     const int r_pad = ix.r4 * 4;
     const int qs_len = mode == FINGER_MODE_FINGER_LP ? ix.m8 * 8 : ix.m4 * 4;
     const int qs_bytes = mode == FINGER_MODE_FINGER_LP ? 4 * ((qs_len + 3) & ~3) : 0;
-    const int tile = mode == FINGER_MODE_FINGER_MLP ? 2 * 32 * NPL * ix.mlp_kp : 0;
+    const int tile = mode == FINGER_MODE_FINGER_MLP ? 2 * 32 * NPL * (ix.mlp_kp + MLP_PAD) : 0;
     int b = 8 * ef_cap + 4 * H + 8 * r_pad + qs_bytes + 32 * 32 * NPL + 32 + tile;
     return (b + 15) & ~15;
 }
@@ -168,7 +168,9 @@ finger_status make_plan(finger_index* ix, int mode, int ef_max, int64_t nq, Sear
     p->H = H;
     p->wpb = wpb;
     p->smem_per_warp = search_smem_per_warp(d, mode, p->ef_cap, p->H, p->NPL);
-    p->blk_smem = mode == FINGER_MODE_FINGER_MLP ? 2 * 64 * ix->mlp_kp + 2 * 64 * 64 + 3 * 64 * 4 : 0;
+    p->blk_smem = mode == FINGER_MODE_FINGER_MLP
+                      ? 2 * 64 * (ix->mlp_kp + MLP_PAD) + 2 * 64 * (64 + MLP_PAD) + 3 * 64 * 4
+                      : 0;
     if (p->blk_smem + (int64_t)p->smem_per_warp * wpb > 227 * 1024) return FINGER_ERR_UNSUPPORTED;
     int bps = 0;
     if (search_occupancy(d, *p, &bps) != cudaSuccess || bps < 1) {

@@ -2,10 +2,14 @@
 // the paper builds FINGER "from any existing graph G", Sec. 3.3).
 //
 // Levels are drawn as in HNSW: level(v) = floor(-ln U_v / ln M) with U_v from
-// the counter-based generator splitmix64(seed ^ v).  For every level l the
-// nodes with level >= l form a layer; its edges come from
-//   1. the exact `candidates` nearest neighbours among the layer's nodes
-//      (brute force, knn.cu; up to 256 on the small upper layers);
+// the counter-based generator splitmix64(seed ^ v).  Nodes are inserted in id
+// order (the rows are i.i.d., so this is a random order).  For every level l
+// the nodes with level >= l form a layer; its edges come from
+//   1. the exact `candidates` nearest neighbours among the layer's nodes with a
+//      smaller id (HNSW's efConstruction search over the nodes inserted
+//      before, made exact; brute force with a causal mask, knn.cu; up to 256 on
+//      the small upper layers).  The first nodes of a cluster thus link to
+//      other clusters, as in HNSW.  `symmetric` takes all of the layer's nodes;
 //   2. the HNSW neighbour-selection heuristic over those candidates, sorted by
 //      (distance, id): keep a candidate only if it is strictly closer to the
 //      node than to every neighbour kept so far, up to M forward links;
@@ -225,7 +229,7 @@ T* dalloc(size_t count) {
 // of width out_w at out_row[...] (global rows for layer 0, up_adj rows above)
 finger_status build_layer(finger_index* ix, const int32_t* d_nodes, int64_t cnt, int kc, int Mf,
                           int Mmax, uint32_t* out, int out_w, const int64_t* d_out_row,
-                          const int32_t* d_cmap, cudaStream_t s) {
+                          const int32_t* d_cmap, bool causal, cudaStream_t s) {
     finger_status status = FINGER_OK;
     const int m4 = ix->m4;
     float4* Xl = nullptr;
@@ -276,7 +280,7 @@ finger_status build_layer(finger_index* ix, const int32_t* d_nodes, int64_t cnt,
     }
     CK(launch_knn(d_nodes ? Xl : reinterpret_cast<const float4*>(ix->X), cnt, m4,
                   d_nodes ? reinterpret_cast<const float*>(Xl) : ix->X, (int64_t)m4 * 4, m4 * 4,
-                  cnt, kk, true, d_nodes, cid, cd, s));
+                  cnt, kk, true, d_nodes, cid, cd, s, causal));
     k_select<<<(unsigned)wblocks, 128, 0, s>>>(reinterpret_cast<const float4*>(ix->X), m4, cid, cd,
                                                kk, cnt, Mf, fwd, fwd_d, Mf, nullptr);
     CK(cudaGetLastError());
@@ -330,7 +334,8 @@ finger_status build_graph(finger_index* ix, const finger_graph_params* p, cudaSt
     const int deg0 = 2 * M;
     if (M < 2 || deg0 > MAX_DEG0 || M > MAX_MUP) return FINGER_ERR_INVALID_ARG;
     int kc = p->candidates > 0 ? p->candidates : 2 * deg0;
-    if (kc > 128 || kc < M) return FINGER_ERR_INVALID_ARG;
+    if (kc > 256 || kc < M) return FINGER_ERR_INVALID_ARG;
+    const bool causal = p->symmetric == 0;
     const int64_t n = ix->n;
     finger_status status = FINGER_OK;
     // levels
@@ -378,7 +383,7 @@ finger_status build_graph(finger_index* ix, const finger_graph_params* p, cudaSt
     }
     {
         CK(cudaMemcpy(d_up_off, up_off.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice));
-        status = build_layer(ix, nullptr, n, kc, M, deg0, adj0, deg0, nullptr, nullptr, s);
+        status = build_layer(ix, nullptr, n, kc, M, deg0, adj0, deg0, nullptr, nullptr, causal, s);
         if (status != FINGER_OK) goto done;
         if (maxlevel > 0) {
             d_nodes = dalloc<int32_t>((size_t)n);
@@ -406,7 +411,7 @@ finger_status build_graph(finger_index* ix, const finger_graph_params* p, cudaSt
             // upper layers are small: offer up to 256 exact candidates so that the
             // selection sees beyond a node's own cluster and keeps long links
             status = build_layer(ix, d_nodes, cnt, (int)std::min<int64_t>(cnt - 1, 256), M, M,
-                                 up_adj, M, d_rows, d_cmap, s);
+                                 up_adj, M, d_rows, d_cmap, causal, s);
             if (status != FINGER_OK) goto done;
         }
     }

@@ -20,6 +20,10 @@ constexpr int MAX_M = 1024;
 constexpr int MAX_DEG0 = 64;
 constexpr int MAX_MUP = 32;
 constexpr int MAX_R = 64;
+// BF16 padding of the predictor's shared-memory rows (features, W1, W2): a row
+// stride of 8 mod 16 elements keeps the 16-byte feature stores and the MMA
+// fragment loads free of bank conflicts
+constexpr int MLP_PAD = 8;
 constexpr int MAX_EF = 1024;
 constexpr int MLP_H = 64;                 // hidden width of the learned predictor
 
@@ -104,10 +108,10 @@ int search_smem_per_warp(const DevIndex& ix, int mode, int ef_cap, int H, int NP
 cudaError_t search_occupancy(const DevIndex& ix, const SearchPlan& p, int* blocks_per_sm);
 void choose_groups(int nchunks, int* G, int* VPL);
 
-// brute force (build.cu)
+// brute force (knn.cu); causal: query row i sees base rows < i only
 cudaError_t launch_knn(const float4* Xb, int64_t nb, int m4, const float* Q, int64_t q_stride,
                        int q_m, int64_t nq, int K, bool exclude_self, const int32_t* remap,
-                       int64_t* out_ids, float* out_d, cudaStream_t s);
+                       int64_t* out_ids, float* out_d, cudaStream_t s, bool causal = false);
 size_t knn_smem(int K);
 
 // graph construction (graph.cu)

@@ -6,7 +6,9 @@
 // 32 dimensions staged transposed in shared memory (each thread a 4 x 4 block).
 // After a tile, values below a query's current K-th key are appended to that
 // query's candidate buffer and one warp per query inserts them into a sorted
-// top-K list kept in shared memory.  Keys are (distance, id).
+// top-K list kept in shared memory.  Keys are (distance, id).  In causal mode
+// (queries and base rows the same array) query row i considers base rows < i
+// only, and tiles above the diagonal are not computed.
 #include <float.h>
 
 #include "internal.cuh"
@@ -24,8 +26,8 @@ __device__ __forceinline__ bool klt(float da, int ia, float db, int ib) {
 __global__ void __launch_bounds__(NT) k_knn(const float4* __restrict__ X, int64_t nb, int m4,
                                             const float* __restrict__ Q, int64_t q_stride,
                                             int q_m, int64_t nq, int K, int exclude_self,
-                                            const int32_t* __restrict__ remap, int64_t* out_ids,
-                                            float* out_d) {
+                                            int causal, const int32_t* __restrict__ remap,
+                                            int64_t* out_ids, float* out_d) {
     extern __shared__ __align__(16) unsigned char sm[];
     float* Qs = reinterpret_cast<float*>(sm);          // KC x QB
     float* Xs = Qs + KC * QB;                          // KC x XB
@@ -49,8 +51,8 @@ __global__ void __launch_bounds__(NT) k_knn(const float4* __restrict__ X, int64_
         thr_i[i] = 0x7fffffff;
     }
     const int m = m4 * 4;
-    // self id of each query (for exclusion)
-    for (int64_t x0 = 0; x0 < nb; x0 += XB) {
+    const int64_t x_end = causal ? (q0 + QB < nb ? q0 + QB : nb) : nb;
+    for (int64_t x0 = 0; x0 < x_end; x0 += XB) {
         float acc[4][4];
 #pragma unroll
         for (int a = 0; a < 4; ++a)
@@ -109,7 +111,7 @@ __global__ void __launch_bounds__(NT) k_knn(const float4* __restrict__ X, int64_
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
                 const int64_t gx = x0 + tx * 4 + b;
-                if (gx >= nb) continue;
+                if (gx >= nb || (causal && gx >= gq)) continue;
                 const int gid = remap ? remap[gx] : (int)gx;
                 if (gid == self) continue;
                 if (klt(acc[a][b], gid, td, ti)) {
@@ -191,7 +193,8 @@ size_t knn_smem(int K) {
 // reported (and query row -> its own id for exclusion).
 cudaError_t launch_knn(const float4* Xb, int64_t nb, int m4, const float* Q, int64_t q_stride,
                        int q_m, int64_t nq, int K, bool exclude_self,
-                       const int32_t* remap, int64_t* out_ids, float* out_d, cudaStream_t s) {
+                       const int32_t* remap, int64_t* out_ids, float* out_d, cudaStream_t s,
+                       bool causal) {
     if (nq == 0) return cudaSuccess;
     const size_t smem = knn_smem(K);
     cudaError_t e = cudaFuncSetAttribute(k_knn, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -199,7 +202,7 @@ cudaError_t launch_knn(const float4* Xb, int64_t nb, int m4, const float* Q, int
     if (e != cudaSuccess) return e;
     const int64_t grid = (nq + QB - 1) / QB;
     k_knn<<<(unsigned)grid, NT, smem, s>>>(Xb, nb, m4, Q, q_stride, q_m, nq, K, exclude_self ? 1 : 0,
-                                           remap, out_ids, out_d);
+                                           causal ? 1 : 0, remap, out_ids, out_d);
     return cudaGetLastError();
 }
 

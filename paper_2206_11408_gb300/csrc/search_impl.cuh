@@ -390,13 +390,11 @@ __device__ __forceinline__ void edge_cos_list(const DevIndex& ix, size_t ebase, 
 // Features of one (q, c, d) triple for the learned angle predictor (an
 // extension; the paper has no learned predictor): f = [u_q * u_d (r values),
 // t_hat, ||q_res|| / ||q||, ||d_res|| / ||d||, a / (|a| + |b| + 1e-6)], with
-// ||d||^2 = b^2 ||c||^2 + ||d_res||^2.  Written as BF16 into a shared-memory
-// tile row (inference) or as FP32 into a global row (harvest).  Returns t_hat,
-// summed in the same order as edge_cos.
-template <bool TO_GLOBAL>
+// ||d||^2 = b^2 ||c||^2 + ||d_res||^2, written as FP32 into a global row
+// (harvest).  Returns t_hat, summed in the same order as edge_cos.
 __device__ __forceinline__ float features_row(const DevIndex& ix, size_t e, const float* uq,
                                               float2 sc, float cc, float ac, float qres_n,
-                                              float qn2, __nv_bfloat16* xrow, float* grow) {
+                                              float qn2, float* grow) {
     const float4* ud = ix.edge_u + e * ix.r4;
     float th = 0.f;
     for (int k = 0; k < ix.r4; ++k) {
@@ -408,31 +406,63 @@ __device__ __forceinline__ float features_row(const DevIndex& ix, size_t e, cons
         th = fmaf(x.z, uq[4 * k + 2], th);
         th = fmaf(x.w, uq[4 * k + 3], th);
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int j = 4 * k + i;
-            if (j < ix.r) {
-                if constexpr (TO_GLOBAL) grow[j] = p[i];
-                else xrow[j] = __float2bfloat16_rn(p[i]);
-            }
-        }
+        for (int i = 0; i < 4; ++i)
+            if (4 * k + i < ix.r) grow[4 * k + i] = p[i];
     }
     const float dnorm = sqrtf(sc.y * sc.y * cc + sc.x * sc.x);
-    const float tail[4] = {th, qn2 > 0.f ? qres_n * rsqrtf(qn2) : 0.f,
-                           dnorm > 0.f ? sc.x / dnorm : 0.f,
-                           ac / (fabsf(ac) + fabsf(sc.y) + 1e-6f)};
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        if constexpr (TO_GLOBAL) grow[ix.r + i] = tail[i];
-        else xrow[ix.r + i] = __float2bfloat16_rn(tail[i]);
-    }
-    if constexpr (!TO_GLOBAL)
-        for (int j = ix.r + 4; j < ix.mlp_kp; ++j) xrow[j] = __float2bfloat16_rn(0.f);
+    grow[ix.r] = th;
+    grow[ix.r + 1] = qn2 > 0.f ? qres_n * rsqrtf(qn2) : 0.f;
+    grow[ix.r + 2] = dnorm > 0.f ? sc.x / dnorm : 0.f;
+    grow[ix.r + 3] = ac / (fabsf(ac) + fabsf(sc.y) + 1e-6f);
     return th;
 }
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
     __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
     return *reinterpret_cast<uint32_t*>(&v);
+}
+
+// The same features as features_row, written as one BF16 row of the predictor
+// tile with 16-byte stores (8 features each; kp is a multiple of 16 and the
+// row is 16-byte aligned).  Returns t_hat, summed in edge_cos order.
+__device__ __forceinline__ float features_tile(const DevIndex& ix, size_t e, const float* uq,
+                                              float2 sc, float cc, float ac, float qres_n,
+                                              float qn2, __nv_bfloat16* xrow) {
+    const float4* ud = ix.edge_u + e * ix.r4;
+    float th = 0.f;
+    for (int k = 0; k < ix.r4; ++k) {
+        const float4 x = __ldg(ud + k);
+        th = fmaf(x.x, uq[4 * k], th);
+        th = fmaf(x.y, uq[4 * k + 1], th);
+        th = fmaf(x.z, uq[4 * k + 2], th);
+        th = fmaf(x.w, uq[4 * k + 3], th);
+    }
+    const float dnorm = sqrtf(sc.y * sc.y * cc + sc.x * sc.x);
+    const float tail[4] = {th, qn2 > 0.f ? qres_n * rsqrtf(qn2) : 0.f,
+                           dnorm > 0.f ? sc.x / dnorm : 0.f,
+                           ac / (fabsf(ac) + fabsf(sc.y) + 1e-6f)};
+    const int r = ix.r;
+    uint4* out = reinterpret_cast<uint4*>(xrow);
+    for (int c = 0; c < (ix.mlp_kp >> 3); ++c) {
+        float f[8];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int k = 2 * c + h;
+            const float4 x = k < ix.r4 ? __ldg(ud + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float xv[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int j = 4 * k + i;
+                float v = 0.f;
+                if (j < r) v = xv[i] * uq[j];
+                else if (j < r + 4) v = tail[j - r];
+                f[4 * h + i] = v;
+            }
+        }
+        out[c] = make_uint4(pack_bf16x2(f[0], f[1]), pack_bf16x2(f[2], f[3]),
+                            pack_bf16x2(f[4], f[5]), pack_bf16x2(f[6], f[7]));
+    }
+    return th;
 }
 
 // D += A B for one m16n8k16 tile, BF16 operands, FP32 accumulators
@@ -444,20 +474,20 @@ __device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, uint32_t b
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-// The predictor r+4 -> 64 -> 64 -> 1 on the 32*NPL feature rows of one
-// expansion (one row per neighbour slot) with warp-level BF16 tensor-core MMAs
+// The predictor r+4 -> 64 -> 64 -> 1 on the first 16*ntiles feature rows of
+// one expansion (the new neighbours, compacted) with warp-level BF16 tensor-core MMAs
 // (m16n8k16, FP32 accumulation).  Layer 1's accumulators are turned into the
 // A operand of layer 2 in registers (the C layout of two n8 tiles is the A
 // layout of one k16 step); layer 3 is an FP32 dot reduced over the lane quad.
 // W1s: 64 x kp BF16 (row = hidden unit), W2s: 64 x 64 BF16, b1s/b2s/w3s FP32.
-template <int NPL>
-__device__ __forceinline__ void mlp_batch(const __nv_bfloat16* xt, int kp,
+__device__ __forceinline__ void mlp_batch(const __nv_bfloat16* xt, int kp, int ntiles,
                                           const __nv_bfloat16* W1s, const __nv_bfloat16* W2s,
                                           const float* b1s, const float* b2s, const float* w3s,
                                           float b3, float* yout, int lane) {
     const int g = lane >> 2, t = lane & 3;
     const int nks = kp >> 4;
-    for (int mt = 0; mt < 2 * NPL; ++mt) {
+    const int xs = kp + MLP_PAD, w2s = 64 + MLP_PAD;   // padded row strides
+    for (int mt = 0; mt < ntiles; ++mt) {
         const int r0 = mt * 16 + g, r1 = r0 + 8;
         float acc[8][4];
 #pragma unroll
@@ -469,13 +499,13 @@ __device__ __forceinline__ void mlp_batch(const __nv_bfloat16* xt, int kp,
             acc[nt][3] = c1;
         }
         for (int ks = 0; ks < nks; ++ks) {
-            const uint32_t* X0 = reinterpret_cast<const uint32_t*>(xt + r0 * kp + 16 * ks);
-            const uint32_t* X1 = reinterpret_cast<const uint32_t*>(xt + r1 * kp + 16 * ks);
+            const uint32_t* X0 = reinterpret_cast<const uint32_t*>(xt + r0 * xs + 16 * ks);
+            const uint32_t* X1 = reinterpret_cast<const uint32_t*>(xt + r1 * xs + 16 * ks);
             const uint32_t a[4] = {X0[t], X1[t], X0[t + 4], X1[t + 4]};
 #pragma unroll
             for (int nt = 0; nt < 8; ++nt) {
                 const uint32_t* Wr =
-                    reinterpret_cast<const uint32_t*>(W1s + (8 * nt + g) * kp + 16 * ks);
+                    reinterpret_cast<const uint32_t*>(W1s + (8 * nt + g) * xs + 16 * ks);
                 mma_bf16(acc[nt], a, Wr[t], Wr[t + 4]);
             }
         }
@@ -496,7 +526,7 @@ __device__ __forceinline__ void mlp_batch(const __nv_bfloat16* xt, int kp,
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk) {
                 const uint32_t* Wr =
-                    reinterpret_cast<const uint32_t*>(W2s + (8 * nt + g) * 64 + 16 * kk);
+                    reinterpret_cast<const uint32_t*>(W2s + (8 * nt + g) * w2s + 16 * kk);
                 mma_bf16(cacc, h[kk], Wr[t], Wr[t + 4]);
             }
             const float wa = w3s[8 * nt + 2 * t], wb = w3s[8 * nt + 2 * t + 1];
@@ -552,13 +582,15 @@ __global__ void __launch_bounds__(128, 5) k_search(DevIndex ix, SearchArgs a) {
     __nv_bfloat16* xt = reinterpret_cast<__nv_bfloat16*>(meta + 8);   // predictor input tile
     // predictor weights, staged once per block at the start of shared memory
     __nv_bfloat16* W1s = reinterpret_cast<__nv_bfloat16*>(sm);
-    __nv_bfloat16* W2s = W1s + 64 * ix.mlp_kp;
-    float* b1s = reinterpret_cast<float*>(W2s + 64 * 64);
+    __nv_bfloat16* W2s = W1s + 64 * (ix.mlp_kp + MLP_PAD);
+    float* b1s = reinterpret_cast<float*>(W2s + 64 * (64 + MLP_PAD));
     float* b2s = b1s + 64;
     float* w3s = b2s + 64;
     if constexpr (MLP) {
-        for (int i = threadIdx.x; i < 64 * ix.mlp_kp; i += blockDim.x) W1s[i] = ix.W1[i];
-        for (int i = threadIdx.x; i < 64 * 64; i += blockDim.x) W2s[i] = ix.W2[i];
+        for (int i = threadIdx.x; i < 64 * ix.mlp_kp; i += blockDim.x)
+            W1s[(i / ix.mlp_kp) * (ix.mlp_kp + MLP_PAD) + i % ix.mlp_kp] = ix.W1[i];
+        for (int i = threadIdx.x; i < 64 * 64; i += blockDim.x)
+            W2s[(i >> 6) * (64 + MLP_PAD) + (i & 63)] = ix.W2[i];
         for (int i = threadIdx.x; i < 64; i += blockDim.x) {
             b1s[i] = ix.b1[i];
             b2s[i] = ix.b2[i];
@@ -756,6 +788,17 @@ __global__ void __launch_bounds__(128, 5) k_search(DevIndex ix, SearchArgs a) {
                 tr[s] = 0.f;
                 hpos[s] = -1;
             }
+            int crow[NPL];          // MLP: compact feature row of each new slot
+            int ncomp = 0;
+#pragma unroll
+            for (int s = 0; s < NPL; ++s) {
+                crow[s] = -1;
+                if constexpr (MLP) {
+                    const unsigned bm = __ballot_sync(FULLMASK, isnew[s]);
+                    if (isnew[s]) crow[s] = ncomp + __popc(bm & ltmask);
+                    ncomp += __popc(bm);
+                }
+            }
             if constexpr (MLP || HARV) {
                 if (use_est) {
 #pragma unroll
@@ -778,23 +821,27 @@ __global__ void __launch_bounds__(128, 5) k_search(DevIndex ix, SearchArgs a) {
                             float th;
                             if constexpr (HARV) {
                                 if (pos >= 0)
-                                    th = features_row<true>(ix, e, uq, sc, cc, ac, qres_n, qn2,
-                                                            nullptr, a.hv_feat + pos * (ix.r + 4));
+                                    th = features_row(ix, e, uq, sc, cc, ac, qres_n, qn2,
+                                                      a.hv_feat + pos * (ix.r + 4));
                                 else
                                     th = edge_cos<false>(ix, e, uq);
                             } else {
-                                th = features_row<false>(ix, e, uq, sc, cc, ac, qres_n, qn2,
-                                                         xt + (size_t)o * ix.mlp_kp, nullptr);
+                                th = features_tile(ix, e, uq, sc, cc, ac, qres_n, qn2,
+                                                   xt + (size_t)crow[s] * (ix.mlp_kp + MLP_PAD));
                             }
                             tr[s] = fmaf(th, ix.alpha, ix.beta);
-                        } else if constexpr (MLP) {
-                            for (int j = 0; j < ix.mlp_kp; ++j)
-                                xt[(size_t)o * ix.mlp_kp + j] = __float2bfloat16_rn(0.f);
                         }
                     }
                     if constexpr (MLP) {
+                        // zero the padding rows of the last 16-row tile, then run
+                        // the predictor on the ceil(ncomp / 16) tiles only; its
+                        // outputs go to `ak` (free until the admission replay)
+                        const int ntiles = (ncomp + 15) >> 4;
+                        uint32_t* xw = reinterpret_cast<uint32_t*>(xt);
+                        const int wpr = (ix.mlp_kp + MLP_PAD) >> 1;
+                        for (int i = ncomp * wpr + lane; i < ntiles * 16 * wpr; i += 32) xw[i] = 0u;
                         __syncwarp();
-                        mlp_batch<NPL>(xt, ix.mlp_kp, W1s, W2s, b1s, b2s, w3s, ix.b3, es, lane);
+                        mlp_batch(xt, ix.mlp_kp, ntiles, W1s, W2s, b1s, b2s, w3s, ix.b3, ak, lane);
                     }
                 }
             }
@@ -810,7 +857,7 @@ __global__ void __launch_bounds__(128, 5) k_search(DevIndex ix, SearchArgs a) {
                     if constexpr (MLP) {
                         // learned predictor in place of distribution matching;
                         // the matched cosine is the fallback for a non-finite output
-                        const float y = es[s * 32 + lane];
+                        const float y = ak[crow[s]];
                         t = isfinite(y) ? y + ix.mlp_eps : tr[s];
                     } else if constexpr (HARV) {
                         t = tr[s];

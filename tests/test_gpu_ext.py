@@ -179,6 +179,44 @@ def test_gpu_graph_builder_invariants():
     jx.close()
 
 
+def _reachable(adj0, entry):
+    n = adj0.shape[0]
+    seen = np.zeros(n, bool)
+    seen[entry] = True
+    frontier = np.array([entry])
+    while frontier.size:
+        nb = adj0[frontier].reshape(-1)
+        nb = np.unique(nb[nb >= 0])
+        nb = nb[~seen[nb]]
+        seen[nb] = True
+        frontier = nb
+    return seen.mean()
+
+
+def test_gpu_graph_insertion_order_links_clusters():
+    """32 well-separated clusters (the GIST-like distribution): with HNSW's
+    insertion order the first nodes of a cluster link to the clusters inserted
+    before, so layer 0 is connected from the entry point; candidates drawn from
+    all nodes (symmetric) stay inside each cluster."""
+    X = workloads.base_vectors(5, 20000)
+    Q = workloads.query_vectors(5, 100)
+    ix = fg.Index(X)
+    ix.build_graph(16, 100, 3005)
+    g = ix.get_graph()
+    reach = _reachable(g["adj0"], g["entry"])
+    assert reach > 0.99, reach
+    ix.build_tables(16, 4005)
+    ix.set_mode(fg.MODE_PLAIN)
+    ids, _ = ix.search(torch.from_numpy(Q).cuda(), 10, 100)
+    gt, _ = oracle.bruteforce(X, Q, 10)
+    rec = oracle.recall(ids.cpu().numpy(), gt, 10)
+    assert rec > 0.9, rec
+    ix.build_graph(16, 100, 3005, symmetric=True)
+    gs = ix.get_graph()
+    assert _reachable(gs["adj0"], gs["entry"]) < reach
+    ix.close()
+
+
 def test_kernel_limit_is_reported_not_faulted():
     """A search that hits the expansion cap returns FINGER_ERR_LIMIT through the
     status word instead of running on; the context stays usable afterwards."""
