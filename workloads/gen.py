@@ -59,8 +59,8 @@ CONFIGS = {
                       tuple(range(10, 401, 10)), True, "lp"),
     4: WorkloadConfig(4, "gauss-unit-1M-96", 1_000_000, 96, 16, 200, 24, 10_000, 10,
                       tuple(range(10, 401, 10)), True, "fp32"),
-    5: WorkloadConfig(5, "lognormal-1M-960", 1_000_000, 960, 32, 200, 64, 50_000, 10,
-                      tuple(range(10, 401, 10)), False, "fp32"),
+    5: WorkloadConfig(5, "lognormal-1M-960", 1_000_000, 960, 32, 256, 64, 50_000, 10,
+                      tuple(range(10, 401, 10)) + tuple(range(450, 1001, 50)), False, "fp32"),
 }
 
 
