@@ -40,7 +40,7 @@ int search_smem_per_warp(const DevIndex& ix, int mode, int ef_cap, int H, int NP
     const int r_pad = ix.r4 * 4;
     const int qs_len = mode == FINGER_MODE_FINGER_LP ? ix.m8 * 8 : ix.m4 * 4;
     const int qs_bytes = mode == FINGER_MODE_FINGER_LP ? 4 * ((qs_len + 3) & ~3) : 0;
-    const int tile = mode == FINGER_MODE_FINGER_MLP ? 2 * 32 * NPL * (ix.mlp_kp + MLP_PAD) : 0;
+    const int tile = mode == FINGER_MODE_FINGER_MLP ? 2 * 16 * (ix.mlp_kp + MLP_PAD) : 0;
     int b = 8 * ef_cap + 4 * H + 8 * r_pad + qs_bytes + 32 * 32 * NPL + 32 + tile;
     return (b + 15) & ~15;
 }
@@ -104,8 +104,8 @@ fg::DevIndex make_dev(const finger_index* ix) {
     d.Xh = reinterpret_cast<const uint4*>(ix->Xh);
     d.edge_q = reinterpret_cast<const uint4*>(ix->edge_q);
     d.code_inv = 1.0f / ix->code_scale;
-    d.W1 = ix->W1;
-    d.W2 = ix->W2;
+    d.W1f = ix->W1f;
+    d.W2f = ix->W2f;
     d.w3 = ix->w3;
     d.b1 = ix->b1;
     d.b2 = ix->b2;
@@ -168,9 +168,7 @@ finger_status make_plan(finger_index* ix, int mode, int ef_max, int64_t nq, Sear
     p->H = H;
     p->wpb = wpb;
     p->smem_per_warp = search_smem_per_warp(d, mode, p->ef_cap, p->H, p->NPL);
-    p->blk_smem = mode == FINGER_MODE_FINGER_MLP
-                      ? 2 * 64 * (ix->mlp_kp + MLP_PAD) + 2 * 64 * (64 + MLP_PAD) + 3 * 64 * 4
-                      : 0;
+    p->blk_smem = 0;
     if (p->blk_smem + (int64_t)p->smem_per_warp * wpb > 227 * 1024) return FINGER_ERR_UNSUPPORTED;
     int bps = 0;
     if (search_occupancy(d, *p, &bps) != cudaSuccess || bps < 1) {
@@ -357,7 +355,7 @@ void finger_index_free(finger_index* ix) {
     DeviceGuard g(ix->device);
     fg_drop_captures(ix);
     void* ptrs[] = {ix->X, ix->xnorm2, ix->adj0, ix->up_off, ix->up_adj, ix->P, ix->Pc,
-                    ix->edge_u, ix->edge_s, ix->Xh, ix->edge_q, ix->W1, ix->W2, ix->w3,
+                    ix->edge_u, ix->edge_s, ix->Xh, ix->edge_q, ix->W1f, ix->W2f, ix->w3,
                     ix->b1, ix->b2, ix->work, ix->err, ix->cnt, ix->bitmap, ix->spill,
                     ix->stage_q, ix->stage_ids, ix->stage_d, ix->eig_G, ix->eig_V};
     for (void* p : ptrs) cudaFree(p);
@@ -366,7 +364,7 @@ void finger_index_free(finger_index* ix) {
 
 static void drop_tables(finger_index* ix) {
     void* ptrs[] = {ix->P, ix->Pc, ix->edge_u, ix->edge_s, ix->Xh, ix->edge_q,
-                    ix->W1, ix->W2, ix->w3, ix->b1, ix->b2, ix->eig_G, ix->eig_V};
+                    ix->W1f, ix->W2f, ix->w3, ix->b1, ix->b2, ix->eig_G, ix->eig_V};
     for (void* p : ptrs) cudaFree(p);
     ix->eig_G = ix->eig_V = nullptr;
     ix->corr = 0.0 / 0.0;
@@ -374,7 +372,7 @@ static void drop_tables(finger_index* ix) {
     ix->edge_s = nullptr;
     ix->Xh = nullptr;
     ix->edge_q = nullptr;
-    ix->W1 = ix->W2 = nullptr;
+    ix->W1f = ix->W2f = nullptr;
     ix->w3 = ix->b1 = ix->b2 = nullptr;
     ix->r = ix->r_pad = ix->r16 = 0;
     ix->has_mlp = 0;

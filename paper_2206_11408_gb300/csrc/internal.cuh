@@ -20,9 +20,9 @@ constexpr int MAX_M = 1024;
 constexpr int MAX_DEG0 = 64;
 constexpr int MAX_MUP = 32;
 constexpr int MAX_R = 64;
-// BF16 padding of the predictor's shared-memory rows (features, W1, W2): a row
-// stride of 8 mod 16 elements keeps the 16-byte feature stores and the MMA
-// fragment loads free of bank conflicts
+// BF16 padding of the predictor's shared-memory feature rows: a row stride of
+// 8 mod 16 elements keeps the 16-byte feature stores and the MMA fragment loads
+// free of bank conflicts
 constexpr int MLP_PAD = 8;
 constexpr int MAX_EF = 1024;
 constexpr int MLP_H = 64;                 // hidden width of the learned predictor
@@ -48,10 +48,11 @@ struct DevIndex {
     const uint4* Xh;        // n x m8 (BF16)
     const uint4* edge_q;    // (n*deg0) x r16 FP8-e4m3 codes of edge_u * code_scale
     float code_inv;         // 1 / code_scale
-    // learned predictor: BF16 W1 (H x kp, zero padded beyond r+4), BF16 W2 (H x H),
-    // w3 (H, BF16-valued FP32), FP32 biases
-    const __nv_bfloat16* W1;
-    const __nv_bfloat16* W2;
+    // learned predictor: BF16 W1 (H x kp, zero padded beyond r+4) and W2 (H x H)
+    // stored fragment-major for m16n8k16 B operands (uint2 per lane per
+    // (n8 tile, k16 step)), w3 (H, BF16-valued FP32), FP32 biases
+    const uint2* W1f;
+    const uint2* W2f;
     const float* w3;
     const float* b1;
     const float* b2;
@@ -163,8 +164,8 @@ struct finger_index {
     // learned predictor
     int has_mlp = 0;
     int mlp_kp = 0;
-    __nv_bfloat16* W1 = nullptr;
-    __nv_bfloat16* W2 = nullptr;
+    uint2* W1f = nullptr;         // fragment-major BF16 (see DevIndex)
+    uint2* W2f = nullptr;
     float* w3 = nullptr;
     float* b1 = nullptr;
     float* b2 = nullptr;

@@ -229,25 +229,51 @@ finger_status finger_load_mlp_internal(finger_index* ix, const float* w, int64_t
         for (int i = 0; i < kp; ++i)
             W1[(size_t)j * kp + i] = __float2bfloat16_rn(i < nf ? w[o.W1 + (int64_t)j * nf + i] : 0.f);
     for (int i = 0; i < HID * HID; ++i) W2[i] = __float2bfloat16_rn(w[o.W2 + i]);
+    // fragment-major B operands of m16n8k16 (row n = 8 nt + g of the weight
+    // matrix, k pairs 16 ks + 2t and 16 ks + 2t + 8 of that row; g = lane / 4,
+    // t = lane % 4): one uint2 per lane per (nt, ks)
+    auto frag = [](const std::vector<__nv_bfloat16>& Wm, int K) {
+        const int nk = K / 16;
+        std::vector<uint2> f((size_t)8 * nk * 32);
+        auto bits = [&](int row, int col) {
+            __nv_bfloat16 v = Wm[(size_t)row * K + col];
+            uint16_t u;
+            memcpy(&u, &v, 2);
+            return (uint32_t)u;
+        };
+        for (int nt = 0; nt < 8; ++nt)
+            for (int ks = 0; ks < nk; ++ks)
+                for (int lane = 0; lane < 32; ++lane) {
+                    const int n = 8 * nt + (lane >> 2), c = 16 * ks + 2 * (lane & 3);
+                    f[((size_t)nt * nk + ks) * 32 + lane] =
+                        make_uint2(bits(n, c) | bits(n, c + 1) << 16,
+                                   bits(n, c + 8) | bits(n, c + 9) << 16);
+                }
+        return f;
+    };
+    const std::vector<uint2> W1f = frag(W1, kp), W2f = frag(W2, HID);
     std::vector<float> w3(HID), b1(w + o.b1, w + o.b1 + HID), b2(w + o.b2, w + o.b2 + HID);
     for (int k = 0; k < HID; ++k) w3[k] = __bfloat162float(__float2bfloat16_rn(w[o.w3 + k]));
     int prev = 0;
     cudaGetDevice(&prev);
     cudaSetDevice(ix->device);
-    cudaFree(ix->W1);
-    cudaFree(ix->W2);
+    cudaFree(ix->W1f);
+    cudaFree(ix->W2f);
     cudaFree(ix->w3);
     cudaFree(ix->b1);
     cudaFree(ix->b2);
-    ix->W1 = ix->W2 = nullptr;
+    ix->W1f = ix->W2f = nullptr;
     ix->w3 = ix->b1 = ix->b2 = nullptr;
-    bool ok = cudaMalloc(&ix->W1, W1.size() * 2) == cudaSuccess &&
-              cudaMalloc(&ix->W2, W2.size() * 2) == cudaSuccess &&
+    bool ok = cudaMalloc(&ix->W1f, W1f.size() * sizeof(uint2)) == cudaSuccess &&
+              cudaMalloc(&ix->W2f, W2f.size() * sizeof(uint2)) == cudaSuccess &&
               cudaMalloc(&ix->w3, HID * 4) == cudaSuccess &&
               cudaMalloc(&ix->b1, HID * 4) == cudaSuccess &&
               cudaMalloc(&ix->b2, HID * 4) == cudaSuccess;
-    ok = ok && cudaMemcpy(ix->W1, W1.data(), W1.size() * 2, cudaMemcpyHostToDevice) == cudaSuccess &&
-         cudaMemcpy(ix->W2, W2.data(), W2.size() * 2, cudaMemcpyHostToDevice) == cudaSuccess &&
+    ok = ok &&
+         cudaMemcpy(ix->W1f, W1f.data(), W1f.size() * sizeof(uint2), cudaMemcpyHostToDevice) ==
+             cudaSuccess &&
+         cudaMemcpy(ix->W2f, W2f.data(), W2f.size() * sizeof(uint2), cudaMemcpyHostToDevice) ==
+             cudaSuccess &&
          cudaMemcpy(ix->w3, w3.data(), HID * 4, cudaMemcpyHostToDevice) == cudaSuccess &&
          cudaMemcpy(ix->b1, b1.data(), HID * 4, cudaMemcpyHostToDevice) == cudaSuccess &&
          cudaMemcpy(ix->b2, b2.data(), HID * 4, cudaMemcpyHostToDevice) == cudaSuccess;

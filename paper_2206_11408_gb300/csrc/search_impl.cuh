@@ -423,45 +423,34 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
 }
 
 // The same features as features_row, written as one BF16 row of the predictor
-// tile with 16-byte stores (8 features each; kp is a multiple of 16 and the
-// row is 16-byte aligned).  Returns t_hat, summed in edge_cos order.
+// tile in a single pass over the edge row: each 16-byte chunk of u_d gives four
+// products (one 8-byte store) and four terms of t_hat; then the four tail
+// features and the zero padding up to kp.  Returns t_hat, summed in edge_cos
+// order.  (Entries r..r_pad-1 of u_d are 0, so their products are 0 before the
+// tail overwrites them.)
 __device__ __forceinline__ float features_tile(const DevIndex& ix, size_t e, const float* uq,
                                               float2 sc, float cc, float ac, float qres_n,
                                               float qn2, __nv_bfloat16* xrow) {
     const float4* ud = ix.edge_u + e * ix.r4;
+    const float4* uq4 = reinterpret_cast<const float4*>(uq);
+    uint2* out = reinterpret_cast<uint2*>(xrow);
     float th = 0.f;
     for (int k = 0; k < ix.r4; ++k) {
         const float4 x = __ldg(ud + k);
-        th = fmaf(x.x, uq[4 * k], th);
-        th = fmaf(x.y, uq[4 * k + 1], th);
-        th = fmaf(x.z, uq[4 * k + 2], th);
-        th = fmaf(x.w, uq[4 * k + 3], th);
+        const float4 y = uq4[k];
+        th = fmaf(x.x, y.x, th);
+        th = fmaf(x.y, y.y, th);
+        th = fmaf(x.z, y.z, th);
+        th = fmaf(x.w, y.w, th);
+        out[k] = make_uint2(pack_bf16x2(x.x * y.x, x.y * y.y), pack_bf16x2(x.z * y.z, x.w * y.w));
     }
     const float dnorm = sqrtf(sc.y * sc.y * cc + sc.x * sc.x);
-    const float tail[4] = {th, qn2 > 0.f ? qres_n * rsqrtf(qn2) : 0.f,
-                           dnorm > 0.f ? sc.x / dnorm : 0.f,
-                           ac / (fabsf(ac) + fabsf(sc.y) + 1e-6f)};
     const int r = ix.r;
-    uint4* out = reinterpret_cast<uint4*>(xrow);
-    for (int c = 0; c < (ix.mlp_kp >> 3); ++c) {
-        float f[8];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int k = 2 * c + h;
-            const float4 x = k < ix.r4 ? __ldg(ud + k) : make_float4(0.f, 0.f, 0.f, 0.f);
-            const float xv[4] = {x.x, x.y, x.z, x.w};
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int j = 4 * k + i;
-                float v = 0.f;
-                if (j < r) v = xv[i] * uq[j];
-                else if (j < r + 4) v = tail[j - r];
-                f[4 * h + i] = v;
-            }
-        }
-        out[c] = make_uint4(pack_bf16x2(f[0], f[1]), pack_bf16x2(f[2], f[3]),
-                            pack_bf16x2(f[4], f[5]), pack_bf16x2(f[6], f[7]));
-    }
+    xrow[r] = __float2bfloat16_rn(th);
+    xrow[r + 1] = __float2bfloat16_rn(qn2 > 0.f ? qres_n * rsqrtf(qn2) : 0.f);
+    xrow[r + 2] = __float2bfloat16_rn(dnorm > 0.f ? sc.x / dnorm : 0.f);
+    xrow[r + 3] = __float2bfloat16_rn(ac / (fabsf(ac) + fabsf(sc.y) + 1e-6f));
+    for (int j = r + 4; j < ix.mlp_kp; ++j) xrow[j] = __float2bfloat16_rn(0.f);
     return th;
 }
 
@@ -474,75 +463,73 @@ __device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, uint32_t b
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-// The predictor r+4 -> 64 -> 64 -> 1 on the first 16*ntiles feature rows of
-// one expansion (the new neighbours, compacted) with warp-level BF16 tensor-core MMAs
-// (m16n8k16, FP32 accumulation).  Layer 1's accumulators are turned into the
-// A operand of layer 2 in registers (the C layout of two n8 tiles is the A
-// layout of one k16 step); layer 3 is an FP32 dot reduced over the lane quad.
-// W1s: 64 x kp BF16 (row = hidden unit), W2s: 64 x 64 BF16, b1s/b2s/w3s FP32.
-__device__ __forceinline__ void mlp_batch(const __nv_bfloat16* xt, int kp, int ntiles,
-                                          const __nv_bfloat16* W1s, const __nv_bfloat16* W2s,
-                                          const float* b1s, const float* b2s, const float* w3s,
-                                          float b3, float* yout, int lane) {
+// The predictor r+4 -> 64 -> 64 -> 1 on one 16-row tile of feature rows with
+// warp-level BF16 tensor-core MMAs (m16n8k16, FP32 accumulation).  Layer 1's
+// accumulators are turned into the A operand of layer 2 in registers (the C
+// layout of two n8 tiles is the A layout of one k16 step); layer 3 is an FP32
+// dot reduced over the lane quad.  The B operands are stored fragment-major
+// (one 8-byte word pair per lane per (n8 tile, k16 step)), so each fragment is
+// one coalesced load that stays in L1; biases and w3 are FP32 in global memory.
+__device__ __forceinline__ void mlp_tile(const __nv_bfloat16* xt, int kp, const uint2* W1f,
+                                         const uint2* W2f, const float* b1, const float* b2,
+                                         const float* w3, float b3, float* yout, int lane) {
     const int g = lane >> 2, t = lane & 3;
     const int nks = kp >> 4;
-    const int xs = kp + MLP_PAD, w2s = 64 + MLP_PAD;   // padded row strides
-    for (int mt = 0; mt < ntiles; ++mt) {
-        const int r0 = mt * 16 + g, r1 = r0 + 8;
-        float acc[8][4];
+    const int xs = kp + MLP_PAD;
+    const int r0 = g, r1 = g + 8;
+    float acc[8][4];
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+        const float c0 = __ldg(b1 + 8 * nt + 2 * t), c1 = __ldg(b1 + 8 * nt + 2 * t + 1);
+        acc[nt][0] = c0;
+        acc[nt][1] = c1;
+        acc[nt][2] = c0;
+        acc[nt][3] = c1;
+    }
+    for (int ks = 0; ks < nks; ++ks) {
+        const uint32_t* X0 = reinterpret_cast<const uint32_t*>(xt + r0 * xs + 16 * ks);
+        const uint32_t* X1 = reinterpret_cast<const uint32_t*>(xt + r1 * xs + 16 * ks);
+        const uint32_t a[4] = {X0[t], X1[t], X0[t + 4], X1[t + 4]};
 #pragma unroll
         for (int nt = 0; nt < 8; ++nt) {
-            const float c0 = b1s[8 * nt + 2 * t], c1 = b1s[8 * nt + 2 * t + 1];
-            acc[nt][0] = c0;
-            acc[nt][1] = c1;
-            acc[nt][2] = c0;
-            acc[nt][3] = c1;
-        }
-        for (int ks = 0; ks < nks; ++ks) {
-            const uint32_t* X0 = reinterpret_cast<const uint32_t*>(xt + r0 * xs + 16 * ks);
-            const uint32_t* X1 = reinterpret_cast<const uint32_t*>(xt + r1 * xs + 16 * ks);
-            const uint32_t a[4] = {X0[t], X1[t], X0[t + 4], X1[t + 4]};
-#pragma unroll
-            for (int nt = 0; nt < 8; ++nt) {
-                const uint32_t* Wr =
-                    reinterpret_cast<const uint32_t*>(W1s + (8 * nt + g) * xs + 16 * ks);
-                mma_bf16(acc[nt], a, Wr[t], Wr[t + 4]);
-            }
-        }
-        uint32_t h[4][4];
-#pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {
-            h[kk][0] = pack_bf16x2(fmaxf(acc[2 * kk][0], 0.f), fmaxf(acc[2 * kk][1], 0.f));
-            h[kk][1] = pack_bf16x2(fmaxf(acc[2 * kk][2], 0.f), fmaxf(acc[2 * kk][3], 0.f));
-            h[kk][2] = pack_bf16x2(fmaxf(acc[2 * kk + 1][0], 0.f), fmaxf(acc[2 * kk + 1][1], 0.f));
-            h[kk][3] = pack_bf16x2(fmaxf(acc[2 * kk + 1][2], 0.f), fmaxf(acc[2 * kk + 1][3], 0.f));
-        }
-        float p0 = 0.f, p1 = 0.f;
-#pragma unroll
-        for (int nt = 0; nt < 8; ++nt) {
-            float cacc[4];
-            cacc[0] = cacc[2] = b2s[8 * nt + 2 * t];
-            cacc[1] = cacc[3] = b2s[8 * nt + 2 * t + 1];
-#pragma unroll
-            for (int kk = 0; kk < 4; ++kk) {
-                const uint32_t* Wr =
-                    reinterpret_cast<const uint32_t*>(W2s + (8 * nt + g) * w2s + 16 * kk);
-                mma_bf16(cacc, h[kk], Wr[t], Wr[t + 4]);
-            }
-            const float wa = w3s[8 * nt + 2 * t], wb = w3s[8 * nt + 2 * t + 1];
-            p0 = fmaf(fmaxf(cacc[0], 0.f), wa, fmaf(fmaxf(cacc[1], 0.f), wb, p0));
-            p1 = fmaf(fmaxf(cacc[2], 0.f), wa, fmaf(fmaxf(cacc[3], 0.f), wb, p1));
-        }
-        p0 += __shfl_xor_sync(FULLMASK, p0, 1);
-        p0 += __shfl_xor_sync(FULLMASK, p0, 2);
-        p1 += __shfl_xor_sync(FULLMASK, p1, 1);
-        p1 += __shfl_xor_sync(FULLMASK, p1, 2);
-        if (t == 0) {
-            yout[r0] = p0 + b3;
-            yout[r1] = p1 + b3;
+            const uint2 w = __ldg(W1f + (nt * nks + ks) * 32 + lane);
+            mma_bf16(acc[nt], a, w.x, w.y);
         }
     }
-    __syncwarp();
+    uint32_t h[4][4];
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+        h[kk][0] = pack_bf16x2(fmaxf(acc[2 * kk][0], 0.f), fmaxf(acc[2 * kk][1], 0.f));
+        h[kk][1] = pack_bf16x2(fmaxf(acc[2 * kk][2], 0.f), fmaxf(acc[2 * kk][3], 0.f));
+        h[kk][2] = pack_bf16x2(fmaxf(acc[2 * kk + 1][0], 0.f), fmaxf(acc[2 * kk + 1][1], 0.f));
+        h[kk][3] = pack_bf16x2(fmaxf(acc[2 * kk + 1][2], 0.f), fmaxf(acc[2 * kk + 1][3], 0.f));
+    }
+    float p0 = 0.f, p1 = 0.f;
+    // layer 2 as a rolled loop over the eight n8 tiles: its accumulators live
+    // only inside one iteration, and the kernel's code stays small enough for
+    // the instruction cache
+#pragma unroll 1
+    for (int nt = 0; nt < 8; ++nt) {
+        float cacc[4];
+        cacc[0] = cacc[2] = __ldg(b2 + 8 * nt + 2 * t);
+        cacc[1] = cacc[3] = __ldg(b2 + 8 * nt + 2 * t + 1);
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+            const uint2 w = __ldg(W2f + (nt * 4 + kk) * 32 + lane);
+            mma_bf16(cacc, h[kk], w.x, w.y);
+        }
+        const float wa = __ldg(w3 + 8 * nt + 2 * t), wb = __ldg(w3 + 8 * nt + 2 * t + 1);
+        p0 = fmaf(fmaxf(cacc[0], 0.f), wa, fmaf(fmaxf(cacc[1], 0.f), wb, p0));
+        p1 = fmaf(fmaxf(cacc[2], 0.f), wa, fmaf(fmaxf(cacc[3], 0.f), wb, p1));
+    }
+    p0 += __shfl_xor_sync(FULLMASK, p0, 1);
+    p0 += __shfl_xor_sync(FULLMASK, p0, 2);
+    p1 += __shfl_xor_sync(FULLMASK, p1, 1);
+    p1 += __shfl_xor_sync(FULLMASK, p1, 2);
+    if (t == 0) {
+        yout[r0] = p0 + b3;
+        yout[r1] = p1 + b3;
+    }
 }
 
 template <int MODE, int G, int VPL, int NPL>
@@ -580,25 +567,6 @@ __global__ void __launch_bounds__(128, 5) k_search(DevIndex ix, SearchArgs a) {
     float* aub = reinterpret_cast<float*>(apos + 32 * NPL);   // ub after it
     int* meta = reinterpret_cast<int*>(aub + 32 * NPL);       // replay results (8 ints)
     __nv_bfloat16* xt = reinterpret_cast<__nv_bfloat16*>(meta + 8);   // predictor input tile
-    // predictor weights, staged once per block at the start of shared memory
-    __nv_bfloat16* W1s = reinterpret_cast<__nv_bfloat16*>(sm);
-    __nv_bfloat16* W2s = W1s + 64 * (ix.mlp_kp + MLP_PAD);
-    float* b1s = reinterpret_cast<float*>(W2s + 64 * (64 + MLP_PAD));
-    float* b2s = b1s + 64;
-    float* w3s = b2s + 64;
-    if constexpr (MLP) {
-        for (int i = threadIdx.x; i < 64 * ix.mlp_kp; i += blockDim.x)
-            W1s[(i / ix.mlp_kp) * (ix.mlp_kp + MLP_PAD) + i % ix.mlp_kp] = ix.W1[i];
-        for (int i = threadIdx.x; i < 64 * 64; i += blockDim.x)
-            W2s[(i >> 6) * (64 + MLP_PAD) + (i & 63)] = ix.W2[i];
-        for (int i = threadIdx.x; i < 64; i += blockDim.x) {
-            b1s[i] = ix.b1[i];
-            b2s[i] = ix.b2[i];
-            w3s[i] = ix.w3[i];
-        }
-        __syncthreads();
-    }
-
     if (FG_CHECKED) g_chk_err = a.err;   // same value from every thread
     const int64_t slot = (int64_t)blockIdx.x * wpb + wib;
     uint32_t* bitmap = a.bitmap + slot * a.words;
@@ -799,49 +767,57 @@ __global__ void __launch_bounds__(128, 5) k_search(DevIndex ix, SearchArgs a) {
                     ncomp += __popc(bm);
                 }
             }
-            if constexpr (MLP || HARV) {
+            if constexpr (HARV) {
                 if (use_est) {
 #pragma unroll
                     for (int s = 0; s < NPL; ++s) {
                         const int o = s * 32 + lane;
                         int64_t pos = -1;
-                        if constexpr (HARV) {
-                            const bool rec = isnew[s] && full0;
-                            const unsigned bm = __ballot_sync(FULLMASK, rec);
-                            unsigned long long base = 0;
-                            if (lane == 0 && bm) base = atomicAdd(a.hv_count, (unsigned long long)__popc(bm));
-                            base = __shfl_sync(FULLMASK, base, 0);
-                            if (rec) pos = (int64_t)base + __popc(bm & ltmask);
-                            if (pos >= a.hv_cap) pos = -1;
-                            hpos[s] = pos;
-                        }
+                        const bool rec = isnew[s] && full0;
+                        const unsigned bm = __ballot_sync(FULLMASK, rec);
+                        unsigned long long base = 0;
+                        if (lane == 0 && bm) base = atomicAdd(a.hv_count, (unsigned long long)__popc(bm));
+                        base = __shfl_sync(FULLMASK, base, 0);
+                        if (rec) pos = (int64_t)base + __popc(bm & ltmask);
+                        if (pos >= a.hv_cap) pos = -1;
+                        hpos[s] = pos;
                         if (isnew[s]) {
                             const size_t e = (size_t)c * ix.deg0 + o;
                             const float2 sc = __ldg(ix.edge_s + e);
-                            float th;
-                            if constexpr (HARV) {
-                                if (pos >= 0)
-                                    th = features_row(ix, e, uq, sc, cc, ac, qres_n, qn2,
-                                                      a.hv_feat + pos * (ix.r + 4));
-                                else
-                                    th = edge_cos<false>(ix, e, uq);
-                            } else {
-                                th = features_tile(ix, e, uq, sc, cc, ac, qres_n, qn2,
-                                                   xt + (size_t)crow[s] * (ix.mlp_kp + MLP_PAD));
-                            }
+                            const float th =
+                                pos >= 0 ? features_row(ix, e, uq, sc, cc, ac, qres_n, qn2,
+                                                        a.hv_feat + pos * (ix.r + 4))
+                                         : edge_cos<false>(ix, e, uq);
                             tr[s] = fmaf(th, ix.alpha, ix.beta);
                         }
                     }
-                    if constexpr (MLP) {
-                        // zero the padding rows of the last 16-row tile, then run
-                        // the predictor on the ceil(ncomp / 16) tiles only; its
-                        // outputs go to `ak` (free until the admission replay)
-                        const int ntiles = (ncomp + 15) >> 4;
-                        uint32_t* xw = reinterpret_cast<uint32_t*>(xt);
-                        const int wpr = (ix.mlp_kp + MLP_PAD) >> 1;
-                        for (int i = ncomp * wpr + lane; i < ntiles * 16 * wpr; i += 32) xw[i] = 0u;
+                }
+            }
+            if constexpr (MLP) {
+                // the new neighbours' feature rows go through the predictor 16 at a
+                // time (one m16 tile per round); outputs land in `ak` (free until
+                // the admission replay) at the neighbour's compact row
+                if (use_est) {
+                    uint32_t* xw = reinterpret_cast<uint32_t*>(xt);
+                    const int xs = ix.mlp_kp + MLP_PAD;
+                    const int wpr = xs >> 1;
+                    for (int base = 0; base < ncomp; base += 16) {
+#pragma unroll
+                        for (int s = 0; s < NPL; ++s) {
+                            if (isnew[s] && crow[s] >= base && crow[s] < base + 16) {
+                                const size_t e = (size_t)c * ix.deg0 + s * 32 + lane;
+                                const float2 sc = __ldg(ix.edge_s + e);
+                                const float th = features_tile(ix, e, uq, sc, cc, ac, qres_n, qn2,
+                                                               xt + (size_t)(crow[s] - base) * xs);
+                                tr[s] = fmaf(th, ix.alpha, ix.beta);
+                            }
+                        }
+                        const int rows = min(16, ncomp - base);
+                        for (int i = rows * wpr + lane; i < 16 * wpr; i += 32) xw[i] = 0u;
                         __syncwarp();
-                        mlp_batch(xt, ix.mlp_kp, ntiles, W1s, W2s, b1s, b2s, w3s, ix.b3, ak, lane);
+                        mlp_tile(xt, ix.mlp_kp, ix.W1f, ix.W2f, ix.b1, ix.b2, ix.w3, ix.b3,
+                                 ak + base, lane);
+                        __syncwarp();
                     }
                 }
             }
