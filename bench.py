@@ -72,12 +72,6 @@ def recall_at(ids: np.ndarray, gt: np.ndarray, K: int) -> float:
     return hits / (K * len(ids))
 
 
-def dist_env():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
-
 
 class Clocks:
     """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
@@ -215,7 +209,9 @@ def tie_recall(ids: np.ndarray, dists: np.ndarray, gt_d: np.ndarray, K: int) -> 
 # ---------------------------------------------------------------- reference
 
 def run_reference(args):
-    ws, rank, _ = dist_env()
+    from paper_2206_11408_gb300.replicas import world
+
+    ws, rank, _ = world()
     if rank != 0:
         return 0
     import oracle
@@ -679,18 +675,23 @@ def main():
 
     import paper_2206_11408_gb300 as fg
 
-    ws, rank, local = dist_env()
+    from paper_2206_11408_gb300 import replicas
+
+    ws, rank, local = replicas.world()
     torch.cuda.set_device(local)
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
     c = workloads.config(args.cfg)
     n = args.n or c.n
     nq = args.nq or c.nq
     K = c.K
     t_setup = time.perf_counter()
     X = workloads.base_vectors(args.cfg, n)
-    Q = workloads.query_vectors(args.cfg, nq)
+    # replicas: every rank holds the whole index and serves its own nq queries
+    q0, q1 = replicas.query_slice(nq, rank)
+    Q = workloads.query_vectors(args.cfg, nq * ws)[q0:q1]
     ix = fg.Index(X, device=local)
     t0 = time.perf_counter()
     cands = args.candidates or c.ef_construction
@@ -764,8 +765,7 @@ def main():
             ix.search(q, K, ef, ids, d)
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                for _ in range(steps)]
-        if ws > 1:
-            torch.distributed.barrier()
+        replicas.barrier()
         torch.cuda.synchronize()
         if clocks:
             clocks.start()
@@ -777,26 +777,28 @@ def main():
             evs[i][1].record(stream)
         g1.record(stream)
         torch.cuda.synchronize()
-        if ws > 1:
-            torch.distributed.barrier()
+        replicas.barrier()
         ck = clocks.stop() if clocks else None
         ix.sync()
         total = g0.elapsed_time(g1)
         per = [a.elapsed_time(b) for a, b in evs]
         return total, per, ck
 
-    # FINGER timed region (the headline) and plain at its own ef
+    # FINGER timed region (the headline) and plain at its own ef; with several
+    # replicas the ef is the largest any rank needed for the recall target
     ef_f, rec_f = choice["finger"]
     ef_p, rec_p = choice["plain"]
+    if ws > 1:
+        ef_f, ef_p = (int(v) for v in replicas.max_over_ranks([ef_f, ef_p], dev))
+        rec_f = recall_at(timed(fg.MODE_FINGER, ef_f)[0], gt, K)
+        rec_p = recall_at(timed(fg.MODE_PLAIN, ef_p)[0], gt, K)
+        rec_f, rec_p = (v / ws for v in replicas.sum_over_ranks([rec_f, rec_p], dev))
     clocks = Clocks(local)
     total_f, per_f, ck = step_loop(fg.MODE_FINGER, ef_f, args.steps, args.warmup, clocks)
     total_p, per_p, _ = step_loop(fg.MODE_PLAIN, ef_p, args.steps, args.warmup)
     ms_f = total_f / args.steps
     ms_p = total_p / args.steps
-    if ws > 1:
-        t = torch.tensor([ms_f, ms_p], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_f, ms_p = float(t[0]), float(t[1])
+    ms_f, ms_p = replicas.max_over_ranks([ms_f, ms_p], dev)
     value = ws * nq / (ms_f / 1000)
     plain_qps = ws * nq / (ms_p / 1000)
 
@@ -823,16 +825,12 @@ def main():
     ix.set_mode(fg.MODE_FINGER, 5)
     for _ in range(args.warmup):
         ix.search_host(qh.numpy(), K, ef_f, ih.numpy(), dh.numpy())
-    if ws > 1:
-        torch.distributed.barrier()
+    replicas.barrier()
     t = time.perf_counter()
     for _ in range(args.steps):
         ix.search_host(qh.numpy(), K, ef_f, ih.numpy(), dh.numpy())
     e2e_ms = 1000 * (time.perf_counter() - t) / args.steps
-    if ws > 1:
-        tt = torch.tensor([e2e_ms], device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = float(tt[0])
+    e2e_ms, = replicas.max_over_ranks([e2e_ms], dev)
     e2e_rec = recall_at(ih.numpy(), gt, K)
 
     cpu = None
@@ -853,7 +851,7 @@ def main():
                        "ef_plain": ef_p, "graph": f"GPU HNSW, insertion order, {cands} exact "
                                                   "candidates + heuristic selection",
                        "l2": "inputs larger than L2 (index ~9 GB), no flush",
-                       "parallelism": f"replicas x{ws}, queries sharded"},
+                       "parallelism": f"replicas x{ws}, {nq} distinct queries per rank"},
             "recall_finger": rec_f, "recall_plain": rec_p, "plain_qps": plain_qps,
             "finger_over_plain": value / plain_qps,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

@@ -212,3 +212,24 @@ def test_two_neighbour_slots_per_lane():
         oi, od, oc = oracle.search(g, X, Q, 10, 64, f)
         _compare(gi, gd, gc, oi, od, oc, gt, 10, f"deg0=48 mode={mode}")
     ix.close()
+
+
+def test_wide_rows_k1_and_ef_equal_k():
+    """m = 300 (the GIST-like distribution's first 300 coordinates): every lane
+    holds several 16-byte chunks of a row; K = 1 and ef = K are the smallest
+    result and candidate lists."""
+    X = np.ascontiguousarray(workloads.base_vectors(5, 2500)[:, :300])
+    Q = np.ascontiguousarray(workloads.query_vectors(5, 120)[:, :300])
+    g = oracle.hnsw_build(X, 16, 60, 21)
+    fp, _ = oracle.build_tables(X, g, 32, 22)
+    ix = fg.Index(X)
+    ix.set_graph(g.adj0, g.level, g.up_off, g.up_adj, g.entry, g.maxlevel, g.M)
+    ix.build_tables(32, 22, basis=fp.P, stats=fp.stats())
+    q = torch.from_numpy(Q).cuda()
+    for K, ef in ((1, 1), (1, 16), (10, 10), (10, 48)):
+        gt, _ = oracle.bruteforce(X, Q, K)
+        for mode, f in ((fg.MODE_PLAIN, None), (fg.MODE_FINGER, fp)):
+            gi, gd, gc = _gpu_search(ix, q, K, ef, mode)
+            oi, od, oc = oracle.search(g, X, Q, K, ef, f)
+            _compare(gi, gd, gc, oi, od, oc, gt, K, f"m=300 K={K} ef={ef} mode={mode}")
+    ix.close()
