@@ -3,7 +3,7 @@
 //
 // finger_search keeps per-warp scratch for its exact visited set (a bitmap of
 // n bits per resident warp plus a list of the ids it set, used once a query's
-// shared-memory hash is half full) and allocates or grows that scratch on
+// shared-memory hash is 3/4 full) and allocates or grows that scratch on
 // first use and whenever a launch needs more resident warps than before.
 // Some callers cannot accept an allocation inside a query call: serving
 // processes that reserve their whole device-memory budget at start-up (a

@@ -18,8 +18,8 @@
 // GB300 mapping.  A warp owns one query from an atomic work counter until the
 // batch is drained (grid = SMs x resident blocks).  Per warp in shared memory:
 // the result list T (keys and ids, the EXP bit marks expanded entries), an
-// exact open-addressing visited hash that spills to a per-warp global bitmap
-// once half full, the unit residual projection of the query, and staging.
+// exact visited hash (buckets of four slots) that spills to a per-warp global
+// bitmap once 3/4 full, the unit residual projection of the query, and staging.
 // One expansion is three dependent gathers: the adjacency row (coalesced,
 // lane j <- neighbour j), the per-edge rows of the new neighbours (lane-per-
 // neighbour 16-byte loads, r-dot against the query projection broadcast from
@@ -241,33 +241,48 @@ __device__ __forceinline__ void t_insert(float* Tk, uint32_t* Ti, int& sz, int e
 
 enum { V_SEEN = 0, V_NEW = 1, V_NEW_SPILL = 2, V_PENDING = 3 };
 
-__device__ __forceinline__ uint32_t hslot(uint32_t id, int logH) {
-    return (id * 2654435769u) >> (32 - logH);
+// The visited hash in shared memory is bucketed: H slots form H/4 buckets of
+// four (one 16-byte load per probe), buckets are probed linearly from the one
+// the multiplicative hash picks.  Short probe chains up to a high load let the
+// table take 3/4 of its slots before the warp switches to spill mode.
+__device__ __forceinline__ uint32_t hbucket(uint32_t id, int logNB) {
+    return (id * 2654435769u) >> (32 - logNB);
 }
 
-// exact test-and-set of the visited set.  Once the shared-memory table is half
+// exact test-and-set of the visited set.  Once the shared-memory table is 3/4
 // full (spill mode) ids not found in it are test-and-set in the warp's global
 // bitmap; the call then returns V_PENDING with the old bitmap word in `oldw`
-// (its value is only waited for where the caller first reads it).
-__device__ __forceinline__ int visit(uint32_t* hash, int H, int logH, uint32_t id, bool spill_mode,
+// (its value is only waited for where the caller first reads it).  Lanes of the
+// warp insert distinct ids concurrently: a lost compare-and-swap means another
+// lane filled that slot, and the bucket is read again.
+__device__ __forceinline__ int visit(uint32_t* hash, int H, int logNB, uint32_t id, bool spill_mode,
                                      uint32_t* bitmap, uint32_t& oldw) {
-    uint32_t h = hslot(id, logH);
-    for (int probe = 0; probe < H; ++probe) {
-        if (!spill_mode) {
-            const uint32_t old = atomicCAS(&hash[h], PAD, id);
-            if (old == PAD) return V_NEW;
-            if (old == id) return V_SEEN;
-        } else {
-            const uint32_t v = hash[h];
-            if (v == id) return V_SEEN;
-            if (v == PAD) {
-                oldw = atomicOr(&bitmap[id >> 5], 1u << (id & 31));
-                return V_PENDING;
-            }
+    const uint32_t mask = (uint32_t)(H >> 2) - 1u;
+    uint32_t b = hbucket(id, logNB);
+    int retries = 0;
+    for (int probe = 0; probe <= (int)mask; ++probe) {
+        uint4 v;   // a fresh read: other lanes may have filled slots since
+        asm volatile("ld.volatile.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                     : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                     : "r"((uint32_t)__cvta_generic_to_shared(hash + 4 * CK(b, H >> 2, 1020))));
+        if (v.x == id || v.y == id || v.z == id || v.w == id) return V_SEEN;
+        const int e = v.x == PAD ? 0 : v.y == PAD ? 1 : v.z == PAD ? 2 : v.w == PAD ? 3 : -1;
+        if (e < 0) {
+            b = (b + 1) & mask;
+            continue;
         }
-        h = (h + 1) & (H - 1);
+        // the id is in no bucket of its probe sequence
+        if (spill_mode) {
+            oldw = atomicOr(&bitmap[id >> 5], 1u << (id & 31));
+            return V_PENDING;
+        }
+        const uint32_t old = atomicCAS(&hash[4 * b + e], PAD, id);
+        if (old == PAD) return V_NEW;
+        if (old == id) return V_SEEN;
+        if (++retries <= 4) --probe;   // re-read this bucket (bounded)
+        else b = (b + 1) & mask;
     }
-    return V_SEEN;  // unreachable: the table is never more than half full plus one batch
+    return V_SEEN;  // unreachable: the table never fills (3/4 plus one batch < 1)
 }
 
 // t_hat for one edge: r-dot of the stored unit residual projection with uq
@@ -571,7 +586,7 @@ __global__ void __launch_bounds__(128, 5) k_search(DevIndex ix, SearchArgs a) {
     const int64_t slot = (int64_t)blockIdx.x * wpb + wib;
     uint32_t* bitmap = a.bitmap + slot * a.words;
     uint32_t* spl = a.spill + slot * a.spill_cap;
-    const int logH = 31 - __clz(a.H);
+    const int logNB = 31 - __clz(a.H >> 2);   // buckets of the visited hash
 
     for (;;) {
         int qi = 0;
@@ -669,7 +684,7 @@ __global__ void __launch_bounds__(128, 5) k_search(DevIndex ix, SearchArgs a) {
         if (lane == 0) {
             Tk[0] = dcur;
             Ti[0] = cur;
-            hash[hslot(cur, logH)] = cur;
+            hash[4 * hbucket(cur, logNB)] = cur;   // the table is empty
         }
         __syncwarp();
         int sz = 1, cursor = 0, hcount = 1, nspill = 0;
@@ -713,7 +728,7 @@ __global__ void __launch_bounds__(128, 5) k_search(DevIndex ix, SearchArgs a) {
                 int res = V_SEEN;
                 uint32_t oldw = 0u;
                 if (nb[s] != PAD)
-                    res = visit(hash, a.H, logH, (uint32_t)CK(nb[s], ix.n, 1004), spill_mode, bitmap,
+                    res = visit(hash, a.H, logNB, (uint32_t)CK(nb[s], ix.n, 1004), spill_mode, bitmap,
                                 oldw);
                 if (!DEFER && res == V_PENDING)
                     res = (oldw & (1u << (nb[s] & 31))) ? V_SEEN : V_NEW_SPILL;
@@ -728,7 +743,7 @@ __global__ void __launch_bounds__(128, 5) k_search(DevIndex ix, SearchArgs a) {
                 hcount += __popc(__ballot_sync(FULLMASK, res == V_NEW));
                 nbs[s * 32 + lane] = nb[s];
             }
-            if (hcount > (a.H >> 1)) spill_mode = true;
+            if (hcount > a.H - (a.H >> 2)) spill_mode = true;
 
             // a4: per-centre prep (Sec. 3.2 identity for q^T c, Supplementary G)
             float ac = 0.f, qres2 = 0.f, qres_n = 0.f;
