@@ -217,11 +217,18 @@ def run_reference(args):
     import oracle
     c = workloads.config(args.cfg)
     n = args.n or c.n
-    X = workloads.base_vectors(args.cfg, n)
-    Q = workloads.query_vectors(args.cfg, args.nq or c.nq)
+    # the oracle's own input type (FP64), converted once before any timing
+    X = workloads.base_vectors(args.cfg, n).astype(np.float64)
+    Q = workloads.query_vectors(args.cfg, args.nq or c.nq).astype(np.float64)
     cores = os.cpu_count() or 1
-    sample = max(cores, 8)
-    # bounded sample: a few seconds of FP64 brute force per step on all cores
+    # bounded sample per step: as many queries (a multiple of the core count) as
+    # fit in the per-step budget, so the whole run stays within a few minutes
+    budget = min(1.0, 150.0 / max(1, args.warmup + args.steps))
+    t = time.perf_counter()
+    oracle.bruteforce(X, Q[:cores], c.K, threads=cores)
+    per = time.perf_counter() - t
+    sample = cores * max(1, int(budget / max(per, 1e-6)))
+    sample = min(sample, Q.shape[0])
     steps_t = []
     for i in range(args.warmup + args.steps):
         lo = (i * sample) % Q.shape[0]
@@ -231,8 +238,6 @@ def run_reference(args):
         dt = time.perf_counter() - t
         if i >= args.warmup:
             steps_t.append(dt)
-        if i == 0 and dt > 20 and sample > cores:
-            sample = cores
     ms = 1000 * statistics.median(steps_t)
     v = sample / (ms / 1000)
     line = {"impl": "reference", "metric": "queries/sec at recall@10=0.95, FINGER vs plain greedy search", "value": v,
@@ -254,6 +259,7 @@ def cpu_baseline(X, Q, K, budget_s=12.0):
     import oracle
     cores = os.cpu_count() or 1
     n = X.shape[0]
+    X, Q = X.astype(np.float64), Q.astype(np.float64)   # the oracle's input type, once
     # size the sample from a short probe
     t = time.perf_counter()
     oracle.bruteforce(X, Q[:cores], K, threads=cores)
