@@ -56,6 +56,8 @@ def parse():
                     help="graph build candidates per node (default: the workload's efConstruction)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--save-curves", default="")
+    ap.add_argument("--flat", action="store_true",
+                    help="single-layer graph (no HNSW hierarchy) instead of HNSW")
     ap.add_argument("--ablation", action="store_true",
                     help="Sec. 4.4 ablation (basis and matching variants) on --cfg")
     ap.add_argument("--profile-ef", type=int, default=0,
@@ -701,7 +703,7 @@ def main():
     ix = fg.Index(X, device=local)
     t0 = time.perf_counter()
     cands = args.candidates or c.ef_construction
-    ix.build_graph(c.M, candidates=cands, level_seed=3000 + args.cfg)
+    ix.build_graph(c.M, candidates=cands, level_seed=3000 + args.cfg, flat=args.flat)
     torch.cuda.synchronize()
     t_graph = time.perf_counter() - t0
     t0 = time.perf_counter()
@@ -854,8 +856,9 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": workload, "n": n, "m": c.m, "nq_per_gpu": nq, "K": K,
                        "M": c.M, "deg0": info["deg0"], "r": c.r, "ef_finger": ef_f,
-                       "ef_plain": ef_p, "graph": f"GPU HNSW, insertion order, {cands} exact "
-                                                  "candidates + heuristic selection",
+                       "ef_plain": ef_p,
+                       "graph": f"GPU {'single-layer' if args.flat else 'HNSW'}, insertion "
+                                f"order, {cands} exact candidates + heuristic selection",
                        "l2": "inputs larger than L2 (index ~9 GB), no flush",
                        "parallelism": f"replicas x{ws}, {nq} distinct queries per rank"},
             "recall_finger": rec_f, "recall_plain": rec_p, "plain_qps": plain_qps,

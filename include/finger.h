@@ -85,6 +85,8 @@ typedef struct {
     int symmetric;        /* 0 (default): HNSW insertion order, node i draws its
                              candidates from the nodes j < i of its level only;
                              1: from all nodes of its level */
+    int flat;             /* 1: every node on level 0 (no hierarchy, entry point
+                             node 0): a single-layer navigable small-world graph */
 } finger_graph_params;
 
 /* Build an HNSW graph on the device.  Levels are drawn as in HNSW from a

@@ -119,11 +119,16 @@ def upper_offsets(level: np.ndarray):
     return off, int(ends[-1]) if len(lv) else 0
 
 
-def hnsw_build(X, M: int, ef_construction: int, seed: int) -> Graph:
-    """Incremental HNSW in FP64, nodes inserted in id order (serial, deterministic)."""
+def hnsw_build(X, M: int, ef_construction: int, seed: int, flat: bool = False) -> Graph:
+    """Incremental HNSW in FP64, nodes inserted in id order (serial, deterministic).
+
+    ``flat=True`` puts every node on level 0: the same incremental insertion and
+    heuristic selection on a single layer (a navigable small-world graph without
+    the hierarchy), searched from node 0 -- a non-HNSW graph for FINGER, which
+    the paper builds "from any existing graph" (Sec. 3.3)."""
     X = _f64(X)
     n, m = X.shape
-    lv = levels(n, M, seed)
+    lv = np.zeros(n, np.int32) if flat else levels(n, M, seed)
     up_off, R = upper_offsets(lv)
     adj0 = np.empty((n, 2 * M), dtype=np.int32)
     up_adj = np.empty((max(R, 1), M), dtype=np.int32)

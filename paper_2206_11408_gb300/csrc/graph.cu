@@ -345,7 +345,7 @@ finger_status build_graph(finger_index* ix, const finger_graph_params* p, cudaSt
     for (int64_t i = 0; i < n; ++i) {
         const uint64_t h = splitmix64(p->level_seed ^ (uint64_t)i);
         const double u = (double)((h >> 11) + 1) * (1.0 / 9007199254740992.0);
-        int l = (int)floor(-log(u) * mL);
+        int l = p->flat ? 0 : (int)floor(-log(u) * mL);
         if (l > 30) l = 30;
         level[i] = l;
         maxlevel = std::max(maxlevel, l);

@@ -233,3 +233,31 @@ def test_wide_rows_k1_and_ef_equal_k():
             oi, od, oc = oracle.search(g, X, Q, K, ef, f)
             _compare(gi, gd, gc, oi, od, oc, gt, K, f"m=300 K={K} ef={ef} mode={mode}")
     ix.close()
+
+
+def test_flat_graph_parity_and_device_builder():
+    """FINGER over a non-HNSW graph (single layer, entry node 0): parity with
+    the oracle on the oracle's flat graph; the device builder's flat graph has
+    no hierarchy and is searchable."""
+    X = workloads.base_vectors(1, 4000)
+    Q = workloads.query_vectors(1, 150)
+    g = oracle.hnsw_build(X, 16, 80, 31, flat=True)
+    fp, _ = oracle.build_tables(X, g, 16, 32)
+    ix = fg.Index(X)
+    ix.set_graph(g.adj0, g.level, g.up_off, g.up_adj, g.entry, g.maxlevel, g.M)
+    ix.build_tables(16, 32, basis=fp.P, stats=fp.stats())
+    q = torch.from_numpy(Q).cuda()
+    gt, _ = oracle.bruteforce(X, Q, 10)
+    for mode, f in ((fg.MODE_PLAIN, None), (fg.MODE_FINGER, fp)):
+        gi, gd, gc = _gpu_search(ix, q, 10, 50, mode)
+        oi, od, oc = oracle.search(g, X, Q, 10, 50, f)
+        _compare(gi, gd, gc, oi, od, oc, gt, 10, f"flat mode={mode}")
+    ix.build_graph(16, 80, 31, flat=True)
+    gg = ix.get_graph()
+    assert (gg["level"] == 0).all() and gg["maxlevel"] == 0 and gg["entry"] == 0
+    ix.build_tables(16, 32)
+    ix.set_mode(fg.MODE_FINGER)
+    ids, _ = ix.search(q, 10, 100)
+    ix.sync()
+    assert oracle.recall(ids.cpu().numpy(), gt, 10) > 0.9
+    ix.close()

@@ -346,3 +346,23 @@ def test_memory_formula_matches_paper_table():
         n, M, r, fg, hg = int(n), int(M), int(r), float(fg), float(hg)
         extra = (r + 2) * n * 2 * M * 4 / 1e9
         assert abs(extra - (fg - hg)) / (fg - hg) < 0.10
+
+
+def test_flat_graph_is_single_layer_and_searchable():
+    """The single-layer option: every node on level 0, entry node 0, the layer-0
+    caps and invariants of the hierarchical build, and exhaustive search
+    (ef = n) finds the brute-force answer."""
+    X = workloads.base_vectors(1, 800)
+    Q = workloads.query_vectors(1, 20)
+    g = oracle.hnsw_build(X, 8, 40, 1, flat=True)
+    assert (g.level == 0).all() and g.maxlevel == 0 and g.entry == 0
+    assert g.up_adj.shape[0] == 0
+    for v in range(0, 800, 13):
+        row = g.adj0[v]
+        valid = row[row >= 0]
+        assert (row[len(valid):] == -1).all() and v not in valid
+        assert len(set(valid.tolist())) == len(valid)
+    ids, d, _ = oracle.search(g, X, Q, 5, 800)
+    gt, gd = oracle.bruteforce(X, Q, 5)
+    assert (ids == gt).all()
+    np.testing.assert_allclose(d, gd, rtol=1e-12)
