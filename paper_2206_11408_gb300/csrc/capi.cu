@@ -357,7 +357,8 @@ void finger_index_free(finger_index* ix) {
     void* ptrs[] = {ix->X, ix->xnorm2, ix->adj0, ix->up_off, ix->up_adj, ix->P, ix->Pc,
                     ix->edge_u, ix->edge_s, ix->Xh, ix->edge_q, ix->W1f, ix->W2f, ix->w3,
                     ix->b1, ix->b2, ix->work, ix->err, ix->cnt, ix->bitmap, ix->spill,
-                    ix->stage_q, ix->stage_ids, ix->stage_d, ix->eig_G, ix->eig_V};
+                    ix->stage_q, ix->stage_ids, ix->stage_d, ix->eig_G, ix->eig_V, ix->xs_hi,
+                    ix->xs_lo};
     for (void* p : ptrs) cudaFree(p);
     delete ix;
 }
@@ -627,10 +628,15 @@ finger_status finger_knn(finger_index* ix, const float* queries, int64_t nq, int
     if (nq == 0) return FINGER_OK;
     if (!queries || !out_ids || !out_dists) return FINGER_ERR_INVALID_ARG;
     DeviceGuard g(ix->device);
-    if (launch_knn(reinterpret_cast<const float4*>(ix->X), ix->n, ix->m4, queries, ix->m, ix->m,
-                   nq, K, false, nullptr, out_ids, out_dists, (cudaStream_t)stream) != cudaSuccess) {
+    cudaError_t e;
+    if (K <= knn_tc_max_k())
+        e = launch_knn_tc(ix, queries, nq, K, out_ids, out_dists, (cudaStream_t)stream);
+    else
+        e = launch_knn(reinterpret_cast<const float4*>(ix->X), ix->n, ix->m4, queries, ix->m, ix->m,
+                       nq, K, false, nullptr, out_ids, out_dists, (cudaStream_t)stream);
+    if (e != cudaSuccess) {
         cudaGetLastError();
-        return FINGER_ERR_CUDA;
+        return e == cudaErrorMemoryAllocation ? FINGER_ERR_OOM : FINGER_ERR_CUDA;
     }
     return FINGER_OK;
 }

@@ -114,6 +114,10 @@ cudaError_t launch_knn(const float4* Xb, int64_t nb, int m4, const float* Q, int
                        int q_m, int64_t nq, int K, bool exclude_self, const int32_t* remap,
                        int64_t* out_ids, float* out_d, cudaStream_t s, bool causal = false);
 size_t knn_smem(int K);
+// tensor-core exact kNN (knn_tc.cu): K <= knn_tc_max_k()
+int knn_tc_max_k();
+cudaError_t launch_knn_tc(finger_index* ix, const float* Q, int64_t nq, int K, int64_t* out_ids,
+                          float* out_d, cudaStream_t s);
 
 // graph construction (graph.cu)
 finger_status build_graph(finger_index* ix, const finger_graph_params* p, cudaStream_t s);
@@ -135,6 +139,8 @@ struct finger_index {
     int m = 0, m_pad = 0, m4 = 0, m8 = 0;
     float* X = nullptr;
     float* xnorm2 = nullptr;
+    __nv_bfloat16* xs_hi = nullptr;   // BF16 high / low parts of X (tensor-core kNN), lazily
+    __nv_bfloat16* xs_lo = nullptr;
     // graph
     int deg0 = 0, M = 0, maxlevel = 0, entry = 0;
     int64_t up_rows = 0;

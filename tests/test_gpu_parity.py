@@ -261,3 +261,22 @@ def test_flat_graph_parity_and_device_builder():
     ix.sync()
     assert oracle.recall(ids.cpu().numpy(), gt, 10) > 0.9
     ix.close()
+
+
+@pytest.mark.parametrize("m,K", [(64, 10), (64, 1), (64, 40), (64, 64), (50, 10), (300, 16)])
+def test_bruteforce_paths_match_oracle(m, K):
+    """Exact kNN on the tensor cores (K <= 40: BF16 split products in tensor
+    memory, FP32 re-rank) and on FFMA (K > 40), against the FP64 oracle; n and
+    nq not multiples of the 128-row tiles, m = 50 (zero-filled K tail) and
+    m = 300 (five K chunks)."""
+    cfg = 5 if m > 64 else 1
+    X = np.ascontiguousarray(workloads.base_vectors(cfg, 3001)[:, :m])
+    Q = np.ascontiguousarray(workloads.query_vectors(cfg, 77)[:, :m])
+    ix = fg.Index(X)
+    ids, d = ix.knn(torch.from_numpy(Q).cuda(), K)
+    torch.cuda.synchronize()
+    ids, d = ids.cpu().numpy(), d.cpu().numpy()
+    gt, gd = oracle.bruteforce(X, Q, K)
+    assert (ids == gt).mean() > 0.999, (ids != gt).sum()
+    np.testing.assert_allclose(d, gd, rtol=REL)
+    ix.close()
