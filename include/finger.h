@@ -316,7 +316,12 @@ finger_status finger_mlp_predict(finger_index* ix, const float* feat, int64_t n,
 
 /* Exact K nearest neighbours of nq queries (device, nq x m) over all n base
  * rows by brute force on the GPU; ascending (distance, id), distances summed
- * as (q - x)^2 in FP32.  K <= 256.  Asynchronous. */
+ * as (q - x)^2 in FP32.  K <= 256.  For K <= 40 the distance matrix runs on
+ * the tensor cores (q.x from BF16 high/low split products accumulated in FP32
+ * in tensor memory, candidate lists of 32 or 64 per row, then an exact FP32
+ * re-rank); larger K use FP32 FFMA tiles.  Asynchronous (stream-ordered
+ * temporaries; the first tensor-core call caches a BF16 split of the base rows,
+ * 4 bytes per element). */
 finger_status finger_knn(finger_index* ix, const float* queries, int64_t nq, int K,
                          int64_t* out_ids, float* out_dists, void* stream);
 
