@@ -327,81 +327,6 @@ __device__ __forceinline__ float edge_cos(const DevIndex& ix, size_t e, const fl
     return acc;
 }
 
-// t_hat for a list of edges of one centre: edge rows (contiguous per centre)
-// are gathered by groups of GE lanes, one 16-byte chunk per lane, U rows per
-// group in flight; the partial dots are reduced inside the group and written
-// to out[o] for list entry o = lst[i] (the neighbour slot).
-template <bool LP>
-__device__ __forceinline__ void edge_cos_list(const DevIndex& ix, size_t ebase, const float* uq,
-                                              const int* lst, int nn, float* out, int lane) {
-    constexpr int U = 4;
-    constexpr int W = LP ? 16 : 4;
-    const int nch = LP ? ix.r16 : ix.r4;
-    const int r_pad = ix.r4 * 4;
-    int GE = 1;
-    while (GE < nch) GE <<= 1;
-    const int RPW = 32 / GE, grp = lane / GE, kin = lane % GE;
-    float qv[W];
-#pragma unroll
-    for (int e = 0; e < W; ++e) {
-        const int k = kin * W + e;
-        qv[e] = (kin < nch && k < r_pad) ? uq[k] : 0.f;
-    }
-    for (int base = 0; base < nn; base += U * RPW) {
-        int o[U];
-        float p[U];
-        if constexpr (!LP) {
-            float4 x[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int i = base + u * RPW + grp;
-                o[u] = i < nn ? lst[i] : -1;
-                x[u] = (o[u] >= 0 && kin < nch) ? __ldg(ix.edge_u + (ebase + o[u]) * ix.r4 + kin)
-                                               : make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u)
-                p[u] = fmaf(x[u].x, qv[0], fmaf(x[u].y, qv[1], fmaf(x[u].z, qv[2], x[u].w * qv[3])));
-        } else {
-            uint4 x[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int i = base + u * RPW + grp;
-                o[u] = i < nn ? lst[i] : -1;
-                x[u] = (o[u] >= 0 && kin < nch) ? __ldg(ix.edge_q + (ebase + o[u]) * ix.r16 + kin)
-                                               : make_uint4(0u, 0u, 0u, 0u);
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const uint32_t w[4] = {x[u].x, x[u].y, x[u].z, x[u].w};
-                float acc = 0.f;
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const __half2_raw lo = __nv_cvt_fp8x2_to_halfraw2(
-                        (__nv_fp8x2_storage_t)(w[i] & 0xFFFFu), __NV_E4M3);
-                    const __half2_raw hi = __nv_cvt_fp8x2_to_halfraw2(
-                        (__nv_fp8x2_storage_t)(w[i] >> 16), __NV_E4M3);
-                    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&lo));
-                    const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&hi));
-                    acc = fmaf(a.x, qv[4 * i + 0], acc);
-                    acc = fmaf(a.y, qv[4 * i + 1], acc);
-                    acc = fmaf(b.x, qv[4 * i + 2], acc);
-                    acc = fmaf(b.y, qv[4 * i + 3], acc);
-                }
-                p[u] = acc * ix.code_inv;
-            }
-        }
-        for (int off = GE >> 1; off > 0; off >>= 1)
-#pragma unroll
-            for (int u = 0; u < U; ++u) p[u] += __shfl_xor_sync(FULLMASK, p[u], off);
-        if (kin == 0)
-#pragma unroll
-            for (int u = 0; u < U; ++u)
-                if (o[u] >= 0) out[o[u]] = p[u];
-    }
-    __syncwarp();
-}
-
 // Features of one (q, c, d) triple for the learned angle predictor (an
 // extension; the paper has no learned predictor): f = [u_q * u_d (r values),
 // t_hat, ||q_res|| / ||q||, ||d_res|| / ||d||, a / (|a| + |b| + 1e-6)], with
