@@ -47,7 +47,23 @@ def _gpu_search(ix, q, K, ef, mode, warmup=5):
     return ids.cpu().numpy(), d.cpu().numpy(), cnt.cpu().numpy()
 
 
+def _fp32_canonical(oi, od):
+    """The oracle's lists reordered by (FP32 distance, id): the kernel computes
+    distances in FP32 and breaks exact ties by id, so two entries whose FP64
+    distances differ below FP32 resolution are a tie at the kernel's precision
+    (their order is not unique; the set and the traversal still are)."""
+    d32 = od.astype(np.float32)
+    out = oi.copy()
+    for qi in range(oi.shape[0]):
+        valid = oi[qi] >= 0
+        order = np.lexsort((oi[qi][valid], d32[qi][valid]))
+        out[qi, :valid.sum()] = oi[qi][valid][order]
+    return out
+
+
 def _compare(gi, gd, gc, oi, od, oc, gt, K, what):
+    oi = _fp32_canonical(oi, od)
+    od = np.sort(od, axis=1)
     match = (gi == oi).all(axis=1)
     assert match.mean() >= 0.99, f"{what}: {match.mean():.4f} of lists identical"
     ok = oi[match] >= 0
@@ -280,3 +296,18 @@ def test_bruteforce_paths_match_oracle(m, K):
     assert (ids == gt).mean() > 0.999, (ids != gt).sum()
     np.testing.assert_allclose(d, gd, rtol=REL)
     ix.close()
+
+
+def test_maximum_ef_and_k(cfg1):
+    """ef at the compiled maximum (1024) and K = 256 on the 10,000-point index:
+    the result list holds 1024 entries, most visits go through the spill path,
+    and the traversal still equals the oracle's."""
+    q = cfg1["q"][:40]
+    Q = cfg1["Q"][:40]
+    gt, _ = oracle.bruteforce(cfg1["X"], Q, 256)
+    for mode, f in ((fg.MODE_PLAIN, None), (fg.MODE_FINGER, cfg1["fp"])):
+        gi, gd, gc = _gpu_search(cfg1["ix"], q, 256, 1024, mode)
+        oi, od, oc = oracle.search(cfg1["g"], cfg1["X"], Q, 256, 1024, f)
+        _compare(gi, gd, gc, oi, od, oc, gt, 256, f"ef=1024 K=256 mode={mode}")
+    with pytest.raises(fg.FingerError):
+        cfg1["ix"].search(q, 10, 1025)                  # above the compiled maximum
