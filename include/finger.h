@@ -87,6 +87,9 @@ typedef struct {
                              1: from all nodes of its level */
     int flat;             /* 1: every node on level 0 (no hierarchy, entry point
                              node 0): a single-layer navigable small-world graph */
+    int fp32_candidates;  /* 1: layer-0 candidates by FP32 FFMA distances; 0
+                             (default): on the tensor cores (BF16 high/low split
+                             products, ~1e-5 relative distance error) */
 } finger_graph_params;
 
 /* Build an HNSW graph on the device.  Levels are drawn as in HNSW from a

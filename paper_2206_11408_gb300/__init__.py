@@ -38,7 +38,8 @@ class FingerError(RuntimeError):
 
 class GraphParams(ctypes.Structure):
     _fields_ = [("M", ctypes.c_int), ("candidates", ctypes.c_int), ("level_seed", ctypes.c_uint64),
-                ("symmetric", ctypes.c_int), ("flat", ctypes.c_int)]
+                ("symmetric", ctypes.c_int), ("flat", ctypes.c_int),
+                ("fp32_candidates", ctypes.c_int)]
 
 
 class BuildParams(ctypes.Structure):
@@ -214,11 +215,14 @@ class Index:
             "finger_index_set_graph")
 
     def build_graph(self, M: int, candidates: int = 0, level_seed: int = 0,
-                    symmetric: bool = False, flat: bool = False, stream=None):
+                    symmetric: bool = False, flat: bool = False, fp32_candidates: bool = False,
+                    stream=None):
         """finger_build_graph: HNSW on the device (insertion order by id, exact
         candidate search); symmetric=True draws candidates from all nodes;
-        flat=True builds the single-layer graph (no hierarchy, entry node 0)."""
-        p = GraphParams(M, candidates, level_seed, int(symmetric), int(flat))
+        flat=True builds the single-layer graph (no hierarchy, entry node 0);
+        fp32_candidates=True ranks layer-0 candidates with FP32 FFMA distances
+        instead of the tensor cores."""
+        p = GraphParams(M, candidates, level_seed, int(symmetric), int(flat), int(fp32_candidates))
         _check(self._lib.finger_build_graph(self._h, ctypes.byref(p), _stream_ptr(stream)),
                "finger_build_graph")
 

@@ -229,7 +229,7 @@ T* dalloc(size_t count) {
 // of width out_w at out_row[...] (global rows for layer 0, up_adj rows above)
 finger_status build_layer(finger_index* ix, const int32_t* d_nodes, int64_t cnt, int kc, int Mf,
                           int Mmax, uint32_t* out, int out_w, const int64_t* d_out_row,
-                          const int32_t* d_cmap, bool causal, cudaStream_t s) {
+                          const int32_t* d_cmap, bool causal, bool tensor, cudaStream_t s) {
     finger_status status = FINGER_OK;
     const int m4 = ix->m4;
     float4* Xl = nullptr;
@@ -278,9 +278,12 @@ finger_status build_layer(finger_index* ix, const int32_t* d_nodes, int64_t cnt,
         status = FINGER_ERR_OOM;
         goto done;
     }
-    CK(launch_knn(d_nodes ? Xl : reinterpret_cast<const float4*>(ix->X), cnt, m4,
-                  d_nodes ? reinterpret_cast<const float*>(Xl) : ix->X, (int64_t)m4 * 4, m4 * 4,
-                  cnt, kk, true, d_nodes, cid, cd, s, causal));
+    if (tensor && causal && !d_nodes)   // layer 0: causal candidates on the tensor cores
+        CK(launch_knn_tc_causal(ix, kk, cid, cd, s));
+    else
+        CK(launch_knn(d_nodes ? Xl : reinterpret_cast<const float4*>(ix->X), cnt, m4,
+                      d_nodes ? reinterpret_cast<const float*>(Xl) : ix->X, (int64_t)m4 * 4,
+                      m4 * 4, cnt, kk, true, d_nodes, cid, cd, s, causal));
     k_select<<<(unsigned)wblocks, 128, 0, s>>>(reinterpret_cast<const float4*>(ix->X), m4, cid, cd,
                                                kk, cnt, Mf, fwd, fwd_d, Mf, nullptr);
     CK(cudaGetLastError());
@@ -383,7 +386,8 @@ finger_status build_graph(finger_index* ix, const finger_graph_params* p, cudaSt
     }
     {
         CK(cudaMemcpy(d_up_off, up_off.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice));
-        status = build_layer(ix, nullptr, n, kc, M, deg0, adj0, deg0, nullptr, nullptr, causal, s);
+        status = build_layer(ix, nullptr, n, kc, M, deg0, adj0, deg0, nullptr, nullptr, causal,
+                             p->fp32_candidates == 0, s);
         if (status != FINGER_OK) goto done;
         if (maxlevel > 0) {
             d_nodes = dalloc<int32_t>((size_t)n);
@@ -411,7 +415,7 @@ finger_status build_graph(finger_index* ix, const finger_graph_params* p, cudaSt
             // upper layers are small: offer up to 256 exact candidates so that the
             // selection sees beyond a node's own cluster and keeps long links
             status = build_layer(ix, d_nodes, cnt, (int)std::min<int64_t>(cnt - 1, 256), M, M,
-                                 up_adj, M, d_rows, d_cmap, causal, s);
+                                 up_adj, M, d_rows, d_cmap, causal, false, s);
             if (status != FINGER_OK) goto done;
         }
     }

@@ -118,6 +118,8 @@ size_t knn_smem(int K);
 int knn_tc_max_k();
 cudaError_t launch_knn_tc(finger_index* ix, const float* Q, int64_t nq, int K, int64_t* out_ids,
                           float* out_d, cudaStream_t s);
+cudaError_t launch_knn_tc_causal(finger_index* ix, int K, int64_t* out_ids, float* out_d,
+                                 cudaStream_t s);
 
 // graph construction (graph.cu)
 finger_status build_graph(finger_index* ix, const finger_graph_params* p, cudaStream_t s);

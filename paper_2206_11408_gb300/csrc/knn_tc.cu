@@ -49,14 +49,23 @@ struct TcArgs {
     int64_t nq, n;
     int nchunk;           // ceil(m / 64)
     int nbt;              // base tiles
-    int nseg;             // base segments per query tile
-    int seg_tiles;        // base tiles per segment
+    int nseg;             // base segments per query tile; segment s holds the base
+                          // tiles s, s + nseg, s + 2 nseg, ... (interleaved)
     int nqt;              // query tiles
+    int causal;           // 1: queries are the base rows, row i sees base rows < i
     const float* qn;      // ||q||^2 (FP32), nq
     const float* xn;      // ||x||^2 (FP32), n
     int32_t* cand;        // nq x nseg x KP candidate ids (-1 = none)
+    float* cand_d;        // optional: their approximate distances
     int* err;             // device status word (FINGER_ERR_LIMIT on a wait timeout)
 };
+
+// work item -> (query tile, segment): the largest causal items first
+__device__ __forceinline__ void item_of(const TcArgs& a, int item, int& qt, int& seg, int& bt_end) {
+    qt = a.causal ? a.nqt - 1 - item / a.nseg : item / a.nseg;
+    seg = item % a.nseg;
+    bt_end = a.causal ? min(a.nbt, qt + 1) : a.nbt;
+}
 
 __device__ __forceinline__ uint32_t s32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -163,9 +172,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if (lane == 0) {
             uint32_t it = 0;
             for (int item = blockIdx.x; item < items && !*abort_flag; item += gridDim.x) {
-                const int qt = item / a.nseg, seg = item % a.nseg;
-                const int b0 = seg * a.seg_tiles, b1 = min(a.nbt, b0 + a.seg_tiles);
-                for (int bt = b0; bt < b1 && !*abort_flag; ++bt)
+                int qt, seg, bt_end;
+                item_of(a, item, qt, seg, bt_end);
+                for (int bt = seg; bt < bt_end && !*abort_flag; bt += a.nseg)
                     for (int c = 0; c < a.nchunk; ++c, ++it) {
                         const int s = it % STAGES;
                         const uint32_t ph = (it / STAGES) & 1u;
@@ -189,9 +198,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                                    ((uint32_t)(TQ >> 4) << 24);
             uint32_t it = 0, tile = 0;
             for (int item = blockIdx.x; item < items && !*abort_flag; item += gridDim.x) {
-                const int seg = item % a.nseg;
-                const int b0 = seg * a.seg_tiles, b1 = min(a.nbt, b0 + a.seg_tiles);
-                for (int bt = b0; bt < b1 && !*abort_flag; ++bt, ++tile) {
+                int qt, seg, bt_end;
+                item_of(a, item, qt, seg, bt_end);
+                for (int bt = seg; bt < bt_end && !*abort_flag; bt += a.nseg, ++tile) {
                     const uint32_t b = tile & 1u, tph = (tile >> 1) & 1u;
                     if (!wait_bar(acce0 + 8 * b, tph ^ 1u, abort_flag, a.err)) break;
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -228,9 +237,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const int row = 32 * (warp & 3) + lane;
         uint32_t tile = 0;
         for (int item = blockIdx.x; item < items && !*abort_flag; item += gridDim.x) {
-            const int qt = item / a.nseg, seg = item % a.nseg;
-            const int b0 = seg * a.seg_tiles, b1 = min(a.nbt, b0 + a.seg_tiles);
+            int qt, seg, bt_end;
+            item_of(a, item, qt, seg, bt_end);
             const int64_t qi = (int64_t)qt * TQ + row;
+            const int64_t id_end = a.causal ? min(qi, a.n) : a.n;   // ids below this count
             const float qn = qi < a.nq ? a.qn[qi] : 0.f;
             for (int k = 0; k < KP; ++k) {
                 Ld[k * TQ + row] = INFINITY;
@@ -238,7 +248,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             }
             int cnt = 0;
             float thr = INFINITY;
-            for (int bt = b0; bt < b1; ++bt, ++tile) {
+            for (int bt = seg; bt < bt_end; bt += a.nseg, ++tile) {
                 const uint32_t b = tile & 1u, tph = (tile >> 1) & 1u;
                 if (!wait_bar(accf0 + 8 * b, tph, abort_flag, a.err)) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -251,7 +261,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     for (int j = 0; j < 32; ++j) {
                         const int64_t id = id0 + j;
                         const float dd =
-                            id < a.n ? fmaf(-2.f, v[j], qn + __ldg(a.xn + id)) : INFINITY;
+                            id < id_end ? fmaf(-2.f, v[j], qn + __ldg(a.xn + id)) : INFINITY;
                         if (dd < thr) {
                             int p = cnt < KP ? cnt : KP - 1;
                             while (p > 0 && Ld[(p - 1) * TQ + row] > dd) {
@@ -270,8 +280,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(acce0 + 8 * b) : "memory");
             }
             if (qi < a.nq) {
-                int32_t* out = a.cand + ((size_t)qi * a.nseg + seg) * KP;
-                for (int k = 0; k < KP; ++k) out[k] = Li[k * TQ + row];
+                const size_t o = ((size_t)qi * a.nseg + seg) * KP;
+                for (int k = 0; k < KP; ++k) a.cand[o + k] = Li[k * TQ + row];
+                if (a.cand_d)
+                    for (int k = 0; k < KP; ++k) a.cand_d[o + k] = Ld[k * TQ + row];
             }
         }
     }
@@ -364,6 +376,41 @@ __global__ void k_rerank(const float4* __restrict__ X, int m4, const float* __re
     }
 }
 
+// Merge of the segments' candidate lists by approximate distance: the K
+// smallest (distance, id) of every row, int64 ids (-1 padded); one warp per row
+__global__ void k_merge_topk(const int32_t* __restrict__ cand, const float* __restrict__ cand_d,
+                             int64_t rows, int nc, int K, int64_t* out_ids, float* out_d) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (w >= rows) return;
+    const int32_t* ci = cand + (size_t)w * nc;
+    const float* cd = cand_d + (size_t)w * nc;
+    int valid = 0;
+    for (int i = lane; i < nc; i += 32) {
+        const int32_t ii = ci[i];
+        if (ii < 0) continue;
+        valid++;
+        const float di = cd[i];
+        int rank = 0;
+        for (int j = 0; j < nc; ++j) {
+            const int32_t ij = ci[j];
+            if (ij < 0) continue;
+            const float dj = cd[j];
+            rank += dj < di || (dj == di && ij < ii);
+        }
+        if (rank < K) {
+            out_ids[(size_t)w * K + rank] = ii;
+            out_d[(size_t)w * K + rank] = di;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) valid += __shfl_xor_sync(0xffffffffu, valid, o);
+    for (int k = valid + lane; k < K; k += 32) {
+        out_ids[(size_t)w * K + k] = -1;
+        out_d[(size_t)w * K + k] = INFINITY;
+    }
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     if (!fn) {
@@ -410,36 +457,72 @@ cudaError_t run_tc(const CUtensorMap* maps, TcArgs a, int grid, cudaStream_t s) 
 // Largest K the tensor-core path serves (its candidate lists hold 32 or 64).
 int knn_tc_max_k() { return 40; }
 
+namespace {
+
+// BF16 split of the base rows, made once per index
+cudaError_t ensure_split(finger_index* ix, cudaStream_t s) {
+    if (ix->xs_hi) return cudaSuccess;
+    const int m = ix->m, ms = (m + 7) & ~7;
+    const int64_t n = ix->n;
+    if (cudaMalloc(&ix->xs_hi, sizeof(__nv_bfloat16) * (size_t)n * ms) != cudaSuccess ||
+        cudaMalloc(&ix->xs_lo, sizeof(__nv_bfloat16) * (size_t)n * ms) != cudaSuccess) {
+        cudaFree(ix->xs_hi);
+        ix->xs_hi = nullptr;
+        ix->xs_lo = nullptr;
+        cudaGetLastError();
+        return cudaErrorMemoryAllocation;
+    }
+    k_split_bf16<<<(unsigned)((n * 32 + 255) / 256), 256, 0, s>>>(ix->X, n, m, ix->m_pad, ms,
+                                                                  ix->xs_hi, ix->xs_lo, nullptr);
+    return cudaGetLastError();
+}
+
+// one launch of k_knn_tc over nq query rows (BF16 parts qh/ql) against the base
+cudaError_t run_items(finger_index* ix, const __nv_bfloat16* qh, const __nv_bfloat16* ql,
+                      const float* qn, int64_t nq, int KP, int nseg, bool causal, int32_t* cand,
+                      float* cand_d, cudaStream_t s) {
+    const int m = ix->m, ms = (m + 7) & ~7;
+    const int64_t n = ix->n;
+    CUtensorMap maps[4];
+    if (!make_map(&maps[0], qh, nq, m, ms) || !make_map(&maps[1], ql, nq, m, ms) ||
+        !make_map(&maps[2], ix->xs_hi, n, m, ms) || !make_map(&maps[3], ix->xs_lo, n, m, ms))
+        return cudaErrorInvalidValue;
+    TcArgs a;
+    a.nq = nq;
+    a.n = n;
+    a.nchunk = (m + KCH - 1) / KCH;
+    a.nbt = (int)((n + TB - 1) / TB);
+    a.nseg = nseg;
+    a.nqt = (int)((nq + TQ - 1) / TQ);
+    a.causal = causal ? 1 : 0;
+    a.qn = qn;
+    a.xn = ix->xnorm2;
+    a.cand = cand;
+    a.cand_d = cand_d;
+    a.err = ix->err;
+    const int grid = (int)std::min<int64_t>(ix->num_sms, (int64_t)a.nqt * nseg);
+    return KP == 32 ? run_tc<32>(maps, a, grid, s) : run_tc<64>(maps, a, grid, s);
+}
+
+}  // namespace
+
 cudaError_t launch_knn_tc(finger_index* ix, const float* Q, int64_t nq, int K, int64_t* out_ids,
                           float* out_d, cudaStream_t s) {
     if (nq <= 0) return cudaSuccess;
     const int m = ix->m, ms = (m + 7) & ~7;
     const int64_t n = ix->n;
-    // cached BF16 split of the base rows
-    if (!ix->xs_hi) {
-        if (cudaMalloc(&ix->xs_hi, sizeof(__nv_bfloat16) * (size_t)n * ms) != cudaSuccess ||
-            cudaMalloc(&ix->xs_lo, sizeof(__nv_bfloat16) * (size_t)n * ms) != cudaSuccess) {
-            cudaFree(ix->xs_hi);
-            ix->xs_hi = nullptr;
-            return cudaErrorMemoryAllocation;
-        }
-        k_split_bf16<<<(unsigned)((n * 32 + 255) / 256), 256, 0, s>>>(
-            ix->X, n, m, ix->m_pad, ms, ix->xs_hi, ix->xs_lo, nullptr);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-    }
+    cudaError_t e = ensure_split(ix, s);
+    if (e != cudaSuccess) return e;
     const int KP = K <= 16 ? 32 : 64;
     const int nqt = (int)((nq + TQ - 1) / TQ);
     const int nbt = (int)((n + TB - 1) / TB);
-    // enough (query tile, base segment) items for two per SM, at most 64 segments
-    int nseg = std::max(1, std::min({nbt, 64, (2 * ix->num_sms + nqt - 1) / nqt}));
-    const int seg_tiles = (nbt + nseg - 1) / nseg;
-    nseg = (nbt + seg_tiles - 1) / seg_tiles;
+    // enough (query tile, base segment) items for two per SM, at most 64
+    // segments; any segmentation is exact here because K <= KP
+    const int nseg = std::max(1, std::min({nbt, 64, (2 * ix->num_sms + nqt - 1) / nqt}));
     const int nc = nseg * KP;
     __nv_bfloat16 *qh = nullptr, *ql = nullptr;
     float* qn = nullptr;
     int32_t* cand = nullptr;
-    cudaError_t e = cudaSuccess;
     if (cudaMallocAsync(&qh, sizeof(__nv_bfloat16) * (size_t)nq * ms, s) != cudaSuccess ||
         cudaMallocAsync(&ql, sizeof(__nv_bfloat16) * (size_t)nq * ms, s) != cudaSuccess ||
         cudaMallocAsync(&qn, sizeof(float) * (size_t)nq, s) != cudaSuccess ||
@@ -449,29 +532,8 @@ cudaError_t launch_knn_tc(finger_index* ix, const float* Q, int64_t nq, int K, i
     }
     k_split_bf16<<<(unsigned)((nq * 32 + 255) / 256), 256, 0, s>>>(Q, nq, m, m, ms, qh, ql, qn);
     if ((e = cudaGetLastError()) != cudaSuccess) goto done;
-    {
-        CUtensorMap maps[4];
-        if (!make_map(&maps[0], qh, nq, m, ms) || !make_map(&maps[1], ql, nq, m, ms) ||
-            !make_map(&maps[2], ix->xs_hi, n, m, ms) || !make_map(&maps[3], ix->xs_lo, n, m, ms)) {
-            e = cudaErrorInvalidValue;
-            goto done;
-        }
-        TcArgs a;
-        a.nq = nq;
-        a.n = n;
-        a.nchunk = (m + KCH - 1) / KCH;
-        a.nbt = nbt;
-        a.nseg = nseg;
-        a.seg_tiles = seg_tiles;
-        a.nqt = nqt;
-        a.qn = qn;
-        a.xn = ix->xnorm2;
-        a.cand = cand;
-        a.err = ix->err;
-        const int grid = std::min(ix->num_sms, nqt * nseg);
-        e = KP == 32 ? run_tc<32>(maps, a, grid, s) : run_tc<64>(maps, a, grid, s);
-        if (e != cudaSuccess) goto done;
-    }
+    if ((e = run_items(ix, qh, ql, qn, nq, KP, nseg, false, cand, nullptr, s)) != cudaSuccess)
+        goto done;
     {
         const int wpb = nc > 1024 ? 1 : 4;
         const size_t smem = (size_t)wpb * 2 * nc * sizeof(float);
@@ -489,6 +551,41 @@ done:
     if (ql) cudaFreeAsync(ql, s);
     if (qn) cudaFreeAsync(qn, s);
     if (cand) cudaFreeAsync(cand, s);
+    return e;
+}
+
+// Causal candidates of the graph builder on the tensor cores: for every base
+// row i, the K (<= 256) smallest approximate distances to the rows j < i,
+// ascending by (distance, id), int64 ids padded with -1.  Eight interleaved
+// base segments keep 64 each: with random ids a node's K nearest spread over
+// the segments (for K = 256, 32 per segment on average), so the merged lists
+// are its K nearest; only the first rows (fewer than 8 x 128 predecessors)
+// can lose candidates beyond 64 of one tile.  Distances carry the BF16-split
+// error (~1e-5 relative), which candidate selection tolerates.
+cudaError_t launch_knn_tc_causal(finger_index* ix, int K, int64_t* out_ids, float* out_d,
+                                 cudaStream_t s) {
+    const int64_t n = ix->n;
+    if (n <= 1) return cudaSuccess;
+    cudaError_t e = ensure_split(ix, s);
+    if (e != cudaSuccess) return e;
+    constexpr int KP = 64, NSEG = 8;
+    const int nc = NSEG * KP;
+    int32_t* cand = nullptr;
+    float* cand_d = nullptr;
+    if (cudaMallocAsync(&cand, sizeof(int32_t) * (size_t)n * nc, s) != cudaSuccess ||
+        cudaMallocAsync(&cand_d, sizeof(float) * (size_t)n * nc, s) != cudaSuccess) {
+        e = cudaErrorMemoryAllocation;
+        goto done;
+    }
+    if ((e = run_items(ix, ix->xs_hi, ix->xs_lo, ix->xnorm2, n, KP, NSEG, true, cand, cand_d, s)) !=
+        cudaSuccess)
+        goto done;
+    k_merge_topk<<<(unsigned)((n * 32 + 255) / 256), 256, 0, s>>>(cand, cand_d, n, nc, K, out_ids,
+                                                                 out_d);
+    e = cudaGetLastError();
+done:
+    if (cand) cudaFreeAsync(cand, s);
+    if (cand_d) cudaFreeAsync(cand_d, s);
     return e;
 }
 

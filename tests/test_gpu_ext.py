@@ -217,6 +217,30 @@ def test_gpu_graph_insertion_order_links_clusters():
     ix.close()
 
 
+def test_tensor_core_candidates_match_fp32_candidates():
+    """Layer-0 candidates ranked on the tensor cores (BF16 split products)
+    against FP32 FFMA: nearly the same graph and the same search quality."""
+    X = workloads.base_vectors(2, 12000)
+    Q = workloads.query_vectors(2, 200)
+    q = torch.from_numpy(Q).cuda()
+    gt, _ = oracle.bruteforce(X, Q, 10)
+    res = {}
+    for fp32 in (True, False):
+        ix = fg.Index(X)
+        ix.build_graph(16, 200, 3002, fp32_candidates=fp32)
+        g = ix.get_graph()
+        ix.set_mode(fg.MODE_PLAIN)
+        ids, _ = ix.search(q, 10, 60)
+        ix.sync()
+        res[fp32] = (g["adj0"], oracle.recall(ids.cpu().numpy(), gt, 10))
+        ix.close()
+    a, b = res[True][0], res[False][0]
+    same = np.mean([len(np.intersect1d(x[x >= 0], y[y >= 0])) / max(1, len(np.union1d(x[x >= 0], y[y >= 0])))
+                    for x, y in zip(a, b)])
+    assert same > 0.95, same
+    assert abs(res[True][1] - res[False][1]) < 0.01, (res[True][1], res[False][1])
+
+
 def test_kernel_limit_is_reported_not_faulted():
     """A search that hits the expansion cap returns FINGER_ERR_LIMIT through the
     status word instead of running on; the context stays usable afterwards."""
