@@ -17,8 +17,12 @@
 //   warp 1     MMA issuer (one elected lane): 3 products x 4 K-steps per chunk
 //              into one of two 128x128 FP32 accumulators in tensor memory
 //   warps 2-5  epilogue: tcgen05.ld of the accumulator (thread = query row),
-//              distance, and insertion into the row's sorted K' list in shared
-//              memory; the accumulator is handed back through an mbarrier
+//              distances and their per-row minimum against the row's K'-th
+//              distance; the few rows with a smaller one are transposed
+//              through shared memory and their new candidates inserted into
+//              the row's sorted K' list by the whole warp (ballot for the
+//              position, shuffle for the shift); the accumulator is handed
+//              back through an mbarrier
 // Work items are (query tile of 128, segment of base tiles), so small query
 // batches still fill the GPU.  Every mbarrier wait is bounded: on a timeout the
 // kernel raises an error flag, every role leaves its loop, and tensor memory is
@@ -135,12 +139,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     k_knn_tc(const __grid_constant__ CUtensorMap tqh, const __grid_constant__ CUtensorMap tql,
              const __grid_constant__ CUtensorMap txh, const __grid_constant__ CUtensorMap txl,
              TcArgs a) {
+    static_assert(KP == 32 || KP == 64, "candidate lists of 32 or 64");
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned char* stages = sm;                                   // STAGES x 64 KB
-    float* Ld = reinterpret_cast<float*>(sm + STAGES * STAGE_BYTES);   // KP x 128 (k-major)
+    float* Ld = reinterpret_cast<float*>(sm + STAGES * STAGE_BYTES);   // 128 x KP (row-major)
     int32_t* Li = reinterpret_cast<int32_t*>(Ld + KP * TQ);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(Li + KP * TQ);   // full[2] empty[2] accf[2] acce[2]
+    float* Bs = reinterpret_cast<float*>(Li + KP * TQ);                // 4 x 32 x 33
+    uint64_t* bars = reinterpret_cast<uint64_t*>(Bs + 4 * 32 * 33);   // full[2] empty[2] accf[2] acce[2]
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 8);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -233,58 +239,142 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             }
         }
     } else {
-        // epilogue: thread <-> query row; warp w reads tensor-memory lanes 32 (w % 4) + lane
-        const int row = 32 * (warp & 3) + lane;
+        // epilogue: warp w owns the query rows 32 (w % 4) + lane of every tile
+        // (the tensor-memory lanes it may read).  Per 32-column block a thread
+        // forms its row's 32 distances and their minimum; only rows whose
+        // minimum beats their K'-th distance go on, through a transpose in
+        // shared memory, to a warp-wide insertion into the row's sorted list.
+        const int quarter = warp & 3;
+        const int row = 32 * quarter + lane;
+        float* B = Bs + (warp - 2) * 32 * 33;               // 32 x 32 transpose, padded
+        float* Lw = Ld + (size_t)quarter * 32 * KP;          // this warp's 32 lists, row-major
+        int32_t* Lwi = Li + (size_t)quarter * 32 * KP;
         uint32_t tile = 0;
         for (int item = blockIdx.x; item < items && !*abort_flag; item += gridDim.x) {
             int qt, seg, bt_end;
             item_of(a, item, qt, seg, bt_end);
-            const int64_t qi = (int64_t)qt * TQ + row;
+            const int64_t q0 = (int64_t)qt * TQ;
+            const int64_t qi = q0 + row;
             const int64_t id_end = a.causal ? min(qi, a.n) : a.n;   // ids below this count
+            const int64_t lim = a.causal ? min(q0, a.n) : a.n;      // smallest id_end of the tile
             const float qn = qi < a.nq ? a.qn[qi] : 0.f;
-            for (int k = 0; k < KP; ++k) {
-                Ld[k * TQ + row] = INFINITY;
-                Li[k * TQ + row] = -1;
+            float thr = qi < a.nq ? INFINITY : -INFINITY;            // K'-th distance of the row
+            for (int k = lane; k < 32 * KP; k += 32) {
+                Lw[k] = INFINITY;
+                Lwi[k] = -1;
             }
-            int cnt = 0;
-            float thr = INFINITY;
+            __syncwarp();
             for (int bt = seg; bt < bt_end; bt += a.nseg, ++tile) {
                 const uint32_t b = tile & 1u, tph = (tile >> 1) & 1u;
                 if (!wait_bar(accf0 + 8 * b, tph, abort_flag, a.err)) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t tbase = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + b * TB;
+                const uint32_t tbase = tmem + ((uint32_t)(32 * quarter) << 16) + b * TB;
+                const bool masked = (int64_t)(bt + 1) * TB > lim;
                 for (int c0 = 0; c0 < TB; c0 += 32) {
                     float v[32];
                     tmem_ld32(tbase + c0, v);
                     const int64_t id0 = (int64_t)bt * TB + c0;
+                    if (!masked) {
+                        const float4* x4 = reinterpret_cast<const float4*>(a.xn + id0);
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const int64_t id = id0 + j;
-                        const float dd =
-                            id < id_end ? fmaf(-2.f, v[j], qn + __ldg(a.xn + id)) : INFINITY;
-                        if (dd < thr) {
-                            int p = cnt < KP ? cnt : KP - 1;
-                            while (p > 0 && Ld[(p - 1) * TQ + row] > dd) {
-                                Ld[p * TQ + row] = Ld[(p - 1) * TQ + row];
-                                Li[p * TQ + row] = Li[(p - 1) * TQ + row];
-                                --p;
-                            }
-                            Ld[p * TQ + row] = dd;
-                            Li[p * TQ + row] = (int32_t)id;
-                            if (cnt < KP) ++cnt;
-                            if (cnt == KP) thr = Ld[(KP - 1) * TQ + row];
+                        for (int j4 = 0; j4 < 8; ++j4) {
+                            const float4 x = __ldg(x4 + j4);
+                            v[4 * j4] = fmaf(-2.f, v[4 * j4], qn + x.x);
+                            v[4 * j4 + 1] = fmaf(-2.f, v[4 * j4 + 1], qn + x.y);
+                            v[4 * j4 + 2] = fmaf(-2.f, v[4 * j4 + 2], qn + x.z);
+                            v[4 * j4 + 3] = fmaf(-2.f, v[4 * j4 + 3], qn + x.w);
+                        }
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) {
+                            const int64_t id = id0 + j;
+                            v[j] = id < id_end ? fmaf(-2.f, v[j], qn + __ldg(a.xn + id)) : INFINITY;
                         }
                     }
+                    float mn = v[0];
+#pragma unroll
+                    for (int j = 1; j < 32; ++j) mn = fminf(mn, v[j]);
+                    unsigned rows = __ballot_sync(0xffffffffu, mn < thr);
+                    if (!rows) continue;
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) B[j * 33 + lane] = v[j];
+                    __syncwarp();
+                    while (rows) {
+                        const int r = __ffs(rows) - 1;
+                        rows &= rows - 1;
+                        float t = __shfl_sync(0xffffffffu, thr, r);
+                        const float dj = B[lane * 33 + r];           // column lane of row r
+                        unsigned hit = __ballot_sync(0xffffffffu, dj < t);
+                        float* Lr = Lw + r * KP;
+                        int32_t* Lir = Lwi + r * KP;
+                        float d0 = Lr[lane], d1 = INFINITY;
+                        int32_t i0 = Lir[lane], i1 = -1;
+                        if (KP == 64) {
+                            d1 = Lr[lane + 32];
+                            i1 = Lir[lane + 32];
+                        }
+                        while (hit) {
+                            const int c = __ffs(hit) - 1;
+                            hit &= hit - 1;
+                            const float cd = __shfl_sync(0xffffffffu, dj, c);
+                            if (!(cd < t)) continue;
+                            const int32_t cid = (int32_t)(id0 + c);
+                            // ids grow along the scan, so equal distances already
+                            // in the list come first: position = #entries <= cd
+                            int pos = __popc(__ballot_sync(0xffffffffu, d0 <= cd));
+                            if (KP == 64) pos += __popc(__ballot_sync(0xffffffffu, d1 <= cd));
+                            const float u0 = __shfl_up_sync(0xffffffffu, d0, 1);
+                            const int32_t ui0 = __shfl_up_sync(0xffffffffu, i0, 1);
+                            if (KP == 64) {
+                                float u1 = __shfl_up_sync(0xffffffffu, d1, 1);
+                                int32_t ui1 = __shfl_up_sync(0xffffffffu, i1, 1);
+                                const float t31 = __shfl_sync(0xffffffffu, d0, 31);
+                                const int32_t ti31 = __shfl_sync(0xffffffffu, i0, 31);
+                                if (lane == 0) {
+                                    u1 = t31;
+                                    ui1 = ti31;
+                                }
+                                if (lane + 32 > pos) {
+                                    d1 = u1;
+                                    i1 = ui1;
+                                } else if (lane + 32 == pos) {
+                                    d1 = cd;
+                                    i1 = cid;
+                                }
+                            }
+                            if (lane > pos) {
+                                d0 = u0;
+                                i0 = ui0;
+                            } else if (lane == pos) {
+                                d0 = cd;
+                                i0 = cid;
+                            }
+                            t = __shfl_sync(0xffffffffu, KP == 64 ? d1 : d0, 31);
+                        }
+                        Lr[lane] = d0;
+                        Lir[lane] = i0;
+                        if (KP == 64) {
+                            Lr[lane + 32] = d1;
+                            Lir[lane + 32] = i1;
+                        }
+                        if (lane == r) thr = t;
+                    }
+                    __syncwarp();
                 }
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                 asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(acce0 + 8 * b) : "memory");
             }
-            if (qi < a.nq) {
-                const size_t o = ((size_t)qi * a.nseg + seg) * KP;
-                for (int k = 0; k < KP; ++k) a.cand[o + k] = Li[k * TQ + row];
-                if (a.cand_d)
-                    for (int k = 0; k < KP; ++k) a.cand_d[o + k] = Ld[k * TQ + row];
+            __syncwarp();
+            for (int r = 0; r < 32; ++r) {
+                const int64_t qr = q0 + 32 * quarter + r;
+                if (qr >= a.nq) break;
+                const size_t o = ((size_t)qr * a.nseg + seg) * KP;
+                for (int k = lane; k < KP; k += 32) {
+                    a.cand[o + k] = Lwi[r * KP + k];
+                    if (a.cand_d) a.cand_d[o + k] = Lw[r * KP + k];
+                }
             }
+            __syncwarp();
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -439,7 +529,7 @@ bool make_map(CUtensorMap* map, const void* base, int64_t rows, int m, int ms) {
 
 template <int KP>
 size_t tc_smem() {
-    return 1024 + (size_t)STAGES * STAGE_BYTES + (size_t)KP * TQ * 8 + 8 * 8 + 16;
+    return 1024 + (size_t)STAGES * STAGE_BYTES + (size_t)KP * TQ * 8 + 4 * 32 * 33 * 4 + 8 * 8 + 16;
 }
 
 template <int KP>
