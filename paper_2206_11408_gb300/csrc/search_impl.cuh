@@ -292,14 +292,24 @@ __device__ __forceinline__ float edge_cos(const DevIndex& ix, size_t e, const fl
     if constexpr (!LP) {
         const float4* u = ix.edge_u + e * ix.r4;
         const float4* v = reinterpret_cast<const float4*>(uq);
-#pragma unroll 4
-        for (int k = 0; k < ix.r4; ++k) {
-            const float4 x = __ldg(u + k);
-            const float4 y = v[k];
-            acc = fmaf(x.x, y.x, acc);
-            acc = fmaf(x.y, y.y, acc);
-            acc = fmaf(x.z, y.z, acc);
-            acc = fmaf(x.w, y.w, acc);
+        // r <= 64: two halves of up to eight 16-byte loads, each half issued
+        // before its products (same summation order as a plain loop)
+#pragma unroll
+        for (int h = 0; h < 16; h += 8) {
+            float4 x[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                if (h + k < ix.r4) x[k] = __ldg(u + h + k);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                if (h + k < ix.r4) {
+                    const float4 y = v[h + k];
+                    acc = fmaf(x[k].x, y.x, acc);
+                    acc = fmaf(x[k].y, y.y, acc);
+                    acc = fmaf(x[k].z, y.z, acc);
+                    acc = fmaf(x[k].w, y.w, acc);
+                }
+            }
         }
     } else {
         const uint4* u = ix.edge_q + e * ix.r16;
@@ -761,6 +771,56 @@ __global__ void __launch_bounds__(128, 5) k_search(DevIndex ix, SearchArgs a) {
                     }
                 }
             }
+            // FP32 FINGER: t_hat of every new neighbour by one balanced gather.
+            // The new neighbours are compacted and lpr lanes share an edge row
+            // (lpr = r/4 rounded up to a power of two, at most 16), so one
+            // 16-byte load per lane covers 32 / lpr rows and eight loads per
+            // lane are in flight at once; an lpr-lane butterfly sums each row.
+            constexpr bool BAL = MODE == FINGER_MODE_FINGER;
+            constexpr int GS = 8;
+            float2 scv[NPL];
+            if constexpr (BAL) {
+                if (use_est) {
+                    int nn = 0;
+#pragma unroll
+                    for (int s = 0; s < NPL; ++s) {
+                        const int o = s * 32 + lane;
+                        scv[s] = isnew[s] ? __ldg(ix.edge_s + (size_t)c * ix.deg0 + o)
+                                          : make_float2(0.f, 0.f);
+                        const unsigned bm = __ballot_sync(FULLMASK, isnew[s]);
+                        if (isnew[s]) lst[nn + __popc(bm & ltmask)] = o;
+                        nn += __popc(bm);
+                    }
+                    __syncwarp();
+                    const int llpr = ix.r4 <= 4 ? 2 : ix.r4 <= 8 ? 3 : 4;
+                    const int lpr = 1 << llpr, rps = 32 >> llpr;
+                    const int sub = lane >> llpr, k4 = lane & (lpr - 1);
+                    const float4 y = k4 < ix.r4 ? reinterpret_cast<const float4*>(uq)[k4]
+                                                : make_float4(0.f, 0.f, 0.f, 0.f);
+                    const float4* eb = ix.edge_u + (size_t)c * ix.deg0 * ix.r4;
+                    for (int base = 0; base < nn; base += GS * rps) {
+                        float4 x[GS];
+#pragma unroll
+                        for (int g = 0; g < GS; ++g) {
+                            const int i = base + g * rps + sub;
+                            x[g] = (i < nn && k4 < ix.r4)
+                                       ? __ldg(eb + (size_t)lst[CK(i, 32 * NPL, 1021)] * ix.r4 + k4)
+                                       : make_float4(0.f, 0.f, 0.f, 0.f);
+                        }
+#pragma unroll
+                        for (int g = 0; g < GS; ++g) {
+                            float p = x[g].x * y.x;
+                            p = fmaf(x[g].y, y.y, p);
+                            p = fmaf(x[g].z, y.z, p);
+                            p = fmaf(x[g].w, y.w, p);
+                            for (int o = lpr >> 1; o > 0; o >>= 1) p += __shfl_xor_sync(FULLMASK, p, o);
+                            const int i = base + g * rps + sub;
+                            if (k4 == 0 && i < nn) xb[lst[CK(i, 32 * NPL, 1022)]] = p;
+                        }
+                    }
+                    __syncwarp();
+                }
+            }
             int nl = 0;
             bool needr[NPL];
 #pragma unroll
@@ -768,9 +828,11 @@ __global__ void __launch_bounds__(128, 5) k_search(DevIndex ix, SearchArgs a) {
                 float est = -INFINITY;
                 if (use_est && isnew[s]) {
                     const size_t e = (size_t)c * ix.deg0 + s * 32 + lane;
-                    const float2 sc = __ldg(ix.edge_s + e);
+                    const float2 sc = BAL ? scv[s] : __ldg(ix.edge_s + e);
                     float t;
-                    if constexpr (MLP) {
+                    if constexpr (BAL) {
+                        t = fmaf(xb[s * 32 + lane], ix.alpha, ix.beta);
+                    } else if constexpr (MLP) {
                         // learned predictor in place of distribution matching;
                         // the matched cosine is the fallback for a non-finite output
                         const float y = ak[crow[s]];
