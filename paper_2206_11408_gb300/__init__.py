@@ -95,6 +95,7 @@ SIGNATURES = {
     "finger_autotune": (_I, [_P, _P, _I64, _I, _I, _P, _P, _P, _P]),
     "finger_set_counters": (_I, [_P, _P]),
     "finger_set_limit": (_I, [_P, _I]),
+    "finger_set_visited_slots": (_I, [_P, _I]),
     "finger_knn": (_I, [_P, _P, _I64, _I, _P, _P, _P]),
     "finger_sync": (_I, [_P]),
     "finger_get_stats": (_I, [_P, _P]),
@@ -296,6 +297,10 @@ class Index:
     def set_limit(self, max_expansions: int):
         """Cap on expansions per query (0 = default n + 16)."""
         _check(self._lib.finger_set_limit(self._h, max_expansions), "finger_set_limit")
+
+    def set_visited_slots(self, bits: int):
+        """Visited-set slot width: 0 = 16-bit where the ids fit (default), 32 = always 32-bit."""
+        _check(self._lib.finger_set_visited_slots(self._h, bits), "finger_set_visited_slots")
 
     def set_counters(self, counters):
         """Per-query counters (int32 CUDA tensor nq x 8) for later searches; None disables."""

@@ -36,12 +36,12 @@ void choose_groups(int nchunks, int* G, int* VPL) {
     }
 }
 
-int search_smem_per_warp(const DevIndex& ix, int mode, int ef_cap, int H, int NPL) {
+int search_smem_per_warp(const DevIndex& ix, int mode, int ef_cap, int H, int NPL, int h16) {
     const int r_pad = ix.r4 * 4;
     const int qs_len = mode == FINGER_MODE_FINGER_LP ? ix.m8 * 8 : ix.m4 * 4;
     const int qs_bytes = mode == FINGER_MODE_FINGER_LP ? 4 * ((qs_len + 3) & ~3) : 0;
     const int tile = mode == FINGER_MODE_FINGER_MLP ? 2 * 16 * (ix.mlp_kp + MLP_PAD) : 0;
-    int b = 8 * ef_cap + 4 * H + 8 * r_pad + qs_bytes + 32 * 32 * NPL + 32 + tile;
+    int b = 8 * ef_cap + (h16 ? 2 : 4) * H + 8 * r_pad + qs_bytes + 32 * 32 * NPL + 32 + tile;
     return (b + 15) & ~15;
 }
 
@@ -166,12 +166,31 @@ finger_status make_plan(finger_index* ix, int mode, int ef_max, int64_t nq, Sear
     if (mode == FINGER_MODE_FINGER_LP) H = std::max(H, pow2ceil(2 * p->ef_cap));
     else H = std::max(H, pow2ceil(ix->m_pad));   // the query is staged in the hash region
     p->H = H;
+    // 16-bit visited slots: ids must fit the bucket index plus 12 bits (n <= 512 H),
+    // and the query staged in the hash region must fit its H / 2 words
+    p->h16 = ix->visited_bits != 32 && mode != FINGER_MODE_FINGER_LP &&
+             ix->n <= 512 * (int64_t)H && H >= 2 * ix->m_pad;
     p->wpb = wpb;
-    p->smem_per_warp = search_smem_per_warp(d, mode, p->ef_cap, p->H, p->NPL);
+    p->smem_per_warp = search_smem_per_warp(d, mode, p->ef_cap, p->H, p->NPL, p->h16);
     p->blk_smem = 0;
     if (p->blk_smem + (int64_t)p->smem_per_warp * wpb > 227 * 1024) return FINGER_ERR_UNSUPPORTED;
+    // the kernel variant with the most resident blocks that shared memory admits:
+    // 8 blocks (64 registers, plain mode), 6 (80 registers, plain and FP32
+    // FINGER), else 5 (96 registers)
     int bps = 0;
-    if (search_occupancy(d, *p, &bps) != cudaSuccess || bps < 1) {
+    p->occ = 5;
+    for (int occ : {8, 6}) {
+        SearchPlan t = *p;
+        t.occ = occ;
+        int b = 0;
+        if (search_occupancy(d, t, &b) == cudaSuccess && b >= occ) {
+            p->occ = occ;
+            bps = b;
+            break;
+        }
+        cudaGetLastError();
+    }
+    if (p->occ == 5 && (search_occupancy(d, *p, &bps) != cudaSuccess || bps < 1)) {
         cudaGetLastError();
         return FINGER_ERR_UNSUPPORTED;
     }
@@ -218,6 +237,7 @@ SearchArgs base_args(finger_index* ix, const SearchPlan& p) {
     a.warmup = ix->warmup;
     a.ef_cap = p.ef_cap;
     a.H = p.H;
+    a.h16 = p.h16;
     a.rerank = 0;
     a.max_expansions = ix->max_expansions > 0 ? ix->max_expansions
                                               : (int)std::min<int64_t>(ix->n + 16, 1 << 30);
@@ -552,6 +572,13 @@ finger_status finger_set_mode(finger_index* ix, int mode, int warmup) {
 finger_status finger_set_limit(finger_index* ix, int max_expansions) {
     if (!ix || max_expansions < 0) return FINGER_ERR_INVALID_ARG;
     ix->max_expansions = max_expansions;
+    return FINGER_OK;
+}
+
+finger_status finger_set_visited_slots(finger_index* ix, int bits) {
+    if (!ix || (bits != 0 && bits != 32)) return FINGER_ERR_INVALID_ARG;
+    if (ix->visited_bits != bits) fg_drop_captures(ix);   // captured launches hold the plan
+    ix->visited_bits = bits;
     return FINGER_OK;
 }
 

@@ -71,6 +71,7 @@ struct SearchArgs {
     float* out_d;
     int warmup;
     int ef_cap, H, rerank;
+    int h16;                // 1: visited hash in 16-bit slots (n <= 512 H)
     int max_expansions;
     uint32_t* work;         // [0] = next query
     int* err;
@@ -98,6 +99,8 @@ struct SearchPlan {
     int wpb;            // warps per block
     int blocks;
     int ef_cap, H;
+    int h16;            // visited hash in 16-bit slots
+    int occ;            // resident blocks per SM the kernel variant is compiled for
     int smem_per_warp;
     int blk_smem;       // per-block shared memory before the warp regions
 };
@@ -105,7 +108,7 @@ struct SearchPlan {
 // kernels / launchers (search.cu)
 cudaError_t launch_search(const DevIndex& ix, const SearchArgs& a, const SearchPlan& p,
                           cudaStream_t s);
-int search_smem_per_warp(const DevIndex& ix, int mode, int ef_cap, int H, int NPL);
+int search_smem_per_warp(const DevIndex& ix, int mode, int ef_cap, int H, int NPL, int h16);
 cudaError_t search_occupancy(const DevIndex& ix, const SearchPlan& p, int* blocks_per_sm);
 void choose_groups(int nchunks, int* G, int* VPL);
 
@@ -183,6 +186,7 @@ struct finger_index {
     int mode = FINGER_MODE_PLAIN;
     int warmup = 5;
     int max_expansions = 0;       // 0 = n + 16
+    int visited_bits = 0;         // visited-hash slots: 0 = 16-bit where they fit, 32 = always 32-bit
     int32_t* cnt_q = nullptr;
     // scratch
     uint32_t* work = nullptr;     // 4 words

@@ -285,6 +285,54 @@ __device__ __forceinline__ int visit(uint32_t* hash, int H, int logNB, uint32_t 
     return V_SEEN;  // unreachable: the table never fills (3/4 plus one batch < 1)
 }
 
+// The same visited set in 16-bit slots, for ids below 2^B with B = logNB + 12
+// (logNB = log2 of the bucket count; buckets of eight slots, one 16-byte load
+// per probe).  h = id * 0x9E3779B1 mod 2^B is a bijection, so the bucket
+// h >> 12 and the 12 low bits identify the id; a slot holds those 12 bits and
+// the probe distance (0..7) in bits 12..14, hence never the empty value
+// 0xFFFF.  An id whose eight buckets are full goes to the bitmap (V_PENDING)
+// on every visit, since slots are never freed.  A lost compare-and-swap means
+// another lane took a slot of the bucket, so after eight the bucket is full.
+__device__ __forceinline__ int visit16(uint16_t* hash, int logNB, uint32_t id, bool spill_mode,
+                                       uint32_t* bitmap, uint32_t& oldw) {
+    const uint32_t h = (id * 0x9E3779B1u) & ((1u << (logNB + 12)) - 1u);
+    const uint32_t nbm = (1u << logNB) - 1u;
+    const uint32_t home = h >> 12, rem = h & 0xFFFu;
+    int retries = 0;
+    for (int dist = 0; dist < 8; ++dist) {
+        const uint32_t b = (home + (uint32_t)dist) & nbm;
+        const uint32_t want = rem | ((uint32_t)dist << 12);
+        uint4 v;
+        asm volatile("ld.volatile.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                     : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                     : "r"((uint32_t)__cvta_generic_to_shared(hash + 8 * CK(b, nbm + 1, 1023))));
+        const uint32_t w2 = want * 0x10001u;
+        if (__vcmpeq2(v.x, w2) | __vcmpeq2(v.y, w2) | __vcmpeq2(v.z, w2) | __vcmpeq2(v.w, w2))
+            return V_SEEN;
+        const uint32_t em = (__vcmpeq2(v.x, 0xFFFFFFFFu) & 0x00010001u) |
+                            ((__vcmpeq2(v.y, 0xFFFFFFFFu) & 0x00010001u) << 1) |
+                            ((__vcmpeq2(v.z, 0xFFFFFFFFu) & 0x00010001u) << 2) |
+                            ((__vcmpeq2(v.w, 0xFFFFFFFFu) & 0x00010001u) << 3);
+        if (!em) continue;   // bucket full: the id, if present, is further on
+        // the id is in no bucket of its probe sequence
+        if (spill_mode) {
+            oldw = atomicOr(&bitmap[id >> 5], 1u << (id & 31));
+            return V_PENDING;
+        }
+        // first empty slot: word k = bit k of the low half, low/high half
+        const int lo = __ffs(em & 0xFu), hi = __ffs(em >> 16);
+        const int e = lo && (!hi || lo <= hi) ? 2 * (lo - 1) : 2 * (hi - 1) + 1;
+        const unsigned short old =
+            atomicCAS(reinterpret_cast<unsigned short*>(hash + 8 * b + e), (unsigned short)0xFFFFu,
+                      (unsigned short)want);
+        if (old == 0xFFFFu) return V_NEW;
+        if (old == want) return V_SEEN;
+        if (++retries <= 8) --dist;   // re-read this bucket (bounded)
+    }
+    oldw = atomicOr(&bitmap[id >> 5], 1u << (id & 31));
+    return V_PENDING;
+}
+
 // t_hat for one edge: r-dot of the stored unit residual projection with uq
 template <bool LP>
 __device__ __forceinline__ float edge_cos(const DevIndex& ix, size_t e, const float* uq) {
@@ -482,8 +530,8 @@ __device__ __forceinline__ void mlp_tile(const __nv_bfloat16* xt, int kp, const 
     }
 }
 
-template <int MODE, int G, int VPL, int NPL>
-__global__ void __launch_bounds__(128, 5) k_search(DevIndex ix, SearchArgs a) {
+template <int MODE, int G, int VPL, int NPL, int OCC>
+__global__ void __launch_bounds__(128, OCC) k_search(DevIndex ix, SearchArgs a) {
     constexpr bool LP = MODE == FINGER_MODE_FINGER_LP;
     constexpr bool EST = MODE != FINGER_MODE_PLAIN;
     constexpr bool MLP = MODE == FINGER_MODE_FINGER_MLP;
@@ -501,11 +549,12 @@ __global__ void __launch_bounds__(128, 5) k_search(DevIndex ix, SearchArgs a) {
     float* Tk = reinterpret_cast<float*>(wb);
     uint32_t* Ti = reinterpret_cast<uint32_t*>(Tk + a.ef_cap);
     uint32_t* hash = Ti + a.ef_cap;
-    float* uq = reinterpret_cast<float*>(hash + a.H);
+    const int hwords = a.h16 ? a.H >> 1 : a.H;   // 32-bit words of the visited hash
+    float* uq = reinterpret_cast<float*>(hash + hwords);
     float* pq = uq + r_pad;
     // the query staging buffer is only read before the visited hash is cleared,
     // so outside the LP mode (which re-reads it for the FP32 re-rank) it lives
-    // inside the hash region (the plan keeps H >= m_pad)
+    // inside the hash region (the plan keeps its words >= m_pad)
     float* qs = LP ? pq + r_pad : reinterpret_cast<float*>(hash);
     uint32_t* nbs = reinterpret_cast<uint32_t*>(LP ? qs + ((qs_len + 3) & ~3) : pq + r_pad);
     float* es = reinterpret_cast<float*>(nbs + 32 * NPL);
@@ -521,7 +570,7 @@ __global__ void __launch_bounds__(128, 5) k_search(DevIndex ix, SearchArgs a) {
     const int64_t slot = (int64_t)blockIdx.x * wpb + wib;
     uint32_t* bitmap = a.bitmap + slot * a.words;
     uint32_t* spl = a.spill + slot * a.spill_cap;
-    const int logNB = 31 - __clz(a.H >> 2);   // buckets of the visited hash
+    const int logNB = 31 - __clz(a.H >> (a.h16 ? 3 : 2));   // buckets of the visited hash
 
     for (;;) {
         int qi = 0;
@@ -614,12 +663,17 @@ __global__ void __launch_bounds__(128, 5) k_search(DevIndex ix, SearchArgs a) {
         }
 
         // ---- a3..a6: layer 0
-        for (int i = lane; i < a.H; i += 32) hash[i] = PAD;
+        for (int i = lane; i < hwords; i += 32) hash[i] = PAD;
         __syncwarp();
         if (lane == 0) {
             Tk[0] = dcur;
             Ti[0] = cur;
-            hash[4 * hbucket(cur, logNB)] = cur;   // the table is empty
+            if (a.h16) {   // the table is empty: distance 0, first slot
+                const uint32_t h = (cur * 0x9E3779B1u) & ((1u << (logNB + 12)) - 1u);
+                reinterpret_cast<uint16_t*>(hash)[8 * (h >> 12)] = (uint16_t)(h & 0xFFFu);
+            } else {
+                hash[4 * hbucket(cur, logNB)] = cur;
+            }
         }
         __syncwarp();
         int sz = 1, cursor = 0, hcount = 1, nspill = 0;
@@ -663,8 +717,10 @@ __global__ void __launch_bounds__(128, 5) k_search(DevIndex ix, SearchArgs a) {
                 int res = V_SEEN;
                 uint32_t oldw = 0u;
                 if (nb[s] != PAD)
-                    res = visit(hash, a.H, logNB, (uint32_t)CK(nb[s], ix.n, 1004), spill_mode, bitmap,
-                                oldw);
+                    res = a.h16 ? visit16(reinterpret_cast<uint16_t*>(hash), logNB,
+                                          (uint32_t)CK(nb[s], ix.n, 1004), spill_mode, bitmap, oldw)
+                                : visit(hash, a.H, logNB, (uint32_t)CK(nb[s], ix.n, 1004), spill_mode,
+                                        bitmap, oldw);
                 if (!DEFER && res == V_PENDING)
                     res = (oldw & (1u << (nb[s] & 31))) ? V_SEEN : V_NEW_SPILL;
                 pend[s] = res == V_PENDING;
@@ -1126,15 +1182,19 @@ __global__ void __launch_bounds__(128, 5) k_search(DevIndex ix, SearchArgs a) {
     }
 }
 
-// instantiate and dispatch one mode over the (G, VPL, NPL) variants
-template <int MODE>
-cudaError_t launch_mode(const DevIndex& ix, const SearchArgs& a, const SearchPlan& p,
-                        cudaStream_t s) {
+// instantiate and dispatch one mode over the (G, VPL, NPL) variants and the
+// resident-block target: 5 blocks of 4 warps (96 registers) everywhere, 6 (80
+// registers) for the plain and FP32 FINGER modes, 8 (64 registers) for the
+// plain mode.  FINGER keeps its gathers in flight in registers, so it is
+// fastest at 6; plain search at 8.
+template <int MODE, int OCC>
+cudaError_t launch_occ(const DevIndex& ix, const SearchArgs& a, const SearchPlan& p,
+                       cudaStream_t s) {
     const int smem = p.blk_smem + p.smem_per_warp * p.wpb;
     const dim3 grid(p.blocks), block(p.wpb * 32);
 #define FG_CASE(G_, V_, N_)                                                                    \
     if (p.G == G_ && p.VPL == V_ && p.NPL == N_) {                                           \
-        auto k = k_search<MODE, G_, V_, N_>;                                                   \
+        auto k = k_search<MODE, G_, V_, N_, OCC>;                                              \
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem); \
         if (e != cudaSuccess) return e;                                                       \
         k<<<grid, block, smem, s>>>(ix, a);                                                   \
@@ -1150,12 +1210,12 @@ cudaError_t launch_mode(const DevIndex& ix, const SearchArgs& a, const SearchPla
     return cudaErrorInvalidValue;
 }
 
-template <int MODE>
-cudaError_t occupancy_mode(const SearchPlan& p, int* blocks) {
+template <int MODE, int OCC>
+cudaError_t occupancy_occ(const SearchPlan& p, int* blocks) {
     const int smem = p.blk_smem + p.smem_per_warp * p.wpb;
 #define FG_CASE(G_, V_, N_)                                                                    \
     if (p.G == G_ && p.VPL == V_ && p.NPL == N_) {                                           \
-        auto k = k_search<MODE, G_, V_, N_>;                                                   \
+        auto k = k_search<MODE, G_, V_, N_, OCC>;                                              \
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem); \
         if (e != cudaSuccess) return e;                                                       \
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k, p.wpb * 32, smem);     \
@@ -1168,6 +1228,32 @@ cudaError_t occupancy_mode(const SearchPlan& p, int* blocks) {
 #undef FG_NPL
 #undef FG_CASE
     return cudaErrorInvalidValue;
+}
+
+template <int MODE>
+cudaError_t launch_mode(const DevIndex& ix, const SearchArgs& a, const SearchPlan& p,
+                        cudaStream_t s) {
+    if constexpr (MODE == FINGER_MODE_PLAIN)
+        if (p.occ == 8) return launch_occ<MODE, 8>(ix, a, p, s);
+    if constexpr (MODE == FINGER_MODE_PLAIN || MODE == FINGER_MODE_FINGER)
+        if (p.occ == 6) return launch_occ<MODE, 6>(ix, a, p, s);
+    if (p.occ != 5) return cudaErrorInvalidValue;
+    return launch_occ<MODE, 5>(ix, a, p, s);
+}
+
+// resident blocks per SM of the variant the plan names; 0 for a variant the
+// mode does not have
+template <int MODE>
+cudaError_t occupancy_mode(const SearchPlan& p, int* blocks) {
+    if constexpr (MODE == FINGER_MODE_PLAIN)
+        if (p.occ == 8) return occupancy_occ<MODE, 8>(p, blocks);
+    if constexpr (MODE == FINGER_MODE_PLAIN || MODE == FINGER_MODE_FINGER)
+        if (p.occ == 6) return occupancy_occ<MODE, 6>(p, blocks);
+    if (p.occ != 5) {
+        *blocks = 0;
+        return cudaSuccess;
+    }
+    return occupancy_occ<MODE, 5>(p, blocks);
 }
 
 }  // namespace fg

@@ -298,16 +298,43 @@ def test_bruteforce_paths_match_oracle(m, K):
     ix.close()
 
 
-def test_maximum_ef_and_k(cfg1):
+@pytest.mark.parametrize("bits", [0, 32])
+def test_maximum_ef_and_k(cfg1, bits):
     """ef at the compiled maximum (1024) and K = 256 on the 10,000-point index:
-    the result list holds 1024 entries, most visits go through the spill path,
-    and the traversal still equals the oracle's."""
+    the result list holds 1024 entries, most visits go through the spill path
+    (and, with 16-bit slots, through full probe sequences), and the traversal
+    still equals the oracle's with either visited-set slot width."""
     q = cfg1["q"][:40]
     Q = cfg1["Q"][:40]
     gt, _ = oracle.bruteforce(cfg1["X"], Q, 256)
-    for mode, f in ((fg.MODE_PLAIN, None), (fg.MODE_FINGER, cfg1["fp"])):
-        gi, gd, gc = _gpu_search(cfg1["ix"], q, 256, 1024, mode)
-        oi, od, oc = oracle.search(cfg1["g"], cfg1["X"], Q, 256, 1024, f)
-        _compare(gi, gd, gc, oi, od, oc, gt, 256, f"ef=1024 K=256 mode={mode}")
+    cfg1["ix"].set_visited_slots(bits)
+    try:
+        for mode, f in ((fg.MODE_PLAIN, None), (fg.MODE_FINGER, cfg1["fp"])):
+            gi, gd, gc = _gpu_search(cfg1["ix"], q, 256, 1024, mode)
+            oi, od, oc = oracle.search(cfg1["g"], cfg1["X"], Q, 256, 1024, f)
+            _compare(gi, gd, gc, oi, od, oc, gt, 256, f"ef=1024 K=256 mode={mode} bits={bits}")
+    finally:
+        cfg1["ix"].set_visited_slots(0)
     with pytest.raises(fg.FingerError):
         cfg1["ix"].search(q, 10, 1025)                  # above the compiled maximum
+
+
+@pytest.mark.parametrize("ef", [20, 100])
+def test_visited_slot_widths_give_the_same_traversal(cfg1, ef):
+    """The visited set is exact with 16-bit and with 32-bit slots, so plain and
+    FINGER search return identical lists, distances and counters; the 32-bit
+    tables also meet the oracle bars."""
+    ix = cfg1["ix"]
+    for mode, f in ((fg.MODE_PLAIN, None), (fg.MODE_FINGER, cfg1["fp"])):
+        a = _gpu_search(ix, cfg1["q"], 10, ef, mode)
+        ix.set_visited_slots(32)
+        try:
+            b = _gpu_search(ix, cfg1["q"], 10, ef, mode)
+        finally:
+            ix.set_visited_slots(0)
+        for x, y in zip(a, b):
+            assert (x == y).all()
+        oi, od, oc = oracle.search(cfg1["g"], cfg1["X"], cfg1["Q"], 10, ef, f)
+        _compare(*b, oi, od, oc, cfg1["gt"], 10, f"32-bit slots mode={mode} ef={ef}")
+    with pytest.raises(fg.FingerError):
+        ix.set_visited_slots(16)
