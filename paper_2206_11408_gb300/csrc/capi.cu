@@ -29,6 +29,10 @@ void choose_groups(int nchunks, int* G, int* VPL) {
     } else if (nchunks <= 16) {
         *G = 16;
         *VPL = 1;
+    } else if (nchunks <= 32) {
+        // two chunks per lane, two rows per warp pass: eight rows in flight
+        *G = 16;
+        *VPL = 2;
     } else {
         *G = 32;
         const int v = (nchunks + 31) / 32;

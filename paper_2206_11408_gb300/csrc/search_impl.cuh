@@ -1201,7 +1201,7 @@ cudaError_t launch_occ(const DevIndex& ix, const SearchArgs& a, const SearchPlan
         return cudaGetLastError();                                                            \
     }
 #define FG_NPL(N_)                                                                             \
-    FG_CASE(8, 1, N_) FG_CASE(16, 1, N_) FG_CASE(32, 1, N_) FG_CASE(32, 2, N_)               \
+    FG_CASE(8, 1, N_) FG_CASE(16, 1, N_) FG_CASE(16, 2, N_) FG_CASE(32, 1, N_) FG_CASE(32, 2, N_)               \
     FG_CASE(32, 4, N_) FG_CASE(32, 8, N_)
     FG_NPL(1)
     FG_NPL(2)
@@ -1221,7 +1221,7 @@ cudaError_t occupancy_occ(const SearchPlan& p, int* blocks) {
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k, p.wpb * 32, smem);     \
     }
 #define FG_NPL(N_)                                                                             \
-    FG_CASE(8, 1, N_) FG_CASE(16, 1, N_) FG_CASE(32, 1, N_) FG_CASE(32, 2, N_)               \
+    FG_CASE(8, 1, N_) FG_CASE(16, 1, N_) FG_CASE(16, 2, N_) FG_CASE(32, 1, N_) FG_CASE(32, 2, N_)               \
     FG_CASE(32, 4, N_) FG_CASE(32, 8, N_)
     FG_NPL(1)
     FG_NPL(2)
