@@ -139,7 +139,7 @@ __device__ __forceinline__ void exact_list(const QRegs<LP, VPL>& q, const DevInd
                                            const uint32_t* nbs, const int* lst, int nlist,
                                            float* xb, int lane) {
     constexpr int RPW = 32 / G;
-    constexpr int U = VPL >= 4 ? 2 : 4;   // rows per group in flight
+    constexpr int U = VPL >= 8 ? 1 : VPL >= 4 ? 2 : 4;   // rows per group in flight
     const int grp = lane / G, kin = lane % G;
     for (int base = 0; base < nlist; base += U * RPW) {
         int o[U];
