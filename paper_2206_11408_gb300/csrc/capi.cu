@@ -170,17 +170,19 @@ finger_status make_plan(finger_index* ix, int mode, int ef_max, int64_t nq, Sear
     if (mode == FINGER_MODE_FINGER_LP) H = std::max(H, pow2ceil(2 * p->ef_cap));
     else H = std::max(H, pow2ceil(ix->m_pad));   // the query is staged in the hash region
     p->H = H;
-    // 16-bit visited slots: ids must fit the bucket index plus 12 bits (n <= 512 H),
-    // and the query staged in the hash region must fit its H / 2 words
-    p->h16 = ix->visited_bits != 32 && mode != FINGER_MODE_FINGER_LP &&
-             ix->n <= 512 * (int64_t)H && H >= 2 * ix->m_pad;
+    // 16-bit visited slots: ids must fit the bucket index plus 13 bits
+    // (n <= 1024 H), and what reuses the table's H / 2 words must fit there:
+    // the staged query (m_pad words) outside LP mode, the re-rank buffer
+    // (2 ef_cap words) in LP mode
+    p->h16 = ix->visited_bits != 32 && ix->n <= 1024 * (int64_t)H &&
+             (mode == FINGER_MODE_FINGER_LP ? H >= 4 * p->ef_cap : H >= 2 * ix->m_pad);
     p->wpb = wpb;
     p->smem_per_warp = search_smem_per_warp(d, mode, p->ef_cap, p->H, p->NPL, p->h16);
     p->blk_smem = 0;
     if (p->blk_smem + (int64_t)p->smem_per_warp * wpb > 227 * 1024) return FINGER_ERR_UNSUPPORTED;
     // the kernel variant with the most resident blocks that shared memory admits:
-    // 8 blocks (64 registers, plain mode), 6 (80 registers, plain and FP32
-    // FINGER), else 5 (96 registers)
+    // 8 blocks (64 registers, plain mode), 6 (80 registers, plain, FP32 FINGER
+    // and LP), else 5 (96 registers)
     int bps = 0;
     p->occ = 5;
     for (int occ : {8, 6}) {

@@ -285,23 +285,23 @@ __device__ __forceinline__ int visit(uint32_t* hash, int H, int logNB, uint32_t 
     return V_SEEN;  // unreachable: the table never fills (3/4 plus one batch < 1)
 }
 
-// The same visited set in 16-bit slots, for ids below 2^B with B = logNB + 12
+// The same visited set in 16-bit slots, for ids below 2^B with B = logNB + 13
 // (logNB = log2 of the bucket count; buckets of eight slots, one 16-byte load
 // per probe).  h = id * 0x9E3779B1 mod 2^B is a bijection, so the bucket
-// h >> 12 and the 12 low bits identify the id; a slot holds those 12 bits and
-// the probe distance (0..7) in bits 12..14, hence never the empty value
-// 0xFFFF.  An id whose eight buckets are full goes to the bitmap (V_PENDING)
+// h >> 13 and the 13 low bits identify the id; a slot holds those 13 bits and
+// the probe distance (0..3) in bits 13..14, hence never the empty value
+// 0xFFFF.  An id whose four buckets are full goes to the bitmap (V_PENDING)
 // on every visit, since slots are never freed.  A lost compare-and-swap means
 // another lane took a slot of the bucket, so after eight the bucket is full.
 __device__ __forceinline__ int visit16(uint16_t* hash, int logNB, uint32_t id, bool spill_mode,
                                        uint32_t* bitmap, uint32_t& oldw) {
-    const uint32_t h = (id * 0x9E3779B1u) & ((1u << (logNB + 12)) - 1u);
+    const uint32_t h = (id * 0x9E3779B1u) & ((1u << (logNB + 13)) - 1u);
     const uint32_t nbm = (1u << logNB) - 1u;
-    const uint32_t home = h >> 12, rem = h & 0xFFFu;
+    const uint32_t home = h >> 13, rem = h & 0x1FFFu;
     int retries = 0;
-    for (int dist = 0; dist < 8; ++dist) {
+    for (int dist = 0; dist < 4; ++dist) {
         const uint32_t b = (home + (uint32_t)dist) & nbm;
-        const uint32_t want = rem | ((uint32_t)dist << 12);
+        const uint32_t want = rem | ((uint32_t)dist << 13);
         uint4 v;
         asm volatile("ld.volatile.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
                      : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
@@ -669,8 +669,8 @@ __global__ void __launch_bounds__(128, OCC) k_search(DevIndex ix, SearchArgs a) 
             Tk[0] = dcur;
             Ti[0] = cur;
             if (a.h16) {   // the table is empty: distance 0, first slot
-                const uint32_t h = (cur * 0x9E3779B1u) & ((1u << (logNB + 12)) - 1u);
-                reinterpret_cast<uint16_t*>(hash)[8 * (h >> 12)] = (uint16_t)(h & 0xFFFu);
+                const uint32_t h = (cur * 0x9E3779B1u) & ((1u << (logNB + 13)) - 1u);
+                reinterpret_cast<uint16_t*>(hash)[8 * (h >> 13)] = (uint16_t)(h & 0x1FFFu);
             } else {
                 hash[4 * hbucket(cur, logNB)] = cur;
             }
@@ -1127,7 +1127,7 @@ __global__ void __launch_bounds__(128, OCC) k_search(DevIndex ix, SearchArgs a) 
         if constexpr (LP) {
             const int R = min(sz, max(K, a.rerank));
             float* rk = reinterpret_cast<float*>(hash);
-            uint32_t* ri = hash + a.ef_cap;   // the plan keeps H >= 2 ef_cap
+            uint32_t* ri = hash + a.ef_cap;   // the plan keeps 2 ef_cap words in the table
             for (int i = 0; i < R; ++i) {
                 const float d = exact_f32_row(qs, ix, Ti[i] & ~EXP, lane);
                 if (lane == 0) Tk[i] = d;
@@ -1184,7 +1184,7 @@ __global__ void __launch_bounds__(128, OCC) k_search(DevIndex ix, SearchArgs a) 
 
 // instantiate and dispatch one mode over the (G, VPL, NPL) variants and the
 // resident-block target: 5 blocks of 4 warps (96 registers) everywhere, 6 (80
-// registers) for the plain and FP32 FINGER modes, 8 (64 registers) for the
+// registers) for the plain, FP32 FINGER and LP modes, 8 (64 registers) for the
 // plain mode.  FINGER keeps its gathers in flight in registers, so it is
 // fastest at 6; plain search at 8.
 template <int MODE, int OCC>
@@ -1235,7 +1235,8 @@ cudaError_t launch_mode(const DevIndex& ix, const SearchArgs& a, const SearchPla
                         cudaStream_t s) {
     if constexpr (MODE == FINGER_MODE_PLAIN)
         if (p.occ == 8) return launch_occ<MODE, 8>(ix, a, p, s);
-    if constexpr (MODE == FINGER_MODE_PLAIN || MODE == FINGER_MODE_FINGER)
+    if constexpr (MODE == FINGER_MODE_PLAIN || MODE == FINGER_MODE_FINGER ||
+                  MODE == FINGER_MODE_FINGER_LP)
         if (p.occ == 6) return launch_occ<MODE, 6>(ix, a, p, s);
     if (p.occ != 5) return cudaErrorInvalidValue;
     return launch_occ<MODE, 5>(ix, a, p, s);
@@ -1247,7 +1248,8 @@ template <int MODE>
 cudaError_t occupancy_mode(const SearchPlan& p, int* blocks) {
     if constexpr (MODE == FINGER_MODE_PLAIN)
         if (p.occ == 8) return occupancy_occ<MODE, 8>(p, blocks);
-    if constexpr (MODE == FINGER_MODE_PLAIN || MODE == FINGER_MODE_FINGER)
+    if constexpr (MODE == FINGER_MODE_PLAIN || MODE == FINGER_MODE_FINGER ||
+                  MODE == FINGER_MODE_FINGER_LP)
         if (p.occ == 6) return occupancy_occ<MODE, 6>(p, blocks);
     if (p.occ != 5) {
         *blocks = 0;

@@ -64,6 +64,14 @@ def test_lp_mode_distances_and_recall(glove_like):
         oi, _, _ = oracle.search(g, X, Q, 10, ef, fp)
         r_lp, r_o = oracle.recall(ids, gt, 10), oracle.recall(oi, gt, 10)
         assert r_lp >= r_o - 0.01, (ef, r_lp, r_o)
+        # the visited set is exact with either slot width: identical results
+        ix.set_visited_slots(32)
+        try:
+            i32, d32 = ix.search(q, 10, ef)
+            ix.sync()
+        finally:
+            ix.set_visited_slots(0)
+        assert (i32.cpu().numpy() == ids).all() and (d32.cpu().numpy() == d).all()
     ix.close()
 
 
