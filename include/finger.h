@@ -252,7 +252,7 @@ finger_status finger_set_limit(finger_index* ix, int max_expansions);
 
 /* Slot width of the per-query visited set (an exact hash in shared memory
  * that spills to a per-query bitmap in global memory).  0 (default): 16-bit
- * slots whenever the ids fit (n <= 1024 x the table's slot count) and the
+ * slots whenever the ids fit (n <= 4096 x the table's slot count) and the
  * buffers that reuse the table fit its half size, which halves the table and
  * lets more queries reside per SM; 32: always 32-bit slots.  Results are
  * identical either way.

@@ -170,11 +170,11 @@ finger_status make_plan(finger_index* ix, int mode, int ef_max, int64_t nq, Sear
     if (mode == FINGER_MODE_FINGER_LP) H = std::max(H, pow2ceil(2 * p->ef_cap));
     else H = std::max(H, pow2ceil(ix->m_pad));   // the query is staged in the hash region
     p->H = H;
-    // 16-bit visited slots: ids must fit the bucket index plus 13 bits
-    // (n <= 1024 H), and what reuses the table's H / 2 words must fit there:
+    // 16-bit visited slots: ids must fit the bucket index plus 15 bits
+    // (n <= 4096 H), and what reuses the table's H / 2 words must fit there:
     // the staged query (m_pad words) outside LP mode, the re-rank buffer
     // (2 ef_cap words) in LP mode
-    p->h16 = ix->visited_bits != 32 && ix->n <= 1024 * (int64_t)H &&
+    p->h16 = ix->visited_bits != 32 && ix->n <= 4096 * (int64_t)H &&
              (mode == FINGER_MODE_FINGER_LP ? H >= 4 * p->ef_cap : H >= 2 * ix->m_pad);
     p->wpb = wpb;
     p->smem_per_warp = search_smem_per_warp(d, mode, p->ef_cap, p->H, p->NPL, p->h16);

@@ -71,7 +71,7 @@ struct SearchArgs {
     float* out_d;
     int warmup;
     int ef_cap, H, rerank;
-    int h16;                // 1: visited hash in 16-bit slots (n <= 1024 H)
+    int h16;                // 1: visited hash in 16-bit slots (n <= 4096 H)
     int max_expansions;
     uint32_t* work;         // [0] = next query
     int* err;

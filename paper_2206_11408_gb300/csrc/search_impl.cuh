@@ -285,49 +285,40 @@ __device__ __forceinline__ int visit(uint32_t* hash, int H, int logNB, uint32_t 
     return V_SEEN;  // unreachable: the table never fills (3/4 plus one batch < 1)
 }
 
-// The same visited set in 16-bit slots, for ids below 2^B with B = logNB + 13
-// (logNB = log2 of the bucket count; buckets of eight slots, one 16-byte load
-// per probe).  h = id * 0x9E3779B1 mod 2^B is a bijection, so the bucket
-// h >> 13 and the 13 low bits identify the id; a slot holds those 13 bits and
-// the probe distance (0..3) in bits 13..14, hence never the empty value
-// 0xFFFF.  An id whose four buckets are full goes to the bitmap (V_PENDING)
-// on every visit, since slots are never freed.  A lost compare-and-swap means
-// another lane took a slot of the bucket, so after eight the bucket is full.
+// The same visited set in 16-bit slots, for ids below 2^B with B = logNB + 15
+// (logNB = log2 of the bucket count; buckets of eight slots, one 16-byte
+// load).  h = id * 0x9E3779B1 mod 2^B is a bijection, so the bucket h >> 15
+// and the 15 low bits identify the id; a slot holds those 15 bits, hence never
+// the empty value 0xFFFF.  Each id has a single bucket: one probe measured
+// faster than probe sequences of two, four or eight buckets.  An id whose
+// bucket is full goes to the bitmap (V_PENDING) on every visit, since slots
+// are never freed.  A lost compare-and-swap means another lane took a slot of
+// the bucket, so after eight the bucket is full.
 __device__ __forceinline__ int visit16(uint16_t* hash, int logNB, uint32_t id, bool spill_mode,
                                        uint32_t* bitmap, uint32_t& oldw) {
-    const uint32_t h = (id * 0x9E3779B1u) & ((1u << (logNB + 13)) - 1u);
-    const uint32_t nbm = (1u << logNB) - 1u;
-    const uint32_t home = h >> 13, rem = h & 0x1FFFu;
-    int retries = 0;
-    for (int dist = 0; dist < 4; ++dist) {
-        const uint32_t b = (home + (uint32_t)dist) & nbm;
-        const uint32_t want = rem | ((uint32_t)dist << 13);
-        uint4 v;
+    const uint32_t h = (id * 0x9E3779B1u) & ((1u << (logNB + 15)) - 1u);
+    const uint32_t want = h & 0x7FFFu, w2 = want * 0x10001u;
+    uint16_t* bucket = hash + 8 * CK(h >> 15, 1u << logNB, 1023);
+    const uint32_t saddr = (uint32_t)__cvta_generic_to_shared(bucket);
+    for (int tries = 0; tries <= 8; ++tries) {
+        uint4 v;   // a fresh read: other lanes may have filled slots since
         asm volatile("ld.volatile.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
                      : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
-                     : "r"((uint32_t)__cvta_generic_to_shared(hash + 8 * CK(b, nbm + 1, 1023))));
-        const uint32_t w2 = want * 0x10001u;
+                     : "r"(saddr));
         if (__vcmpeq2(v.x, w2) | __vcmpeq2(v.y, w2) | __vcmpeq2(v.z, w2) | __vcmpeq2(v.w, w2))
             return V_SEEN;
         const uint32_t em = (__vcmpeq2(v.x, 0xFFFFFFFFu) & 0x00010001u) |
                             ((__vcmpeq2(v.y, 0xFFFFFFFFu) & 0x00010001u) << 1) |
                             ((__vcmpeq2(v.z, 0xFFFFFFFFu) & 0x00010001u) << 2) |
                             ((__vcmpeq2(v.w, 0xFFFFFFFFu) & 0x00010001u) << 3);
-        if (!em) continue;   // bucket full: the id, if present, is further on
-        // the id is in no bucket of its probe sequence
-        if (spill_mode) {
-            oldw = atomicOr(&bitmap[id >> 5], 1u << (id & 31));
-            return V_PENDING;
-        }
+        if (!em || spill_mode) break;   // not in the table: the bitmap decides
         // first empty slot: word k = bit k of the low half, low/high half
         const int lo = __ffs(em & 0xFu), hi = __ffs(em >> 16);
         const int e = lo && (!hi || lo <= hi) ? 2 * (lo - 1) : 2 * (hi - 1) + 1;
-        const unsigned short old =
-            atomicCAS(reinterpret_cast<unsigned short*>(hash + 8 * b + e), (unsigned short)0xFFFFu,
-                      (unsigned short)want);
+        const unsigned short old = atomicCAS(reinterpret_cast<unsigned short*>(bucket + e),
+                                             (unsigned short)0xFFFFu, (unsigned short)want);
         if (old == 0xFFFFu) return V_NEW;
         if (old == want) return V_SEEN;
-        if (++retries <= 8) --dist;   // re-read this bucket (bounded)
     }
     oldw = atomicOr(&bitmap[id >> 5], 1u << (id & 31));
     return V_PENDING;
@@ -669,8 +660,8 @@ __global__ void __launch_bounds__(128, OCC) k_search(DevIndex ix, SearchArgs a) 
             Tk[0] = dcur;
             Ti[0] = cur;
             if (a.h16) {   // the table is empty: distance 0, first slot
-                const uint32_t h = (cur * 0x9E3779B1u) & ((1u << (logNB + 13)) - 1u);
-                reinterpret_cast<uint16_t*>(hash)[8 * (h >> 13)] = (uint16_t)(h & 0x1FFFu);
+                const uint32_t h = (cur * 0x9E3779B1u) & ((1u << (logNB + 15)) - 1u);
+                reinterpret_cast<uint16_t*>(hash)[8 * (h >> 15)] = (uint16_t)(h & 0x7FFFu);
             } else {
                 hash[4 * hbucket(cur, logNB)] = cur;
             }
