@@ -18,13 +18,15 @@
 // GB300 mapping.  A warp owns one query from an atomic work counter until the
 // batch is drained (grid = SMs x resident blocks).  Per warp in shared memory:
 // the result list T (keys and ids, the EXP bit marks expanded entries), an
-// exact visited hash (buckets of four slots) that spills to a per-warp global
-// bitmap once 3/4 full, the unit residual projection of the query, and staging.
-// One expansion is three dependent gathers: the adjacency row (coalesced,
-// lane j <- neighbour j), the per-edge rows of the new neighbours (lane-per-
-// neighbour 16-byte loads, r-dot against the query projection broadcast from
-// shared memory), and the full rows of the neighbours whose estimate passes
-// (groups of G lanes per row, 16-byte loads, shuffle reduction).  Estimates
+// exact visited hash (16-bit slots, one bucket of eight per id, where the ids
+// fit; else 32-bit slots in probed buckets of four) that spills to a per-warp
+// global bitmap once 3/4 full, the unit residual projection of the query, and
+// staging.  One expansion is three dependent gathers: the adjacency row
+// (coalesced, lane j <- neighbour j), the per-edge rows of the new neighbours
+// (FP32 FINGER: compacted, r/4 lanes per row, eight 16-byte loads per lane in
+// flight, butterfly sums; other modes: one lane per row), and the full rows
+// of the neighbours whose estimate passes (groups of G lanes per row, 16-byte
+// loads, shuffle reduction).  Estimates
 // are formed for every new neighbour against the ub at the start of the
 // expansion; the sequential gate is then replayed in adjacency order so the
 // traversal is exactly the per-neighbour one of Algorithm 4.
