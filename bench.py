@@ -62,6 +62,9 @@ def parse():
                     help="Sec. 4.4 ablation (basis and matching variants) on --cfg")
     ap.add_argument("--profile-ef", type=int, default=0,
                     help="profiling run: set up, then only --warmup + 1 FINGER searches at this ef")
+    ap.add_argument("--partitioned", type=int, default=0,
+                    help="database split into this many parts, each with its own index, results "
+                         "merged on the device (under torchrun: one part per rank)")
     return ap.parse_args()
 
 
@@ -596,6 +599,129 @@ def leg_batch(args):
     return line
 
 
+def leg_partitioned(args):
+    """Database-partitioned FINGER search on the SIFT-like workload: the base
+    rows split into P contiguous parts, each with its own GPU-built graph and
+    tables; every query is searched in every part and the parts' K nearest are
+    merged on the device (finger_merge_topk).  Under torchrun each rank holds
+    one part and the exchange is an NCCL all-gather; on one process the parts
+    run one after another on one GPU.  The timed step is the whole path: all
+    parts' searches, the exchange and the merge, for all queries."""
+    import torch
+
+    import paper_2206_11408_gb300 as fg
+    from paper_2206_11408_gb300 import replicas, shards
+
+    ws, rank, local = replicas.world()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    c = workloads.config(args.cfg)
+    n = args.n or c.n
+    nq = args.nq or c.nq
+    K = c.K
+    P = ws if ws > 1 else args.partitioned
+    mine = [rank] if ws > 1 else list(range(P))
+    X = workloads.base_vectors(args.cfg, n)
+    Q = workloads.query_vectors(args.cfg, nq)
+    q = torch.from_numpy(Q).cuda()
+    t0 = time.perf_counter()
+    parts = []
+    for p in mine:
+        lo, hi = shards.shard_range(n, p, P)
+        ix = fg.Index(X[lo:hi])
+        ix.build_graph(c.M, candidates=args.candidates or c.ef_construction,
+                       level_seed=3000 + args.cfg + 100 * p)
+        ix.build_tables(c.r, 4000 + args.cfg + 100 * p)
+        ix.set_mode(fg.MODE_FINGER, 5)
+        parts.append((lo, ix))
+    gt, _ = parts[0][1].knn(q, K) if P == 1 else (None, None)
+    if gt is None:
+        # exact kNN of the whole database, from each part's exact kNN merged
+        loc = [(ix.knn(q, K), lo) for lo, ix in parts]
+        gi = torch.stack([a[0][0] for a in loc])
+        gd = torch.stack([a[0][1] for a in loc])
+        if ws > 1:
+            gi, gd = shards.exchange(gi[0], gd[0])
+            offs = shards.offsets(parts[0][0], device=q.device)
+        else:
+            offs = [lo for _, lo in loc]
+        gt, _ = fg.merge_topk(gi, gd, offs)
+    gt = gt.cpu().numpy()
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    offs_all = [shards.shard_range(n, p, P)[0] for p in range(P)]
+
+    def step(ef):
+        outs = [ix.search(q, K, ef) for _, ix in parts]
+        gi = torch.stack([o[0] for o in outs])
+        gd = torch.stack([o[1] for o in outs])
+        if ws > 1:
+            gi, gd = shards.exchange(gi[0], gd[0])
+        return fg.merge_topk(gi, gd, offs_all)
+
+    stream = torch.cuda.current_stream()
+    curve, choice = [], None
+    for ef in (40, 60, 80, 100, 120, 140, 160, 200):
+        step(ef)
+        replicas.barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ids, d = step(ef)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = replicas.max_over_ranks([e0.elapsed_time(e1)], device=q.device)[0]
+        rec = recall_at(ids.cpu().numpy(), gt, K)
+        curve.append((ef, rec, nq / (ms / 1000)))
+        if rec >= TARGET_RECALL and choice is None:
+            choice = ef
+    if choice is None:
+        choice = max(curve, key=lambda t: t[1])[0]
+    clocks = Clocks(local)
+    for _ in range(args.warmup):
+        step(choice)
+    torch.cuda.synchronize()
+    replicas.barrier()
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        ids, d = step(choice)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    ms = replicas.max_over_ranks([e0.elapsed_time(e1) / args.steps], device=q.device)[0]
+    # the merge kernel alone, on this process's stacked inputs
+    outs = [ix.search(q, K, choice) for _, ix in parts]
+    gi = torch.stack([o[0] for o in outs])
+    gd = torch.stack([o[1] for o in outs])
+    if ws > 1:
+        gi, gd = shards.exchange(gi[0], gd[0])
+    m0, m1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    m0.record(stream)
+    for _ in range(10):
+        fg.merge_topk(gi, gd, offs_all)
+    m1.record(stream)
+    torch.cuda.synchronize()
+    for _, ix in parts:
+        ix.sync()
+    rec = recall_at(ids.cpu().numpy(), gt, K)
+    line = {"metric": "queries/sec at recall@10=0.95, FINGER on a partitioned database",
+            "value": nq / (ms / 1000), "unit": "queries/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": c.name if n == c.n else f"{c.name}[:{n}]", "n": n, "m": c.m,
+                       "nq": nq, "K": K, "M": c.M, "r": c.r, "parts": P,
+                       "parts_per_gpu": len(mine), "ef": choice},
+            "recall": rec, "curve": curve, "merge_kernel_ms": m0.elapsed_time(m1) / 10,
+            "setup_s": setup_s, "clocks": ck, "gpu_launches": args.steps * (len(mine) + 1)}
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return line if rank == 0 else None
+
+
 def leg_ablation(args):
     """Sec. 4.4 on a synthetic stand-in: FINGER's SVD basis vs a random Gaussian
     (RPLSH) basis, each with and without distribution matching.  Per variant:
@@ -674,6 +800,11 @@ def main():
         return run_reference(args)
     if args.ablation:
         print(json.dumps(leg_ablation(args)), flush=True)
+        return 0
+    if args.partitioned:
+        line = leg_partitioned(args)
+        if line is not None:
+            print(json.dumps(line), flush=True)
         return 0
     if args.cfg in (3, 4, 5):
         line = {3: leg_lp, 4: leg_mlp, 5: leg_batch}[args.cfg](args)

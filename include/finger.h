@@ -337,6 +337,27 @@ finger_status finger_mlp_predict(finger_index* ix, const float* feat, int64_t n,
 finger_status finger_knn(finger_index* ix, const float* queries, int64_t nq, int K,
                          int64_t* out_ids, float* out_dists, void* stream);
 
+/* ------------------------------------------- partitioned-database search
+ * A database split into S disjoint parts, each with its own index (graph and
+ * FINGER tables), is searched part by part (on one or several GPUs); the
+ * answer for a query is the K smallest (distance, id) keys of the union of
+ * the parts' K nearest (the kNN problem of Sec. 2 over the union).  This
+ * merge is the exchange step of that search.
+ *
+ * ids, dists: device, S x nq x K (part-major), each part's rows as returned by
+ *   finger_search on that part: ascending, ids local to the part, -1 / +inf
+ *   padded.
+ * id_offsets: host, S values >= 0 added to a part's ids (its first global id).
+ * out_ids, out_dists: device, nq x K, ascending by (distance, global id),
+ *   -1 / +inf padded when the parts hold fewer than K results in total.
+ * 1 <= S <= 64, 1 <= K <= 1024, otherwise FINGER_ERR_INVALID_ARG (also for a
+ * NULL pointer with nq > 0 or a negative offset).  Runs on the calling
+ * thread's current device, asynchronously on `stream`; the caller owns every
+ * buffer. */
+finger_status finger_merge_topk(const int64_t* ids, const float* dists, int shards, int64_t nq,
+                                int K, const int64_t* id_offsets, int64_t* out_ids,
+                                float* out_dists, void* stream);
+
 /* --------------------------------------------------- status and stats */
 
 typedef struct {

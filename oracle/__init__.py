@@ -152,6 +152,28 @@ def bruteforce(X, Q, K: int, threads: int = 0):
     return ids, d
 
 
+def merge_topk(ids_list, dists_list, offsets, K: int):
+    """K nearest over a partitioned database: the K smallest (distance, global
+    id) keys of the union of the parts' lists (the kNN problem of Sec. 2 over
+    the union).  ids_list / dists_list: one nq x K pair per part with local
+    ids (-1 = empty); offsets: each part's first global id.  Distances keep
+    their dtype; missing results are -1 / +inf."""
+    nq = ids_list[0].shape[0]
+    out_i = np.full((nq, K), -1, dtype=np.int64)
+    out_d = np.full((nq, K), np.inf, dtype=np.asarray(dists_list[0]).dtype)
+    for q in range(nq):
+        cand = []
+        for ids, d, off in zip(ids_list, dists_list, offsets):
+            for i, x in zip(ids[q], d[q]):
+                if i >= 0:
+                    cand.append((x, int(i) + int(off)))
+        cand.sort()
+        for k, (x, g) in enumerate(cand[:K]):
+            out_i[q, k] = g
+            out_d[q, k] = x
+    return out_i, out_d
+
+
 # ---------------------------------------------------------------- search
 
 

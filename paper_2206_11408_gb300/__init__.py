@@ -108,6 +108,7 @@ SIGNATURES = {
     "finger_get_predictor": (_I, [_P, _P, _P]),
     "finger_mlp_loss_grad": (_I, [_P, _I, _P, _P, _P, _I64, _P, _P, _P]),
     "finger_mlp_predict": (_I, [_P, _P, _I64, _P, _P]),
+    "finger_merge_topk": (_I, [_P, _P, _I, _I64, _I, _P, _P, _P, _P]),
 }
 
 
@@ -153,6 +154,29 @@ def _dev_ptr(t, dtype, name):
     if t.dtype != dtype or not t.is_contiguous():
         raise TypeError(f"{name} must be a contiguous {dtype} tensor")
     return ctypes.c_void_p(t.data_ptr())
+
+
+def merge_topk(ids, dists, id_offsets, stream=None):
+    """K nearest over a partitioned database: the K smallest (distance, global
+    id) keys of the parts' own lists.  ids, dists: CUDA tensors S x nq x K
+    (part-major, local ids, -1 / +inf padded); id_offsets: the S first global
+    ids.  Returns (ids, dists) as nq x K CUDA tensors."""
+    import torch
+    if ids.dim() != 3 or dists.shape != ids.shape:
+        raise ValueError("ids and dists must both be S x nq x K")
+    S, nq, K = ids.shape
+    offs = np.ascontiguousarray(np.asarray(id_offsets, dtype=np.int64))
+    if offs.shape != (S,):
+        raise ValueError(f"id_offsets must hold {S} values")
+    out_ids = torch.empty((nq, K), dtype=torch.int64, device=ids.device)
+    out_d = torch.empty((nq, K), dtype=torch.float32, device=ids.device)
+    with torch.cuda.device(ids.device):
+        _check(lib().finger_merge_topk(_dev_ptr(ids, torch.int64, "ids"),
+                                       _dev_ptr(dists, torch.float32, "dists"), S, nq, K,
+                                       _np_ptr(offs), _dev_ptr(out_ids, torch.int64, "out_ids"),
+                                       _dev_ptr(out_d, torch.float32, "out_dists"),
+                                       _stream_ptr(stream)), "finger_merge_topk")
+    return out_ids, out_d
 
 
 def table_bytes(n: int, deg0: int, r: int, lp: bool = False) -> int:

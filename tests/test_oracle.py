@@ -366,3 +366,31 @@ def test_flat_graph_is_single_layer_and_searchable():
     gt, gd = oracle.bruteforce(X, Q, 5)
     assert (ids == gt).all()
     np.testing.assert_allclose(d, gd, rtol=1e-12)
+
+
+def test_merge_of_exact_part_knn_is_exact_knn():
+    """The K nearest of a database are the K smallest keys of its parts' K
+    nearest: merging the exact kNN of three uneven parts (one smaller than K,
+    so its lists are padded) gives the exact kNN of the whole, ties included
+    (integer data produce equal distances, broken by global id)."""
+    rng = np.random.default_rng(11)
+    X = rng.integers(0, 4, size=(700, 6)).astype(np.float32)
+    Q = rng.integers(0, 4, size=(25, 6)).astype(np.float32)
+    K = 12
+    cuts = [0, 5, 300, 700]
+    ids_l, d_l = [], []
+    for lo, hi in zip(cuts[:-1], cuts[1:]):
+        i, d = oracle.bruteforce(X[lo:hi], Q, K)
+        ids_l.append(i)
+        d_l.append(d)
+    assert (ids_l[0][:, 5:] == -1).all()            # the 5-row part pads its lists
+    mi, md = oracle.merge_topk(ids_l, d_l, cuts[:-1], K)
+    gi, gd = oracle.bruteforce(X, Q, K)
+    assert (mi == gi).all()
+    assert (md == gd).all()
+    # more results asked than the parts hold in total: padded
+    i1, d1 = oracle.bruteforce(X[:3], Q, 4)
+    i2, d2 = oracle.bruteforce(X[3:5], Q, 4)
+    mi, md = oracle.merge_topk([i1, i2], [d1, d2], [0, 3], 6)
+    gi, gd = oracle.bruteforce(X[:5], Q, 6)
+    assert (mi == gi).all() and (mi[:, 5] == -1).all() and np.isinf(md[:, 5]).all()
