@@ -45,3 +45,28 @@ def test_status_strings():
     L = fg.lib()
     for s in range(9):
         assert L.finger_status_str(s)
+
+
+def test_argument_errors_are_reported_before_any_device_work():
+    """Bad arguments of the index-free merge and of the visited-slot option
+    come back as FINGER_ERR_INVALID_ARG (1) from host-side checks, so they are
+    testable without a GPU."""
+    L = fg.lib()
+    one = (ctypes.c_int64 * 1)(0)
+    neg = (ctypes.c_int64 * 2)(0, -5)
+    p = ctypes.c_void_p(16)   # never dereferenced: the checks reject first
+    args = dict(ids=p, d=p, S=1, nq=4, K=10, offs=one, oi=p, od=p)
+
+    def merge(**kw):
+        a = dict(args, **kw)
+        return L.finger_merge_topk(a["ids"], a["d"], a["S"], a["nq"], a["K"], a["offs"],
+                                   a["oi"], a["od"], None)
+
+    assert merge(S=0) == 1 and merge(S=65) == 1
+    assert merge(K=0) == 1 and merge(K=1025) == 1
+    assert merge(nq=-1) == 1
+    assert merge(offs=None) == 1
+    assert merge(S=2, offs=neg) == 1
+    assert merge(ids=None) == 1 and merge(od=None) == 1
+    assert merge(nq=0) == 0                       # nothing to merge
+    assert L.finger_set_visited_slots(None, 0) == 1
