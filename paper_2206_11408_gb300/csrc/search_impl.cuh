@@ -824,7 +824,8 @@ __global__ void __launch_bounds__(128, OCC) k_search(DevIndex ix, SearchArgs a) 
             // The new neighbours are compacted and lpr lanes share an edge row
             // (lpr = r/4 rounded up to a power of two, at most 16), so one
             // 16-byte load per lane covers 32 / lpr rows and eight loads per
-            // lane are in flight at once; an lpr-lane butterfly sums each row.
+            // lane are in flight at once; the row sums come from a
+            // transpose-reduce over the row's lanes (a butterfly for lpr = 4).
             constexpr bool BAL = MODE == FINGER_MODE_FINGER;
             constexpr int GS = 8;
             float2 scv[NPL];
@@ -856,15 +857,48 @@ __global__ void __launch_bounds__(128, OCC) k_search(DevIndex ix, SearchArgs a) 
                                        ? __ldg(eb + (size_t)lst[CK(i, 32 * NPL, 1021)] * ix.r4 + k4)
                                        : make_float4(0.f, 0.f, 0.f, 0.f);
                         }
+                        float pg[GS];
 #pragma unroll
                         for (int g = 0; g < GS; ++g) {
-                            float p = x[g].x * y.x;
-                            p = fmaf(x[g].y, y.y, p);
-                            p = fmaf(x[g].z, y.z, p);
-                            p = fmaf(x[g].w, y.w, p);
-                            for (int o = lpr >> 1; o > 0; o >>= 1) p += __shfl_xor_sync(FULLMASK, p, o);
-                            const int i = base + g * rps + sub;
-                            if (k4 == 0 && i < nn) xb[lst[CK(i, 32 * NPL, 1022)]] = p;
+                            pg[g] = x[g].x * y.x;
+                            pg[g] = fmaf(x[g].y, y.y, pg[g]);
+                            pg[g] = fmaf(x[g].z, y.z, pg[g]);
+                            pg[g] = fmaf(x[g].w, y.w, pg[g]);
+                        }
+                        if (lpr >= 8) {
+                            // transpose-reduce over the row's lanes: each step hands the
+                            // partner lane half of the remaining slots, so the eight
+                            // sums take 8 shuffles instead of 8 x log2(lpr)
+                            const bool hi8 = lpr == 16;
+                            const int kb = hi8 ? k4 >> 1 : k4;   // slot this lane ends with
+                            const int o0 = lpr >> 1;
+                            float q4[4], q2[2];
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) {
+                                const bool b = kb & 4;
+                                const float sd = b ? pg[j] : pg[j + 4];
+                                q4[j] = (b ? pg[j + 4] : pg[j]) + __shfl_xor_sync(FULLMASK, sd, o0);
+                            }
+#pragma unroll
+                            for (int j = 0; j < 2; ++j) {
+                                const bool b = kb & 2;
+                                const float sd = b ? q4[j] : q4[j + 2];
+                                q2[j] = (b ? q4[j + 2] : q4[j]) + __shfl_xor_sync(FULLMASK, sd, o0 >> 1);
+                            }
+                            const bool b1 = kb & 1;
+                            float t = (b1 ? q2[1] : q2[0]) +
+                                      __shfl_xor_sync(FULLMASK, b1 ? q2[0] : q2[1], o0 >> 2);
+                            if (hi8) t += __shfl_xor_sync(FULLMASK, t, 1);
+                            const int i = base + kb * rps + sub;
+                            if ((!hi8 || !(k4 & 1)) && i < nn) xb[lst[CK(i, 32 * NPL, 1022)]] = t;
+                        } else {
+#pragma unroll
+                            for (int g = 0; g < GS; ++g) {
+                                float p = pg[g];
+                                for (int o = lpr >> 1; o > 0; o >>= 1) p += __shfl_xor_sync(FULLMASK, p, o);
+                                const int i = base + g * rps + sub;
+                                if (k4 == 0 && i < nn) xb[lst[CK(i, 32 * NPL, 1022)]] = p;
+                            }
                         }
                     }
                     __syncwarp();
