@@ -341,7 +341,7 @@ finger_status finger_knn(finger_index* ix, const float* queries, int64_t nq, int
  * A database split into S disjoint parts, each with its own index (graph and
  * FINGER tables), is searched part by part (on one or several GPUs); the
  * answer for a query is the K smallest (distance, id) keys of the union of
- * the parts' K nearest (the kNN problem of Sec. 2 over the union).  This
+ * the parts' K nearest (the kNN problem of Sec. 1 over the union).  This
  * merge is the exchange step of that search.
  *
  * ids, dists: device, S x nq x K (part-major), each part's rows as returned by

@@ -154,7 +154,7 @@ def bruteforce(X, Q, K: int, threads: int = 0):
 
 def merge_topk(ids_list, dists_list, offsets, K: int):
     """K nearest over a partitioned database: the K smallest (distance, global
-    id) keys of the union of the parts' lists (the kNN problem of Sec. 2 over
+    id) keys of the union of the parts' lists (the kNN problem of Sec. 1 over
     the union).  ids_list / dists_list: one nq x K pair per part with local
     ids (-1 = empty); offsets: each part's first global id.  Distances keep
     their dtype; missing results are -1 / +inf."""

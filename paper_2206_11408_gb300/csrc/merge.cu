@@ -2,7 +2,7 @@
 //
 // The K nearest neighbours of a query over a partitioned database are the K
 // smallest (distance, id) keys of the union of the partitions' own K nearest
-// (the kNN problem of Sec. 2 applied to the union; keys ordered as in the
+// (the kNN problem of Sec. 1 applied to the union; keys ordered as in the
 // search, distance then id).  One warp per query ranks every candidate of the
 // S lists against all others and writes those of rank < K to their slot.
 #include "internal.cuh"

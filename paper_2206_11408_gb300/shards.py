@@ -3,7 +3,7 @@
 The database is split into contiguous parts; every process holds the index
 (graph and FINGER tables) of its own part, searches every query there, and
 the parts' K nearest are exchanged and merged into the K nearest of the whole
-database (the kNN problem of Sec. 2 of arXiv 2206.11408 over the union of the
+database (the kNN problem of Sec. 1 of arXiv 2206.11408 over the union of the
 parts).  Unlike query replicas (``replicas.py``) this path has a real exchange
 step: an all-gather of nq x K (id, distance) pairs per part, then the top-K
 merge on the device (``finger_merge_topk``).  Results differ from one index
