@@ -67,6 +67,8 @@ def lib():
         L.orc_sample_pairs.argtypes = [P, i64, i32, u64, i32, P]
         L.orc_estimate.argtypes = [P, P, P, i32, P, i32, P]
         L.orc_estimate.restype = ctypes.c_double
+        L.orc_estimate_mlp.argtypes = [P, P, P, i32, P, i32, P, P, ctypes.c_double, P, P]
+        L.orc_estimate_mlp.restype = ctypes.c_double
         _lib = L
     return _lib
 
@@ -233,6 +235,21 @@ def estimate(q, c, d, fp: FingerParams) -> float:
     q, c, d, P = _f64(q), _f64(c), _f64(d), _f64(fp.P)
     st = fp.stats()
     return float(lib().orc_estimate(_p(q), _p(c), _p(d), q.shape[0], _p(P), P.shape[0], _p(st)))
+
+
+def estimate_mlp(q, c, d, fp: FingerParams, mlp_weights, mlp_eps: float = 0.0):
+    """Algorithm 3 on one triple with the learned predictor in place of
+    distribution matching (extension), as the oracle's search applies it.
+    Returns (estimate, features (r + 4), raw prediction)."""
+    q, c, d, P = _f64(q), _f64(c), _f64(d), _f64(fp.P)
+    st = fp.stats()
+    w = _f64(mlp_weights)
+    r = P.shape[0]
+    f = np.zeros(r + 4, np.float64)
+    y = np.zeros(1, np.float64)
+    e = lib().orc_estimate_mlp(_p(q), _p(c), _p(d), q.shape[0], _p(P), r, _p(st), _p(w),
+                               float(mlp_eps), _p(f), _p(y))
+    return float(e), f, float(y[0])
 
 
 # --------------------------------------------------- Algorithm 2 (FINGER build)

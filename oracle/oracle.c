@@ -353,7 +353,8 @@ static double mlp_predict(const double* w, int nf, const double* f) {
 static double appx_dist(const double* xc, const double* xd, int m, double cc, const double* q_proj,
                         const double* q_res, double qres_n2, const double* Pq, const double* P,
                         int r, const double* st, double* d_proj, double* d_res, double* diff,
-                        double* Pd, const double* q, const double* mlp, double mlp_eps) {
+                        double* Pd, const double* q, const double* mlp, double mlp_eps,
+                        double* f_out, double* y_out) {
     double mu = st[0], sigma = st[1], muh = st[2], sigmah = st[3], eps = st[4];
     double ratio = sigmah > 0 ? sigma / sigmah : 0.0;
     double b = cc > 0 ? dot(xc, xd, m) / cc : 0.0;
@@ -380,6 +381,9 @@ static double appx_dist(const double* xc, const double* xd, int m, double cc, co
         f[r + 2] = ndn > 0 ? sqrt(dres_n2) / ndn : 0.0;
         f[r + 3] = a / (fabs(a) + fabs(b) + 1e-6);
         double y = mlp_predict(mlp, r + 4, f);
+        if (f_out)
+            for (int k = 0; k < r + 4; ++k) f_out[k] = f[k];
+        if (y_out) *y_out = y;
         if (isfinite(y)) t = y + mlp_eps;
     }
     (void)q_res;
@@ -414,7 +418,29 @@ double orc_estimate(const double* q, const double* xc, const double* xd, int m, 
     double qres_n2;
     double cc = centre_parts(xc, q, m, P, r, q_proj, q_res, &qres_n2, Pq);
     double e = appx_dist(xc, xd, m, cc, q_proj, q_res, qres_n2, Pq, P, r, stats, d_proj, d_res,
-                         diff, Pd, q, NULL, 0.0);
+                         diff, Pd, q, NULL, 0.0, NULL, NULL);
+    free(w);
+    return e;
+}
+
+/* Algorithm 3 with the learned predictor in place of distribution matching
+ * (extension), exposed for tests: the r + 4 features the predictor saw go to
+ * f_out, its raw output to y_out; returns the estimate. */
+double orc_estimate_mlp(const double* q, const double* xc, const double* xd, int m,
+                        const double* P, int r, const double* stats, const double* mlp,
+                        double mlp_eps, double* f_out, double* y_out) {
+    double* w = (double*)malloc(sizeof(double) * (size_t)(6 * m + 2 * r + 2));
+    double* q_proj = w;
+    double* q_res = w + m;
+    double* d_proj = w + 2 * m;
+    double* d_res = w + 3 * m;
+    double* diff = w + 4 * m;
+    double* Pq = w + 5 * m;
+    double* Pd = Pq + r;
+    double qres_n2;
+    double cc = centre_parts(xc, q, m, P, r, q_proj, q_res, &qres_n2, Pq);
+    double e = appx_dist(xc, xd, m, cc, q_proj, q_res, qres_n2, Pq, P, r, stats, d_proj, d_res,
+                         diff, Pd, q, mlp, mlp_eps, f_out, y_out);
     free(w);
     return e;
 }
@@ -494,7 +520,7 @@ static void search_one(const double* X, int m, const int32_t* adj0, int deg0, co
             int full = tlen == ef;
             if (use_est && full) {
                 double est = appx_dist(xc, xd, m, cc, q_proj, q_res, qres_n2, Pq, P, r, st,
-                                       d_proj, d_res, diff, Pd, q, mlp, mlp_eps);
+                                       d_proj, d_res, diff, Pd, q, mlp, mlp_eps, NULL, NULL);
                 cnt[CNT_ESTIMATES]++;
                 double ub = T[tlen - 1].kv.d;
                 if (est > ub) {

@@ -136,6 +136,69 @@ def test_greedy_path_graph_hand_trace():
     assert ids[0].tolist() == [7, 8, 6]
 
 
+def _alg4_case():
+    import json
+    t = json.load(open(os.path.join(GOLDEN, "alg4_hand_trace.json")))
+    names = sorted(t["ids"], key=t["ids"].get)
+    X = np.array([t["points"][k] for k in names], np.float64)
+    rows = [[t["ids"][v] for v in t["adjacency"][k]] for k in names]
+    g = _graph_from_rows(rows, 2, M=1)
+    g.entry = t["ids"][t["entry"]]
+    s = t["stats"]
+    fp = oracle.FingerParams(np.array(t["P"], np.float64), s["mu"], s["sigma"], s["mu_hat"],
+                             s["sigma_hat"], s["eps"])
+    return t, X, g, fp
+
+
+def test_finger_hand_trace_warmup_and_gate():
+    """Algorithm 4 traced by hand (tests/golden/alg4_hand_trace.json).
+
+    Points A=(0,2), B=(0,4), C=(0,-8), D=(-6,-1); path graph A-B-C-D; entry A;
+    q = (-1,-4); ef = K = 2; P = [1, 0] (r = 1); mu = 1/4, sigma = 1,
+    mu_hat = 1/2, sigma_hat = 2, eps = 1/4, so t = (t_hat - 1/2)/2 + 1/4 + 1/4
+    = t_hat/2 + 1/4.  Every quantity below is exact in binary floating point.
+
+    d(q,A) = 1 + 36 = 37.  T = [A 37].
+    Expansion 1 (c = A, warm-up): B is new, exact d = 1 + 64 = 65, |T| < ef:
+      admitted.  T = [A* 37, B 65].
+    Expansion 2 (c = B = (0,4), ||c||^2 = 16): C is new and |T| = ef.
+      With warm-up 1 it is estimated: a = q.c/16 = -1, b = c.C/16 = -2,
+      q_res = (-1,0), C_res = (0,0), so t_hat = 0 (zero norm) and
+      est = (a-b)^2 16 + 1 + 0 - 0 = 17 < ub = 65: not skipped.
+      With warm-up 2 it is exact without an estimate.  Exact d = 1 + 16 = 17,
+      admitted; A is visited.  T = [C 17, A* 37].
+    Expansion 3 (c = C = (0,-8), ||c||^2 = 64): D is new, |T| = ef, estimated
+      (both warm-ups): a = 32/64 = 1/2, b = 8/64 = 1/8, q_res = (-1,0),
+      D_res = (-6,0), P q_res = -1, P D_res = -6, t_hat = 1, t = 3/4;
+      est = (3/8)^2 64 + 1 + 36 - 2*1*6*3/4 = 9 + 37 - 9 = 37 = ub (A).
+      Algorithm 4 skips only an estimate above ub: D gets its exact distance
+      25 + 9 = 34 < 37 and is admitted.  T = [C* 17, D 34].
+      (A gate that also skipped est = ub would drop D and end with [C, A].)
+    Expansion 4 (c = D): C is visited.  No unexpanded entry remains.
+    Counters: expansions 4, examined 3 (B, C, D), estimates 2 (warm-up 1) or
+    1 (warm-up 2), skipped 0, exact 3, admitted 3.
+
+    A warm-up counted one expansion late or early, or a gate that skips on
+    equality, changes these counters."""
+    t, X, g, fp = _alg4_case()
+    q = np.array([t["query"]], np.float64)
+    names = {v: k for k, v in t["ids"].items()}
+    for key, warmup in (("warmup1_strict", 1), ("warmup2_strict", 2)):
+        exp = t["expected"][key]
+        ids, d, c = oracle.search(g, X, q, t["K"], t["ef"], fp, warmup=warmup)
+        assert [names[i] for i in ids[0]] == exp["ids"], key
+        assert d[0].tolist() == exp["dists"], key
+        cnt = dict(zip(oracle.CNT_NAMES, c[0]))
+        for k in ("expansions", "examined", "estimates", "skipped", "exact", "admitted"):
+            assert cnt[k] == exp[k], (key, k, cnt[k], exp[k])
+    # the estimate that meets ub exactly, from Algorithm 3 alone
+    assert oracle.estimate(q[0], X[2], X[3], fp) == 37.0
+    assert oracle.estimate(q[0], X[1], X[2], fp) == 17.0
+    # the exact-distance branch for D is what makes the two gate readings differ
+    nonstrict = t["expected"]["warmup1_nonstrict"]
+    assert nonstrict["ids"] != t["expected"]["warmup1_strict"]["ids"]
+
+
 def test_greedy_complete_graph_is_bruteforce():
     rng = np.random.default_rng(1)
     X = rng.standard_normal((60, 5))

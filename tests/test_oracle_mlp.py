@@ -98,3 +98,37 @@ def test_predictor_hook_constant_equals_matching(small):
                                mlp_eps=e0)
     assert (i1 == i2).all() and (c1 == c2).all()
     assert c1[:, 3].sum() > 0
+
+
+def test_c_predictor_matches_numpy_forward():
+    """The predictor inside the oracle's search (oracle.c: features assembled in
+    Algorithm 3, then the r+4 -> 64 -> 64 -> 1 network) against the numpy
+    definition in oracle/mlp.py, on random BF16 weights with non-zero biases
+    (every layer matters), random triples and both signs of every feature."""
+    rng = np.random.default_rng(11)
+    m, r = 24, 6
+    nf = r + 4
+    P = np.linalg.qr(rng.standard_normal((m, m)))[0][:r]
+    w = mlp.init(nf, 12)
+    w[mlp.H * nf:mlp.H * nf + mlp.H] = rng.normal(0, 0.3, mlp.H)            # b1
+    w[-(2 * mlp.H + 1):-(mlp.H + 1)] = rng.normal(0, 0.3, mlp.H)             # b2
+    w[-1] = 0.125                                                            # b3
+    w = mlp.quantize_weights(w, nf)
+    fp = oracle.FingerParams(P, 0.1, 0.9, 0.05, 1.1, 0.02)
+    eps_p = 0.03
+    outs = []
+    for _ in range(50):
+        q, c, d = rng.standard_normal((3, m))
+        est, f_c, y_c = oracle.estimate_mlp(q, c, d, fp, w, eps_p)
+        f_np, _ = mlp.features(q, c, d, P)
+        np.testing.assert_allclose(f_c, f_np, rtol=1e-12, atol=1e-14)
+        y_np, _ = mlp.forward(w, f_np[None, :], nf, round_act=True)
+        assert y_c == pytest.approx(float(y_np[0]), rel=1e-12, abs=1e-12)
+        # the estimate uses t = prediction + eps' in Eq. (2)
+        cc = c @ c
+        a, b = (c @ q) / cc, (c @ d) / cc
+        qr, dr = q - a * c, d - b * c
+        ref = (a - b) ** 2 * cc + qr @ qr + dr @ dr - 2 * np.linalg.norm(qr) * np.linalg.norm(dr) * (y_c + eps_p)
+        assert est == pytest.approx(ref, rel=1e-12, abs=1e-12)
+        outs.append(y_c)
+    assert np.std(outs) > 1e-3          # the network is not constant on these inputs
