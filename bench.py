@@ -60,7 +60,7 @@ def parse():
     ap.add_argument("--flat", action="store_true",
                     help="single-layer graph (no HNSW hierarchy) instead of HNSW")
     ap.add_argument("--ablation", action="store_true",
-                    help="Sec. 4.4 ablation (basis and matching variants) on --cfg")
+                    help="Sec. 4.3 ablation (basis and matching variants) on --cfg")
     ap.add_argument("--profile-ef", type=int, default=0,
                     help="profiling run: set up, then only --warmup + 1 FINGER searches at this ef")
     ap.add_argument("--partitioned", type=int, default=0,
@@ -724,7 +724,7 @@ def leg_partitioned(args):
 
 
 def leg_ablation(args):
-    """Sec. 4.4 on a synthetic stand-in: FINGER's SVD basis vs a random Gaussian
+    """Sec. 4.3 on a synthetic stand-in: FINGER's SVD basis vs a random Gaussian
     (RPLSH) basis, each with and without distribution matching.  Per variant:
     the approximation error |t - t_hat| / |t| of the residual cosine on triples
     harvested from FINGER traversals of training queries (t the true cosine,
@@ -787,7 +787,7 @@ def leg_ablation(args):
         cs = cnt.sum(0).cpu().numpy().astype(np.float64) / nq_s
         pts.append([ef, round(recall_at(ids.cpu().numpy(), gt, c.K), 4), round(cs[4] + cs[6], 1)])
     out["plain"] = {"curve_ef_recall_effcalls": pts}
-    return {"metric": "Sec. 4.4 ablation: approximation error and recall@10 vs effective "
+    return {"metric": "Sec. 4.3 ablation: approximation error and recall@10 vs effective "
                       "distance calls", "impl": "ours", "n_gpus": 1, "data": "synthetic",
             "config": {"workload": c.name if n == c.n else f"{c.name}[:{n}]", "n": n, "m": c.m,
                        "r": c.r, "M": c.M, "nq": nq_s},

@@ -125,8 +125,16 @@ typedef struct {
 
 finger_status finger_get_info(const finger_index* ix, finger_info* out);
 
-/* Save / load the whole index (vectors, graph, tables, predictor) in a
- * versioned little-endian binary file.  load places it on `device`. */
+/* Save / load the whole search index in a versioned little-endian binary
+ * file: the vectors, the graph, and what FINGER precomputes once and stores
+ * with the index before any query (Sec. 3.3: the basis P and the matching
+ * statistics; Supplementary G: c^T c and P c per node, and per layer-0 edge
+ * the unit projected residual, ||d_res|| and b, whose memory Supplementary F
+ * accounts as (r + 2) floats per edge), plus the LP tables and the learned
+ * predictor when present.  load places it on `device`.  The caller owns
+ * `path`; *out receives a new index the caller frees with finger_index_free.
+ * Errors: FINGER_ERR_IO (open/read/write), FINGER_ERR_FORMAT (magic, version
+ * or sizes), FINGER_ERR_OOM, FINGER_ERR_CUDA. */
 finger_status finger_index_save(const finger_index* ix, const char* path);
 finger_status finger_index_load(const char* path, int device, finger_index** out);
 void finger_index_free(finger_index* ix);
@@ -141,7 +149,7 @@ typedef struct {
     const double* stats_host; /* optional {mu, sigma, mu_hat, sigma_hat, eps};
                                  NULL = computed from the sampled pairs */
     int build_lp;             /* also build BF16 rows and FP8-e4m3 codes (mode LP) */
-    int flags;                /* ablations of Sec. 4.4, 0 = the full method:
+    int flags;                /* ablations of Sec. 4.3, 0 = the full method:
                                  FINGER_BUILD_NO_MATCHING: t = t_hat + eps
                                  (stored as mu = mu_hat = 0, sigma = sigma_hat
                                  = 1; eps = mean |Y - X|);
@@ -220,9 +228,11 @@ finger_status finger_search_host(finger_index* ix, const float* queries_host, in
  * whose kernels overlap on the GPU race on it and must be serialised.  The
  * first call on a device looks up the array's device address and caches it;
  * make that first call before any stream capture.  A launch uses as many
- * resident warps as the array holds (ceil(n/32) bitmap words + up to 16384
- * spill ids per warp); if not even one fits (n above roughly 5e8) the call
- * returns FINGER_ERR_UNSUPPORTED.  Asynchronous on `stream`. */
+ * resident warps as the array holds (ceil(n/32) bitmap words + the same spill
+ * list as finger_search, min(max(n, 64), 65536) ids, per warp: about 176
+ * warps at n = 1M, so large batches run on fewer warps than finger_search);
+ * if not even one fits (n above roughly 5e8) the call returns
+ * FINGER_ERR_UNSUPPORTED.  Asynchronous on `stream`. */
 finger_status finger_search_noalloc(finger_index* ix, const float* queries, int64_t nq, int K,
                                     int ef, int64_t* out_ids, float* out_dists, void* stream);
 
@@ -372,6 +382,14 @@ typedef struct {
 
 /* Synchronise the index's device and return the latched kernel status. */
 finger_status finger_sync(finger_index* ix);
+
+/* Synchronise and copy the summed traversal counters and the latched status
+ * into *out (caller-owned).  The counters are the quantities the paper
+ * measures the method by: "exact" plus "upper" are the full m-dimensional
+ * distance calls and "estimates" the r-dimensional ones, which combine into
+ * Sec. 4.3's effective number of distance calls (full + estimates * r / m);
+ * "skipped" counts the estimates that exceeded the upper bound, the calls
+ * Sec. 3.1 observes to be the large majority after the first steps. */
 finger_status finger_get_stats(finger_index* ix, finger_stats* out);
 finger_status finger_reset_stats(finger_index* ix);
 const char* finger_status_str(finger_status s);

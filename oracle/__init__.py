@@ -314,7 +314,7 @@ def pair_cosines(X, pairs: np.ndarray, P: np.ndarray, chunk: int = 1 << 16):
 def matching_stats(Xc: np.ndarray, Yc: np.ndarray, matching: bool = True, use_eps: bool = True):
     """mu, sigma (std), mu_hat, sigma_hat, eps of Algorithm 2 (population 1/N).
 
-    Ablations of Sec. 4.4: ``matching=False`` keeps the low-rank cosine as it
+    Ablations of Sec. 4.3: ``matching=False`` keeps the low-rank cosine as it
     is (the map becomes t = t_hat + eps, returned as mu = mu_hat = 0,
     sigma = sigma_hat = 1) and eps is then the mean |Y - X|;
     ``use_eps=False`` drops the error-correction term (eps = 0)."""
@@ -359,7 +359,7 @@ def build_tables(X, g: Graph, r: int, seed: int, samples_per_node: int = 1,
                  matching: bool = True, use_eps: bool = True):
     """Algorithm 2: sample S, D_res, SVD -> P, then the matching statistics.
 
-    ``basis`` (r x m) replaces the SVD basis (the RPLSH comparison of Sec. 4.4
+    ``basis`` (r x m) replaces the SVD basis (the RPLSH comparison of Sec. 4.3
     passes a random Gaussian matrix); ``matching`` / ``use_eps`` are the
     ablations of :func:`matching_stats`."""
     pairs = sample_pairs(g.adj0, seed, samples_per_node)

@@ -271,7 +271,7 @@ class Index:
                      build_lp: bool = False, matching: bool = True, use_eps: bool = True,
                      stream=None):
         """finger_build_tables.  ``basis`` (r x m) replaces the SVD basis (e.g.
-        a random Gaussian matrix: the RPLSH comparison of Sec. 4.4); ``matching``
+        a random Gaussian matrix: the RPLSH comparison of Sec. 4.3); ``matching``
         and ``use_eps`` False are the ablations of FINGER_BUILD_NO_MATCHING and
         FINGER_BUILD_NO_EPS."""
         keep = []

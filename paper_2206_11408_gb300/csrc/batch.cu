@@ -13,6 +13,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <mutex>
 #include <vector>
 
 #include "internal.cuh"
@@ -41,14 +42,30 @@ struct Captured {
     cudaKernelNodeParams kp{};
 };
 
-std::map<const finger_index*, std::map<std::pair<int64_t, int>, Captured>>& captures() {
-    static std::map<const finger_index*, std::map<std::pair<int64_t, int>, Captured>> c;
+using CaptureMap = std::map<std::pair<int64_t, int>, Captured>;
+
+// Captured graphs of every index, keyed by index.  The outer map is shared by
+// all indices, so every lookup, insertion and removal of an index's entry
+// holds the mutex; the inner map of one index is touched only by calls on
+// that index (which callers serialise) and std::map keeps its node in place
+// while other indices come and go.
+std::map<const finger_index*, CaptureMap>& captures() {
+    static std::map<const finger_index*, CaptureMap> c;
     return c;
+}
+std::mutex& captures_mutex() {
+    static std::mutex mu;
+    return mu;
+}
+CaptureMap& captures_of(const finger_index* ix) {
+    std::lock_guard<std::mutex> lock(captures_mutex());
+    return captures()[ix];
 }
 
 }  // namespace
 
 void fg_drop_captures(const finger_index* ix) {
+    std::lock_guard<std::mutex> lock(captures_mutex());
     auto it = captures().find(ix);
     if (it == captures().end()) return;
     for (auto& kv : it->second) {
@@ -108,7 +125,7 @@ finger_status finger_search_batch(finger_index* ix, const float* queries, int64_
     a.rerank = 32;
     const DevIndex d = make_dev(ix);
     const auto key = std::make_pair(nqb, bucket * 4 + ix->mode);
-    auto& caps = captures()[ix];
+    auto& caps = captures_of(ix);
     auto it = caps.find(key);
     finger_status ret = FINGER_OK;
     if (it == caps.end()) {

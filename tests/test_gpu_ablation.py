@@ -1,4 +1,4 @@
-"""GPU parity of the ablation switches (Sec. 4.4) and of the rank rule
+"""GPU parity of the ablation switches (Sec. 4.3) and of the rank rule
 (Supplementary E) against the FP64 oracle, on the oracle's own HNSW graph of
 the 10,000-point, 64-dimensional Gaussian mixture.
 

@@ -1,4 +1,4 @@
-"""Pins of the oracle's ablation switches (Sec. 4.4: RPLSH basis, no
+"""Pins of the oracle's ablation switches (Sec. 4.3: RPLSH basis, no
 distribution matching, no error term) and of the rank rule (Supplementary E),
 each against something other than the oracle itself: a library routine, a
 closed form, or an algorithmic reduction."""
