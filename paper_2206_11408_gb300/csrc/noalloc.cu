@@ -19,17 +19,27 @@
 // name as a device address, so the first call on each device (with that device
 // current) looks the address up with cudaGetSymbolAddress and caches it; that
 // first call should come before any stream capture.  Every call shares the
-// array and the array keeps the previous call's contents: each call clears the
-// work counter and the visited bitmaps it is about to use.  Two calls whose
-// kernels overlap on the GPU (on different streams, or from several host
-// threads) race on the array; callers must serialise them.
+// array and the array keeps the previous call's contents.  What must start at
+// zero is the work counter and every visited bitmap.  Each call clears the
+// counter (the array's first 256 bytes).  The bitmaps need no clear per call:
+// the kernel sets a bitmap bit only for an id it also appends to the query's
+// spill list, and before the query ends (also when it stops at a limit) it
+// zeroes every word the list names, so a launch that runs to completion leaves
+// its bitmap region zero.  The spill lists follow that region and keep ids, so
+// the library remembers, per device, where the zeroed region ends: a call
+// whose bitmaps reach beyond it (the first call on a device, a larger n or
+// more warps than the call before, or any call after one whose launch failed
+// to enqueue) clears its whole bitmap region first.  Two calls whose kernels
+// overlap on the GPU (on different streams, or from several host threads)
+// race on the array; callers must serialise them.
 //
 // Capacity: a launch needs, per resident warp, ceil(n / 32) words of bitmap
-// (padded to 16 bytes) and a spill list of min(max(n, 64), 16384) ids.  The
-// launch uses as many warps as fit (fewer than finger_search when n is large);
-// if not even one warp fits (n above roughly 5e8) the call returns
-// FINGER_ERR_UNSUPPORTED.  A query whose visited set outgrows its spill list
-// stops early and latches FINGER_ERR_LIMIT, as in finger_search.
+// (padded to 16 bytes) and a spill list of min(max(n, 64), 65536) ids, the
+// same list length as finger_search, so a query ends with the same results and
+// status as there.  The launch uses as many warps as fit: at n = 1M about 176
+// (finger_search runs several thousand), at n = 200k about 233; below four
+// warps the block shrinks (n above roughly 1.3e8); if not even one warp fits
+// (n above roughly 5e8) the call returns FINGER_ERR_UNSUPPORTED.
 #include <algorithm>
 #include <mutex>
 
@@ -47,11 +57,13 @@ namespace {
 constexpr size_t NOALLOC_SCRATCH_BYTES = size_t(64) << 20;
 constexpr size_t NOALLOC_HEADER = 256;     // work counter, padded
 constexpr int NOALLOC_MAX_DEVICES = 64;
-constexpr int NOALLOC_SPILL_CAP = 16384;
+constexpr int NOALLOC_SPILL_CAP = 1 << 16;   // as in finger_search
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
 
 void* g_scratch_addr[NOALLOC_MAX_DEVICES] = {};
+// end (byte offset) of the bitmap region known to be zero after the last call
+size_t g_zero_end[NOALLOC_MAX_DEVICES] = {};
 std::mutex g_scratch_mu;
 
 // device address of the scratch array on the current device (looked up once)
@@ -66,6 +78,16 @@ cudaError_t scratch_address(int device, void** out) {
     }
     *out = g_scratch_addr[device];
     return cudaSuccess;
+}
+
+size_t zero_end(int device) {
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    return g_zero_end[device];
+}
+
+void set_zero_end(int device, size_t end) {
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    g_zero_end[device] = end;
 }
 
 }  // namespace
@@ -112,11 +134,14 @@ extern "C" finger_status finger_search_noalloc(finger_index* ix, const float* qu
             uint32_t* bitmap = reinterpret_cast<uint32_t*>(b + NOALLOC_HEADER);
             uint32_t* spill = bitmap + slots * words;
             cudaStream_t s = (cudaStream_t)stream;
-            // the array keeps the last call's contents: clear the work counter
-            // and the bitmaps of the warps this launch uses
-            if (cudaMemsetAsync(b, 0, NOALLOC_HEADER + (size_t)(slots * words * 4), s) !=
-                cudaSuccess) {
+            // the array keeps the last call's contents: the work counter is
+            // cleared on every call, this call's bitmap region only where it
+            // reaches beyond the region known to be zero (see the file comment)
+            const size_t need = NOALLOC_HEADER + (size_t)(slots * words * 4);
+            const size_t clear = need <= zero_end(ix->device) ? NOALLOC_HEADER : need;
+            if (cudaMemsetAsync(b, 0, clear, s) != cudaSuccess) {
                 cudaGetLastError();
+                set_zero_end(ix->device, 0);
                 ret = FINGER_ERR_CUDA;
             } else {
                 SearchArgs a = fg_base_args(ix, p);
@@ -134,8 +159,10 @@ extern "C" finger_status finger_search_noalloc(finger_index* ix, const float* qu
                 a.spill_cap = spill_cap;
                 if (launch_search(make_dev(ix), a, p, s) != cudaSuccess) {
                     cudaGetLastError();
+                    set_zero_end(ix->device, 0);
                     ret = FINGER_ERR_CUDA;
                 } else {
+                    set_zero_end(ix->device, need);
                     ix->searches += nq;
                 }
             }
