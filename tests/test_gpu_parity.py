@@ -2,15 +2,16 @@
 
 Workload: the 10,000-point, 64-dimensional 16-cluster Gaussian mixture with
 200 queries, an HNSW graph (M = 16, efConstruction = 100) built by the oracle,
-FINGER rank 16.  Bars: result lists identical to the oracle on >= 99 % of
-queries, per-pair distances within 1e-5 relative of FP64, recall@10 within
-0.002 of the oracle's at the same ef, traversal counters identical on the
-queries whose lists match.
+FINGER rank 16.  Bars (tests/parity_util.py): result lists identical to the
+oracle on >= 99 % of queries, per-pair distances within 1e-5 relative of FP64,
+recall@10 within 0.002 of the oracle's at the same ef, traversal counters
+identical on >= 97 % of the queries whose lists match.
 """
 import numpy as np
 import pytest
 
 import oracle
+import parity_util
 import workloads
 
 torch = pytest.importorskip("torch")
@@ -36,48 +37,8 @@ def cfg1():
     ix.close()
 
 
-def _gpu_search(ix, q, K, ef, mode, warmup=5):
-    ix.set_mode(mode, warmup)
-    cnt = torch.zeros((q.shape[0], 8), dtype=torch.int32, device="cuda")
-    ix.set_counters(cnt)
-    ids, d = ix.search(q, K, ef)
-    torch.cuda.synchronize()
-    ix.sync()
-    ix.set_counters(None)
-    return ids.cpu().numpy(), d.cpu().numpy(), cnt.cpu().numpy()
-
-
-def _fp32_canonical(oi, od):
-    """The oracle's lists reordered by (FP32 distance, id): the kernel computes
-    distances in FP32 and breaks exact ties by id, so two entries whose FP64
-    distances differ below FP32 resolution are a tie at the kernel's precision
-    (their order is not unique; the set and the traversal still are)."""
-    d32 = od.astype(np.float32)
-    out = oi.copy()
-    for qi in range(oi.shape[0]):
-        valid = oi[qi] >= 0
-        order = np.lexsort((oi[qi][valid], d32[qi][valid]))
-        out[qi, :valid.sum()] = oi[qi][valid][order]
-    return out
-
-
-def _compare(gi, gd, gc, oi, od, oc, gt, K, what):
-    oi = _fp32_canonical(oi, od)
-    od = np.sort(od, axis=1)
-    match = (gi == oi).all(axis=1)
-    assert match.mean() >= 0.99, f"{what}: {match.mean():.4f} of lists identical"
-    ok = oi[match] >= 0
-    rel = np.abs(gd[match][ok] - od[match][ok]) / np.maximum(od[match][ok], 1e-30)
-    assert rel.max() < REL, f"{what}: max rel distance error {rel.max():.2e}"
-    # counters: expansions, examined, estimates, skipped, exact, admitted, upper.
-    # An estimate within FP32 rounding of ub can flip one gate decision without
-    # changing the result list, so equal counters are required on 97 % of the
-    # queries whose lists match.
-    same = (gc[match][:, :7] == oc[match][:, :7]).all(axis=1)
-    diff = np.abs(gc[match][~same][:, :7].astype(np.int64) - oc[match][~same][:, :7]).sum(0)
-    assert same.mean() >= 0.97, f"{what}: counters equal on {same.mean():.4f}; diff {diff}"
-    r_g, r_o = oracle.recall(gi, gt, K), oracle.recall(oi, gt, K)
-    assert abs(r_g - r_o) <= 0.002, f"{what}: recall {r_g} vs oracle {r_o}"
+_gpu_search = parity_util.gpu_search
+_compare = parity_util.compare
 
 
 def test_bruteforce_knn_matches_oracle(cfg1):
