@@ -51,8 +51,15 @@ enum {
     FINGER_MODE_FINGER = 1,     /* Algorithm 4 with Algorithm 3 as the gate */
     FINGER_MODE_FINGER_LP = 2,  /* Algorithm 4 on BF16 rows and FP8-e4m3 residual codes,
                                    FP32 accumulation, final top-K re-ranked in FP32 */
-    FINGER_MODE_FINGER_MLP = 3  /* Algorithm 4 with a learned angle predictor in place of
+    FINGER_MODE_FINGER_MLP = 3, /* Algorithm 4 with a learned angle predictor in place of
                                    distribution matching; matching is the fallback */
+    FINGER_MODE_FINGER_F16 = 4  /* Algorithm 4 with the per-edge unit residual projections
+                                   (Supplementary G) stored as FP16 codes; FP32 vectors and
+                                   FP32 arithmetic.  Needs tables built with
+                                   FINGER_BUILD_HALF_CODES.  The whole code block of the
+                                   expanded node (deg0 rows, contiguous) is read together
+                                   with its adjacency row, so an expansion needs one
+                                   dependent round trip to memory fewer than in mode FINGER */
 };
 
 /* --------------------------------------------------------------- index */
@@ -153,11 +160,17 @@ typedef struct {
                                  FINGER_BUILD_NO_MATCHING: t = t_hat + eps
                                  (stored as mu = mu_hat = 0, sigma = sigma_hat
                                  = 1; eps = mean |Y - X|);
-                                 FINGER_BUILD_NO_EPS: eps = 0 */
+                                 FINGER_BUILD_NO_EPS: eps = 0;
+                                 and FINGER_BUILD_HALF_CODES (below) */
 } finger_build_params;
 
 #define FINGER_BUILD_NO_MATCHING 1
 #define FINGER_BUILD_NO_EPS 2
+/* also store every edge's unit residual projection P d_res / ||P d_res|| as
+ * FP16 codes (round to nearest even from FP32), rows of r rounded up to 8, 16,
+ * 32 or 64 halves, for FINGER_MODE_FINGER_F16.  Not an ablation: the matching
+ * statistics are those of the FP32 tables. */
+#define FINGER_BUILD_HALF_CODES 4
 
 /* Algorithm 2 and Supplementary G on the device.  For every node c with at
  * least two layer-0 neighbours a pair (d, d') is drawn with the counter rule

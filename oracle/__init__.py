@@ -62,10 +62,12 @@ def lib():
         L.orc_hnsw_build.argtypes = [P, i64, i32, i32, i32, P, P, i64, P, P, P, P]
         L.orc_hnsw_build.restype = i32
         L.orc_search.argtypes = [P, i64, i32, P, i32, P, P, i32, i32, i32, P, i64, i32, i32, P,
-                                 i32, P, i32, i32, P, P, P, i32, P, ctypes.c_double]
+                                 i32, P, i32, i32, P, P, P, i32, P, ctypes.c_double, i32]
         L.orc_search.restype = i32
         L.orc_sample_pairs.argtypes = [P, i64, i32, u64, i32, P]
-        L.orc_estimate.argtypes = [P, P, P, i32, P, i32, P]
+        L.orc_estimate.argtypes = [P, P, P, i32, P, i32, P, i32]
+        L.orc_half_round.argtypes = [ctypes.c_double]
+        L.orc_half_round.restype = ctypes.c_double
         L.orc_estimate.restype = ctypes.c_double
         L.orc_estimate_mlp.argtypes = [P, P, P, i32, P, i32, P, P, ctypes.c_double, P, P]
         L.orc_estimate_mlp.restype = ctypes.c_double
@@ -189,6 +191,7 @@ class FingerParams:
     sigma_hat: float
     eps: float
     corr: float = float("nan")      # Pearson correlation of X and Y over S (Supp. E)
+    codes: int = 0                  # 16: the per-edge unit P d_res stored as binary16 codes
 
     def stats(self):
         return np.array([self.mu, self.sigma, self.mu_hat, self.sigma_hat, self.eps], np.float64)
@@ -211,10 +214,10 @@ def search(g: Graph, X, Q, K: int, ef: int, finger: FingerParams | None = None, 
     cnt = np.empty((nq, 8), dtype=np.int64)
     if finger is None:
         P = np.zeros((1, m), np.float64)
-        r, st, fl = 1, np.zeros(5, np.float64), 0
+        r, st, fl, codes = 1, np.zeros(5, np.float64), 0, 0
     else:
         P = _f64(finger.P)
-        r, st, fl = P.shape[0], finger.stats(), 1
+        r, st, fl, codes = P.shape[0], finger.stats(), 1, int(finger.codes)
     adj0 = np.ascontiguousarray(g.adj0, dtype=np.int32)
     up_adj = np.ascontiguousarray(g.up_adj if len(g.up_adj) else np.full((1, g.M), -1, np.int32),
                                   dtype=np.int32)
@@ -223,7 +226,7 @@ def search(g: Graph, X, Q, K: int, ef: int, finger: FingerParams | None = None, 
     rc = lib().orc_search(_p(X), n, m, _p(adj0), adj0.shape[1], _p(up_off), _p(up_adj), g.M,
                           g.entry, g.maxlevel, _p(Q), nq, K, ef, _p(P), r, _p(st), warmup, fl,
                           _p(ids), _p(d), _p(cnt), threads, _p(mw) if mw is not None else None,
-                          float(mlp_eps))
+                          float(mlp_eps), codes)
     if rc != 0:
         raise ValueError("orc_search rejected its arguments")
     return ids, d, cnt
@@ -234,7 +237,14 @@ def estimate(q, c, d, fp: FingerParams) -> float:
     projection onto centre c, the residual norms and the matched angle."""
     q, c, d, P = _f64(q), _f64(c), _f64(d), _f64(fp.P)
     st = fp.stats()
-    return float(lib().orc_estimate(_p(q), _p(c), _p(d), q.shape[0], _p(P), P.shape[0], _p(st)))
+    return float(lib().orc_estimate(_p(q), _p(c), _p(d), q.shape[0], _p(P), P.shape[0], _p(st),
+                                    int(fp.codes)))
+
+
+def half_round(x: float) -> float:
+    """The oracle's rounding of a code to the nearest binary16 value (ties to
+    even), as FINGER_F16 stores the per-edge unit residual projections."""
+    return float(lib().orc_half_round(float(x)))
 
 
 def estimate_mlp(q, c, d, fp: FingerParams, mlp_weights, mlp_eps: float = 0.0):

@@ -310,6 +310,21 @@ typedef struct {
     int expanded;
 } tent_t;
 
+/* round to the nearest IEEE binary16 value, ties to even, directly from FP64
+ * (11 significant bits; spacing 2^-24 below the smallest normal 2^-14; no
+ * overflow handling: the codes are components of unit vectors) */
+static double half_rne(double x) {
+    if (x == 0.0 || !isfinite(x)) return x;
+    int e;
+    frexp(fabs(x), &e);              /* |x| in [2^(e-1), 2^e) */
+    int q = e - 11;                  /* spacing of binary16 values there */
+    if (q < -24) q = -24;
+    const double sp = ldexp(1.0, q);
+    return nearbyint(x / sp) * sp;   /* the default rounding mode: ties to even */
+}
+
+double orc_half_round(double x) { return half_rne(x); }
+
 /* round to the nearest bfloat16 (ties to even) through FP32 */
 static double bf16r(double x) {
     float f = (float)x;
@@ -354,7 +369,7 @@ static double appx_dist(const double* xc, const double* xd, int m, double cc, co
                         const double* q_res, double qres_n2, const double* Pq, const double* P,
                         int r, const double* st, double* d_proj, double* d_res, double* diff,
                         double* Pd, const double* q, const double* mlp, double mlp_eps,
-                        double* f_out, double* y_out) {
+                        double* f_out, double* y_out, int codes) {
     double mu = st[0], sigma = st[1], muh = st[2], sigmah = st[3], eps = st[4];
     double ratio = sigmah > 0 ? sigma / sigmah : 0.0;
     double b = cc > 0 ? dot(xc, xd, m) / cc : 0.0;
@@ -367,6 +382,12 @@ static double appx_dist(const double* xc, const double* xd, int m, double cc, co
     for (int k = 0; k < r; ++k) Pd[k] = dot(P + (size_t)k * m, d_res, m);
     double nq_ = sqrt(dot(Pq, Pq, r)), nd_ = sqrt(dot(Pd, Pd, r));
     double that = (nq_ > 0 && nd_ > 0) ? dot(Pq, Pd, r) / (nq_ * nd_) : 0.0;
+    if (codes == 16 && nq_ > 0 && nd_ > 0) {
+        /* the stored code of the edge is its unit P d_res rounded to binary16;
+         * t_hat is its dot with the unit P q_res */
+        that = 0.0;
+        for (int k = 0; k < r; ++k) that += (Pq[k] / nq_) * half_rne(Pd[k] / nd_);
+    }
     double t = (that - muh) * ratio + mu;
     t = t + eps;
     if (mlp) {
@@ -406,7 +427,7 @@ static double centre_parts(const double* xc, const double* q, int m, const doubl
 
 /* Algorithm 3 on one (q, c, d) triple, exposed for tests. */
 double orc_estimate(const double* q, const double* xc, const double* xd, int m, const double* P,
-                    int r, const double* stats) {
+                    int r, const double* stats, int codes) {
     double* w = (double*)malloc(sizeof(double) * (size_t)(6 * m + 2 * r + 2));
     double* q_proj = w;
     double* q_res = w + m;
@@ -418,7 +439,7 @@ double orc_estimate(const double* q, const double* xc, const double* xd, int m, 
     double qres_n2;
     double cc = centre_parts(xc, q, m, P, r, q_proj, q_res, &qres_n2, Pq);
     double e = appx_dist(xc, xd, m, cc, q_proj, q_res, qres_n2, Pq, P, r, stats, d_proj, d_res,
-                         diff, Pd, q, NULL, 0.0, NULL, NULL);
+                         diff, Pd, q, NULL, 0.0, NULL, NULL, codes);
     free(w);
     return e;
 }
@@ -440,7 +461,7 @@ double orc_estimate_mlp(const double* q, const double* xc, const double* xd, int
     double qres_n2;
     double cc = centre_parts(xc, q, m, P, r, q_proj, q_res, &qres_n2, Pq);
     double e = appx_dist(xc, xd, m, cc, q_proj, q_res, qres_n2, Pq, P, r, stats, d_proj, d_res,
-                         diff, Pd, q, mlp, mlp_eps, f_out, y_out);
+                         diff, Pd, q, mlp, mlp_eps, f_out, y_out, 0);
     free(w);
     return e;
 }
@@ -452,7 +473,7 @@ static void search_one(const double* X, int m, const int32_t* adj0, int deg0, co
                        int K, int ef, const double* P, int r, const double* st, int warmup,
                        int finger, int64_t* out_ids, double* out_d, int64_t* cnt, char* visited,
                        int32_t* touched, tent_t* T, double* work, const double* mlp,
-                       double mlp_eps) {
+                       double mlp_eps, int codes) {
     for (int i = 0; i < CNT_N; ++i) cnt[i] = 0;
     /* ---- upper layers: greedy descent (search-layer with ef = 1) */
     int32_t cur = entry;
@@ -520,7 +541,8 @@ static void search_one(const double* X, int m, const int32_t* adj0, int deg0, co
             int full = tlen == ef;
             if (use_est && full) {
                 double est = appx_dist(xc, xd, m, cc, q_proj, q_res, qres_n2, Pq, P, r, st,
-                                       d_proj, d_res, diff, Pd, q, mlp, mlp_eps, NULL, NULL);
+                                       d_proj, d_res, diff, Pd, q, mlp, mlp_eps, NULL, NULL,
+                                       codes);
                 cnt[CNT_ESTIMATES]++;
                 double ub = T[tlen - 1].kv.d;
                 if (est > ub) {
@@ -555,7 +577,7 @@ int orc_search(const double* X, int64_t n, int m, const int32_t* adj0, int deg0,
                const int64_t* up_off, const int32_t* up_adj, int Mup, int entry, int maxlevel,
                const double* Q, int64_t nq, int K, int ef, const double* P, int r,
                const double* stats, int warmup, int finger, int64_t* ids, double* dists,
-               int64_t* counters, int nthreads, const double* mlp, double mlp_eps) {
+               int64_t* counters, int nthreads, const double* mlp, double mlp_eps, int codes) {
     if (ef < 1 || K < 1) return -1;
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
@@ -574,7 +596,7 @@ int orc_search(const double* X, int64_t n, int m, const int32_t* adj0, int deg0,
             search_one(X, m, adj0, deg0, up_off, up_adj, Mup, entry, maxlevel, Q + (size_t)qi * m,
                        K, ef, P, r, stats, warmup, finger, ids + qi * K, dists + qi * K,
                        counters ? counters + qi * CNT_N : cnt_local, visited, touched, T, work,
-                       mlp, mlp_eps);
+                       mlp, mlp_eps, codes);
         }
         free(visited);
         free(touched);

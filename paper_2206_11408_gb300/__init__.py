@@ -18,9 +18,10 @@ import numpy as np
 from . import _build
 
 __all__ = ["Index", "lib", "MODE_PLAIN", "MODE_FINGER", "MODE_FINGER_LP", "MODE_FINGER_MLP",
+           "MODE_FINGER_F16",
            "FingerError", "COUNTER_NAMES", "table_bytes"]
 
-MODE_PLAIN, MODE_FINGER, MODE_FINGER_LP, MODE_FINGER_MLP = 0, 1, 2, 3
+MODE_PLAIN, MODE_FINGER, MODE_FINGER_LP, MODE_FINGER_MLP, MODE_FINGER_F16 = 0, 1, 2, 3, 4
 COUNTER_NAMES = ("expansions", "examined", "estimates", "skipped", "exact", "admitted", "upper",
                  "gathered")
 STATUS = {0: "ok", 1: "invalid argument", 2: "i/o error", 3: "bad index file format",
@@ -47,7 +48,7 @@ class BuildParams(ctypes.Structure):
                 ("basis_host", ctypes.c_void_p), ("stats_host", ctypes.c_void_p),
                 ("build_lp", ctypes.c_int), ("flags", ctypes.c_int)]
 
-BUILD_NO_MATCHING, BUILD_NO_EPS = 1, 2
+BUILD_NO_MATCHING, BUILD_NO_EPS, BUILD_HALF_CODES = 1, 2, 4
 
 
 class TrainParams(ctypes.Structure):
@@ -269,11 +270,12 @@ class Index:
     # ------------------------------------------------------------- tables
     def build_tables(self, r: int, seed: int, samples_per_node: int = 1, basis=None, stats=None,
                      build_lp: bool = False, matching: bool = True, use_eps: bool = True,
-                     stream=None):
+                     half_codes: bool = False, stream=None):
         """finger_build_tables.  ``basis`` (r x m) replaces the SVD basis (e.g.
         a random Gaussian matrix: the RPLSH comparison of Sec. 4.3); ``matching``
         and ``use_eps`` False are the ablations of FINGER_BUILD_NO_MATCHING and
-        FINGER_BUILD_NO_EPS."""
+        FINGER_BUILD_NO_EPS; ``half_codes`` also stores the FP16 codes of
+        MODE_FINGER_F16 (FINGER_BUILD_HALF_CODES)."""
         keep = []
         bp = None
         sp = None
@@ -285,16 +287,19 @@ class Index:
             s = np.ascontiguousarray(stats, dtype=np.float64)
             keep.append(s)
             sp = _np_ptr(s)
-        flags = (0 if matching else BUILD_NO_MATCHING) | (0 if use_eps else BUILD_NO_EPS)
+        flags = ((0 if matching else BUILD_NO_MATCHING) | (0 if use_eps else BUILD_NO_EPS) |
+                 (BUILD_HALF_CODES if half_codes else 0))
         p = BuildParams(r, seed, samples_per_node, bp, sp, int(build_lp), flags)
         _check(self._lib.finger_build_tables(self._h, ctypes.byref(p), _stream_ptr(stream)),
                "finger_build_tables")
 
     def select_rank(self, seed: int, threshold: float = 0.7, r_step: int = 8, r_max: int = 64,
-                    samples_per_node: int = 1, build_lp: bool = False, stream=None):
+                    samples_per_node: int = 1, build_lp: bool = False, half_codes: bool = False,
+                    stream=None):
         """finger_select_rank: rank rule of Supplementary E, then the tables at
         that rank.  Returns (r, [correlation of each candidate tried])."""
-        p = BuildParams(0, seed, samples_per_node, None, None, int(build_lp), 0)
+        p = BuildParams(0, seed, samples_per_node, None, None, int(build_lp),
+                        BUILD_HALF_CODES if half_codes else 0)
         r_out = ctypes.c_int()
         trace = np.full(-(-r_max // r_step), np.nan)
         _check(self._lib.finger_select_rank(self._h, ctypes.byref(p), ctypes.c_double(threshold),

@@ -19,8 +19,13 @@ cudaError_t occupancy_mode0(const SearchPlan&, int*);
 cudaError_t occupancy_mode1(const SearchPlan&, int*);
 cudaError_t occupancy_mode2(const SearchPlan&, int*);
 cudaError_t occupancy_mode3(const SearchPlan&, int*);
-cudaError_t launch_mode4(const DevIndex&, const SearchArgs&, const SearchPlan&, cudaStream_t);
-cudaError_t occupancy_mode4(const SearchPlan&, int*);
+cudaError_t launch_f16_k2(const DevIndex&, const SearchArgs&, const SearchPlan&, cudaStream_t);
+cudaError_t launch_f16_k4(const DevIndex&, const SearchArgs&, const SearchPlan&, cudaStream_t);
+cudaError_t occupancy_f16_k2(const SearchPlan&, int*);
+cudaError_t occupancy_f16_k4(const SearchPlan&, int*);
+cudaError_t launch_mode_harvest(const DevIndex&, const SearchArgs&, const SearchPlan&,
+                                cudaStream_t);
+cudaError_t occupancy_mode_harvest(const SearchPlan&, int*);
 
 void choose_groups(int nchunks, int* G, int* VPL) {
     if (nchunks <= 8) {
@@ -40,12 +45,21 @@ void choose_groups(int nchunks, int* G, int* VPL) {
     }
 }
 
+// length (floats) of the unit query-residual projection u_q in shared memory:
+// the FP16-code mode reads it in chunks of 8 per code chunk, zero padded
+int search_uq_len(const DevIndex& ix, int mode) {
+    const int r_pad = ix.r4 * 4;
+    return mode == FINGER_MODE_FINGER_F16 ? std::max(r_pad, 16 * ix.hks) : r_pad;
+}
+
 int search_smem_per_warp(const DevIndex& ix, int mode, int ef_cap, int H, int NPL, int h16) {
     const int r_pad = ix.r4 * 4;
+    const int uq_len = search_uq_len(ix, mode);
     const int qs_len = mode == FINGER_MODE_FINGER_LP ? ix.m8 * 8 : ix.m4 * 4;
     const int qs_bytes = mode == FINGER_MODE_FINGER_LP ? 4 * ((qs_len + 3) & ~3) : 0;
     const int tile = mode == FINGER_MODE_FINGER_MLP ? 2 * 16 * (ix.mlp_kp + MLP_PAD) : 0;
-    int b = 8 * ef_cap + (h16 ? 2 : 4) * H + 8 * r_pad + qs_bytes + 32 * 32 * NPL + 32 + tile;
+    int b = 8 * ef_cap + (h16 ? 2 : 4) * H + 4 * (uq_len + r_pad) + qs_bytes + 32 * 32 * NPL +
+            32 + tile;
     return (b + 15) & ~15;
 }
 
@@ -56,18 +70,20 @@ cudaError_t launch_search(const DevIndex& ix, const SearchArgs& a, const SearchP
         case 1: return launch_mode1(ix, a, p, s);
         case 2: return launch_mode2(ix, a, p, s);
         case 3: return launch_mode3(ix, a, p, s);
-        case MODE_HARVEST: return launch_mode4(ix, a, p, s);
+        case 4: return ix.hks == 2 ? launch_f16_k2(ix, a, p, s) : launch_f16_k4(ix, a, p, s);
+        case MODE_HARVEST: return launch_mode_harvest(ix, a, p, s);
     }
     return cudaErrorInvalidValue;
 }
 
-cudaError_t search_occupancy(const DevIndex&, const SearchPlan& p, int* bps) {
+cudaError_t search_occupancy(const DevIndex& ix, const SearchPlan& p, int* bps) {
     switch (p.mode) {
         case 0: return occupancy_mode0(p, bps);
         case 1: return occupancy_mode1(p, bps);
         case 2: return occupancy_mode2(p, bps);
         case 3: return occupancy_mode3(p, bps);
-        case MODE_HARVEST: return occupancy_mode4(p, bps);
+        case 4: return ix.hks == 2 ? occupancy_f16_k2(p, bps) : occupancy_f16_k4(p, bps);
+        case MODE_HARVEST: return occupancy_mode_harvest(p, bps);
     }
     return cudaErrorInvalidValue;
 }
@@ -108,6 +124,8 @@ fg::DevIndex make_dev(const finger_index* ix) {
     d.Xh = reinterpret_cast<const uint4*>(ix->Xh);
     d.edge_q = reinterpret_cast<const uint4*>(ix->edge_q);
     d.code_inv = 1.0f / ix->code_scale;
+    d.edge_h = reinterpret_cast<const uint4*>(ix->edge_h);
+    d.hks = ix->hks;
     d.W1f = ix->W1f;
     d.W2f = ix->W2f;
     d.w3 = ix->w3;
@@ -234,6 +252,7 @@ finger_status check_mode_ready(const finger_index* ix, int mode) {
     if (!ix->adj0) return FINGER_ERR_NOT_BUILT;
     if (mode != FINGER_MODE_PLAIN && !ix->edge_u) return FINGER_ERR_NOT_BUILT;
     if (mode == FINGER_MODE_FINGER_LP && !ix->edge_q) return FINGER_ERR_NOT_BUILT;
+    if (mode == FINGER_MODE_FINGER_F16 && !ix->edge_h) return FINGER_ERR_NOT_BUILT;
     if (mode == FINGER_MODE_FINGER_MLP && !ix->has_mlp) return FINGER_ERR_NOT_BUILT;
     return FINGER_OK;
 }
@@ -384,14 +403,15 @@ void finger_index_free(finger_index* ix) {
                     ix->edge_u, ix->edge_s, ix->Xh, ix->edge_q, ix->W1f, ix->W2f, ix->w3,
                     ix->b1, ix->b2, ix->work, ix->err, ix->cnt, ix->bitmap, ix->spill,
                     ix->stage_q, ix->stage_ids, ix->stage_d, ix->eig_G, ix->eig_V, ix->xs_hi,
-                    ix->xs_lo};
+                    ix->xs_lo, ix->edge_h};
     for (void* p : ptrs) cudaFree(p);
     delete ix;
 }
 
 static void drop_tables(finger_index* ix) {
     void* ptrs[] = {ix->P, ix->Pc, ix->edge_u, ix->edge_s, ix->Xh, ix->edge_q,
-                    ix->W1f, ix->W2f, ix->w3, ix->b1, ix->b2, ix->eig_G, ix->eig_V};
+                    ix->W1f, ix->W2f, ix->w3, ix->b1, ix->b2, ix->eig_G, ix->eig_V,
+                    ix->edge_h};
     for (void* p : ptrs) cudaFree(p);
     ix->eig_G = ix->eig_V = nullptr;
     ix->corr = 0.0 / 0.0;
@@ -399,6 +419,8 @@ static void drop_tables(finger_index* ix) {
     ix->edge_s = nullptr;
     ix->Xh = nullptr;
     ix->edge_q = nullptr;
+    ix->edge_h = nullptr;
+    ix->hks = 0;
     ix->W1f = ix->W2f = nullptr;
     ix->w3 = ix->b1 = ix->b2 = nullptr;
     ix->r = ix->r_pad = ix->r16 = 0;
@@ -518,6 +540,7 @@ finger_status finger_get_info(const finger_index* ix, finger_info* out) {
     if (ix->adj0) b += ix->n * ix->deg0 * 4 + ix->n * 8 + ix->up_rows * ix->M * 4;
     if (ix->edge_u) b += ix->n * ix->r_pad * 4 + finger_table_bytes(ix->n, ix->deg0, ix->r_pad, 0);
     if (ix->edge_q) b += finger_table_bytes(ix->n, ix->deg0, ix->r, 1) + ix->n * ix->m8 * 16;
+    if (ix->edge_h) b += ix->n * (ix->deg0 > 32 ? 4 : 2) * ix->hks * 512;
     b += ix->bitmap_slots * ix->words * 4 + ix->bitmap_slots * ix->spill_cap * 4;
     out->device_bytes = b;
     return FINGER_OK;
@@ -569,7 +592,7 @@ finger_status finger_get_tables(const finger_index* ix, float* P, double* stats,
 }
 
 finger_status finger_set_mode(finger_index* ix, int mode, int warmup) {
-    if (!ix || mode < 0 || mode > 3) return FINGER_ERR_INVALID_ARG;
+    if (!ix || mode < 0 || mode > FINGER_MODE_FINGER_F16) return FINGER_ERR_INVALID_ARG;
     ix->mode = mode;
     if (warmup >= 0) ix->warmup = warmup;
     return FINGER_OK;

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_fp8.h>
 #include <stdint.h>
 
@@ -48,6 +49,10 @@ struct DevIndex {
     const uint4* Xh;        // n x m8 (BF16)
     const uint4* edge_q;    // (n*deg0) x r16 FP8-e4m3 codes of edge_u * code_scale
     float code_inv;         // 1 / code_scale
+    // FP16 unit residual codes (mode FINGER_F16) in m16n8k16 A-fragment order:
+    // per node 2 NPL tiles of 16 slots x hks k steps x 32 lanes x 16 bytes
+    const uint4* edge_h;
+    int hks;                // k steps of 16 codes: 2 (r <= 32) or 4 (r <= 64)
     // learned predictor: BF16 W1 (H x kp, zero padded beyond r+4) and W2 (H x H)
     // stored fragment-major for m16n8k16 B operands (uint2 per lane per
     // (n8 tile, k16 step)), w3 (H, BF16-valued FP32), FP32 biases
@@ -91,7 +96,10 @@ struct SearchArgs {
     int64_t hv_cap;
 };
 
-constexpr int MODE_HARVEST = 4;     // FINGER traversal that records predictor training data
+constexpr int MODE_HARVEST = 5;     // FINGER traversal that records predictor training data
+// kernel instances of the public mode FINGER_F16 by k steps of the code table
+constexpr int MODE_F16_K2 = 6;      // r <= 32
+constexpr int MODE_F16_K4 = 7;      // r <= 64
 
 struct SearchPlan {
     int mode;
@@ -171,6 +179,9 @@ struct finger_index {
     __nv_bfloat16* Xh = nullptr;
     uint8_t* edge_q = nullptr;
     int r16 = 0;
+    // FP16 codes (fragment order, see DevIndex)
+    uint16_t* edge_h = nullptr;
+    int hks = 0;
     float code_scale = 256.0f;
     // learned predictor
     int has_mlp = 0;

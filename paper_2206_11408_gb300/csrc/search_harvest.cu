@@ -2,11 +2,11 @@
 #include "search_impl.cuh"
 
 namespace fg {
-cudaError_t launch_mode4(const DevIndex& ix, const SearchArgs& a, const SearchPlan& p,
-                         cudaStream_t s) {
+cudaError_t launch_mode_harvest(const DevIndex& ix, const SearchArgs& a, const SearchPlan& p,
+                                cudaStream_t s) {
     return launch_mode<MODE_HARVEST>(ix, a, p, s);
 }
-cudaError_t occupancy_mode4(const SearchPlan& p, int* blocks) {
+cudaError_t occupancy_mode_harvest(const SearchPlan& p, int* blocks) {
     return occupancy_mode<MODE_HARVEST>(p, blocks);
 }
 }  // namespace fg

@@ -378,6 +378,90 @@ __device__ __forceinline__ float edge_cos(const DevIndex& ix, size_t e, const fl
     return acc;
 }
 
+// ---- FP16 codes (mode FINGER_F16).  The estimates of one expansion are the
+// matrix-vector product t_hat = A u_q of the centre's code rows A (rows =
+// slots, FP16) with the unit residual projection of the query u_q, run on the
+// tensor cores as m16n8k16 MMAs with FP32 accumulation.  The table holds A in
+// the MMA's A-fragment order: for centre c, tile T (slots 16T .. 16T+15, NT =
+// 32 NPL slots per node, zero rows beyond deg0) and k step ks (codes 16ks ..
+// 16ks+15, KS = 2 or 4 steps), 32 lanes x 16 bytes, lane l = 4g + t holding
+// rows 16T+g and 16T+g+8 at codes 16ks+2t, +1, +8, +9.  A centre's block is
+// contiguous and its address depends on c alone, so it is requested in the
+// same round trip as c's adjacency row, one 16-byte load per lane per (tile,
+// k step), at most eight per round.  u_q is split into FP16 high and low parts
+// (hi = fp16(u), lo = fp16(u - hi)) for the even and odd columns of B, so
+// columns 2t and 2t+1 of the product sum to A u_q with u_q kept to about 22
+// bits; the codes are exact FP16 values.  KS and NT are compile-time, so the
+// whole product is straight-line code.
+__device__ __forceinline__ void mma_f16(float* d, const uint4& a, uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a.x), "r"(a.y), "r"(a.z), "r"(a.w), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ uint32_t pack_half2(float lo, float hi) {
+    __half2 v = __floats2half2_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&v);
+}
+
+// one round: tiles t0 .. t0 + TPR - 1 (TPR = min(NT, 8 / KS)) into hx[T KS + ks]
+template <int KS, int NT>
+__device__ __forceinline__ void wb_load(const DevIndex& ix, uint32_t c, int t0, uint4 (&hx)[8],
+                                        int lane) {
+    constexpr int TPR = NT * KS <= 8 ? NT : 8 / KS;
+    const uint4* base = ix.edge_h + ((size_t)c * NT + t0) * KS * 32 + lane;
+#pragma unroll
+    for (int T = 0; T < TPR; ++T)
+#pragma unroll
+        for (int ks = 0; ks < KS; ++ks) hx[T * KS + ks] = __ldg(base + (T * KS + ks) * 32);
+}
+
+// t_hat of rows 16(t0+T)+g (v[2(t0+T)]) and +8 (v[2(t0+T)+1]) for the round's
+// tiles.  k step outer: the B fragment of one step (lane 4g + t gives column g
+// at codes 16ks + 2t, +1 and +8, +9; even columns the high part, odd columns
+// the low part) serves every tile, and each code register dies at its MMA.
+template <int KS, int NT>
+__device__ __forceinline__ void wb_mma(const uint4 (&hx)[8], const float* uq, int t0,
+                                       float (&v)[8], int lane) {
+    constexpr int TPR = NT * KS <= 8 ? NT : 8 / KS;
+    const int g = lane >> 2, t = lane & 3;
+    const bool lo = g & 1;
+    float acc[TPR][4];
+#pragma unroll
+    for (int T = 0; T < TPR; ++T) acc[T][0] = acc[T][1] = acc[T][2] = acc[T][3] = 0.f;
+#pragma unroll
+    for (int ks = 0; ks < KS; ++ks) {
+        const float2 x01 = *reinterpret_cast<const float2*>(uq + 16 * ks + 2 * t);
+        const float2 x89 = *reinterpret_cast<const float2*>(uq + 16 * ks + 2 * t + 8);
+        const float2 h01 = __half22float2(__floats2half2_rn(x01.x, x01.y));
+        const float2 h89 = __half22float2(__floats2half2_rn(x89.x, x89.y));
+        const uint32_t b0 = lo ? pack_half2(x01.x - h01.x, x01.y - h01.y) : pack_half2(x01.x, x01.y);
+        const uint32_t b1 = lo ? pack_half2(x89.x - h89.x, x89.y - h89.y) : pack_half2(x89.x, x89.y);
+#pragma unroll
+        for (int T = 0; T < TPR; ++T) mma_f16(acc[T], hx[T * KS + ks], b0, b1);
+    }
+#pragma unroll
+    for (int T = 0; T < TPR; ++T) {
+        v[2 * (t0 + T)] = acc[T][0] + acc[T][1];
+        v[2 * (t0 + T) + 1] = acc[T][2] + acc[T][3];
+    }
+}
+
+// lane j of slot block s receives t_hat of row 32s + j: lane 4g + t offers
+// row 32s + 8t + g
+template <int NPL>
+__device__ __forceinline__ void wb_route(const float (&v)[8], float* th, int lane) {
+    const int t = lane & 3;
+    const int src = 4 * (lane & 7) + (lane >> 3);
+#pragma unroll
+    for (int s = 0; s < NPL; ++s) {
+        const float e = t == 0 ? v[4 * s] : t == 1 ? v[4 * s + 1] : t == 2 ? v[4 * s + 2] : v[4 * s + 3];
+        th[s] = __shfl_sync(FULLMASK, e, src);
+    }
+}
+
 // Features of one (q, c, d) triple for the learned angle predictor (an
 // extension; the paper has no learned predictor): f = [u_q * u_d (r values),
 // t_hat, ||q_res|| / ||q||, ||d_res|| / ||d||, a / (|a| + |b| + 1e-6)], with
@@ -529,6 +613,10 @@ __global__ void __launch_bounds__(128, OCC) k_search(DevIndex ix, SearchArgs a) 
     constexpr bool EST = MODE != FINGER_MODE_PLAIN;
     constexpr bool MLP = MODE == FINGER_MODE_FINGER_MLP;
     constexpr bool HARV = MODE == MODE_HARVEST;
+    // FP16 codes, product on the tensor cores (public mode FINGER_F16), k steps
+    constexpr bool WB = MODE == MODE_F16_K2 || MODE == MODE_F16_K4;
+    constexpr int WKS = MODE == MODE_F16_K2 ? 2 : 4;
+    constexpr int WNT = 2 * NPL;                            // tiles per node
     extern __shared__ __align__(16) unsigned char sm[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
@@ -544,7 +632,8 @@ __global__ void __launch_bounds__(128, OCC) k_search(DevIndex ix, SearchArgs a) 
     uint32_t* hash = Ti + a.ef_cap;
     const int hwords = a.h16 ? a.H >> 1 : a.H;   // 32-bit words of the visited hash
     float* uq = reinterpret_cast<float*>(hash + hwords);
-    float* pq = uq + r_pad;
+    const int uq_len = WB ? max(r_pad, 16 * WKS) : r_pad;   // FP16 codes: zero padded
+    float* pq = uq + uq_len;
     // the query staging buffer is only read before the visited hash is cleared,
     // so outside the LP mode (which re-reads it for the FP32 re-rank) it lives
     // inside the hash region (the plan keeps its words >= m_pad)
@@ -600,6 +689,8 @@ __global__ void __launch_bounds__(128, OCC) k_search(DevIndex ix, SearchArgs a) 
             }
             __syncwarp();
         }
+        if constexpr (WB)
+            for (int i = r_pad + lane; i < uq_len; i += 32) uq[i] = 0.f;
         int c_exp = 0, c_exa = 0, c_est = 0, c_skip = 0, c_exact = 0, c_adm = 0, c_up = 0,
             c_gath = 0;
         bool fail = false;
@@ -699,10 +790,47 @@ __global__ void __launch_bounds__(128, OCC) k_search(DevIndex ix, SearchArgs a) 
                 if (lane < r_pad) pc0 = __ldg(pcr + lane);
                 if (lane + 32 < r_pad) pc1 = __ldg(pcr + lane + 32);
             }
+            // FP16 codes: c's code block and edge scalars, requested in the same
+            // round trip as the adjacency row
+            uint4 hx[8];
+            float2 scw[NPL];
+            float th[NPL];
+            float wac = 0.f, wqres2 = 0.f;   // a and ||q_res||^2 of this centre
+            if constexpr (WB) {
+                if (use_est) {
+#pragma unroll
+                    for (int s = 0; s < NPL; ++s) {
+                        const int j = s * 32 + lane;
+                        scw[s] = j < ix.deg0 ? __ldg(ix.edge_s + (size_t)c * ix.deg0 + j)
+                                             : make_float2(0.f, 0.f);
+                    }
+                    wb_load<WKS, WNT>(ix, c, 0, hx, lane);
+                    // per-centre prep (Sec. 3.2 identity for q^T c, Supplementary G),
+                    // then the product: the codes arrive with the adjacency row
+                    // and are consumed before the visited test
+                    const float qc = 0.5f * (qn2 + cc - dc);
+                    wac = cc > 0.f ? qc / cc : 0.f;
+                    wqres2 = fmaxf(qn2 - wac * qc, 0.f);
+                    const float u0 = lane < r_pad ? pq[lane] - wac * pc0 : 0.f;
+                    const float u1 = lane + 32 < r_pad ? pq[lane + 32] - wac * pc1 : 0.f;
+                    const float nrm = warp_sum(u0 * u0 + u1 * u1);
+                    const float inv = nrm > 0.f ? rsqrtf(nrm) : 0.f;
+                    if (lane < r_pad) uq[lane] = u0 * inv;
+                    if (lane + 32 < r_pad) uq[lane + 32] = u1 * inv;
+                    __syncwarp();
+                    float v[8];
+                    wb_mma<WKS, WNT>(hx, uq, 0, v, lane);
+                    if constexpr (WNT * WKS > 8) {   // second round: tiles 2, 3
+                        wb_load<WKS, WNT>(ix, c, 2, hx, lane);
+                        wb_mma<WKS, WNT>(hx, uq, 2, v, lane);
+                    }
+                    wb_route<NPL>(v, th, lane);
+                }
+            }
             // In FINGER mode a bitmap test-and-set is resolved only after the
             // neighbour's edge row has been requested, so the two round trips
             // overlap; a neighbour that turns out visited just drops its estimate.
-            constexpr bool DEFER = MODE == FINGER_MODE_FINGER;
+            constexpr bool DEFER = MODE == FINGER_MODE_FINGER || WB;
             bool isnew[NPL], pend[NPL];
             uint32_t pold[NPL];
 #pragma unroll
@@ -731,18 +859,24 @@ __global__ void __launch_bounds__(128, OCC) k_search(DevIndex ix, SearchArgs a) 
 
             // a4: per-centre prep (Sec. 3.2 identity for q^T c, Supplementary G)
             float ac = 0.f, qres2 = 0.f, qres_n = 0.f;
-            if (use_est) {
+            if (WB && use_est) {   // formed at the pop
+                ac = wac;
+                qres2 = wqres2;
+                qres_n = sqrtf(qres2);
+            } else if (use_est) {
                 const float qc = 0.5f * (qn2 + cc - dc);
                 ac = cc > 0.f ? qc / cc : 0.f;
                 qres2 = fmaxf(qn2 - ac * qc, 0.f);
                 qres_n = sqrtf(qres2);
-                const float u0 = lane < r_pad ? pq[lane] - ac * pc0 : 0.f;
-                const float u1 = lane + 32 < r_pad ? pq[lane + 32] - ac * pc1 : 0.f;
-                const float nrm = warp_sum(u0 * u0 + u1 * u1);
-                const float inv = nrm > 0.f ? rsqrtf(nrm) : 0.f;
-                if (lane < r_pad) uq[lane] = u0 * inv;
-                if (lane + 32 < r_pad) uq[lane + 32] = u1 * inv;
-                __syncwarp();
+                {
+                    const float u0 = lane < r_pad ? pq[lane] - ac * pc0 : 0.f;
+                    const float u1 = lane + 32 < r_pad ? pq[lane + 32] - ac * pc1 : 0.f;
+                    const float nrm = warp_sum(u0 * u0 + u1 * u1);
+                    const float inv = nrm > 0.f ? rsqrtf(nrm) : 0.f;
+                    if (lane < r_pad) uq[lane] = u0 * inv;
+                    if (lane + 32 < r_pad) uq[lane + 32] = u1 * inv;
+                    __syncwarp();
+                }
             }
 
             // a5: estimates of the new neighbours against ub at expansion start
@@ -911,10 +1045,12 @@ __global__ void __launch_bounds__(128, OCC) k_search(DevIndex ix, SearchArgs a) 
                 float est = -INFINITY;
                 if (use_est && isnew[s]) {
                     const size_t e = (size_t)c * ix.deg0 + s * 32 + lane;
-                    const float2 sc = BAL ? scv[s] : __ldg(ix.edge_s + e);
+                    const float2 sc = BAL ? scv[s] : WB ? scw[s] : __ldg(ix.edge_s + e);
                     float t;
                     if constexpr (BAL) {
                         t = fmaf(xb[s * 32 + lane], ix.alpha, ix.beta);
+                    } else if constexpr (WB) {
+                        t = fmaf(th[s], ix.alpha, ix.beta);
                     } else if constexpr (MLP) {
                         // learned predictor in place of distribution matching;
                         // the matched cosine is the fallback for a non-finite output
@@ -1263,7 +1399,7 @@ cudaError_t launch_mode(const DevIndex& ix, const SearchArgs& a, const SearchPla
     if constexpr (MODE == FINGER_MODE_PLAIN)
         if (p.occ == 8) return launch_occ<MODE, 8>(ix, a, p, s);
     if constexpr (MODE == FINGER_MODE_PLAIN || MODE == FINGER_MODE_FINGER ||
-                  MODE == FINGER_MODE_FINGER_LP)
+                  MODE == FINGER_MODE_FINGER_LP || MODE == MODE_F16_K2 || MODE == MODE_F16_K4)
         if (p.occ == 6) return launch_occ<MODE, 6>(ix, a, p, s);
     if (p.occ != 5) return cudaErrorInvalidValue;
     return launch_occ<MODE, 5>(ix, a, p, s);
@@ -1276,7 +1412,7 @@ cudaError_t occupancy_mode(const SearchPlan& p, int* blocks) {
     if constexpr (MODE == FINGER_MODE_PLAIN)
         if (p.occ == 8) return occupancy_occ<MODE, 8>(p, blocks);
     if constexpr (MODE == FINGER_MODE_PLAIN || MODE == FINGER_MODE_FINGER ||
-                  MODE == FINGER_MODE_FINGER_LP)
+                  MODE == FINGER_MODE_FINGER_LP || MODE == MODE_F16_K2 || MODE == MODE_F16_K4)
         if (p.occ == 6) return occupancy_occ<MODE, 6>(p, blocks);
     if (p.occ != 5) {
         *blocks = 0;

@@ -599,6 +599,34 @@ __global__ void k_lp_codes(const float* edge_u, int64_t ne, int r_pad, int r16b,
     out[i] = (uint8_t)__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
 }
 
+// FP16 codes in m16n8k16 A-fragment order: thread i writes the 16 bytes of
+// lane l = i % 32 for (node c, tile T, k step ks) = i / 32, i.e. rows
+// 16T + g and 16T + g + 8 (g = l / 4) at codes 16ks + 2t, +1, +8, +9
+// (t = l % 4), each edge_u entry rounded to nearest even (0 beyond the node's
+// deg0 rows and beyond r_pad codes; padding slots hold 0 in edge_u already).
+__global__ void k_half_codes(const float* edge_u, int64_t n, int deg0, int r_pad, int tiles,
+                             int ks_n, uint4* out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n * tiles * ks_n * 32) return;
+    const int l = (int)(i & 31);
+    int64_t f = i >> 5;
+    const int ks = (int)(f % ks_n);
+    f /= ks_n;
+    const int T = (int)(f % tiles);
+    const int64_t c = f / tiles;
+    const int g = l >> 2, t = l & 3;
+    auto code = [&](int row, int k) -> float {
+        return row < deg0 && k < r_pad ? edge_u[((size_t)c * deg0 + row) * r_pad + k] : 0.f;
+    };
+    const int r0 = 16 * T + g, r1 = r0 + 8, k0 = 16 * ks + 2 * t, k1 = k0 + 8;
+    __half2 w[4];
+    w[0] = __floats2half2_rn(code(r0, k0), code(r0, k0 + 1));
+    w[1] = __floats2half2_rn(code(r1, k0), code(r1, k0 + 1));
+    w[2] = __floats2half2_rn(code(r0, k1), code(r0, k1 + 1));
+    w[3] = __floats2half2_rn(code(r1, k1), code(r1, k1 + 1));
+    out[i] = *reinterpret_cast<const uint4*>(w);
+}
+
 template <class T>
 T* dalloc(size_t count) {
     void* p = nullptr;
@@ -644,6 +672,29 @@ cudaError_t lp_rebuild(finger_index* ix) {
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     ix->r16 = r16b / 16;
+    return cudaDeviceSynchronize();
+}
+
+// FP16 unit residual codes from the FP32 tables (mode FINGER_F16), in the
+// tensor cores' A-fragment order: per node 2 tiles of 16 slots (4 when
+// deg0 > 32; rows beyond deg0 are zero) x 2 k steps of 16 codes (4 when
+// r > 32) x 512 bytes
+cudaError_t half_rebuild(finger_index* ix) {
+    using namespace fg;
+    cudaFree(ix->edge_h);
+    ix->edge_h = nullptr;
+    ix->hks = 0;
+    const int hks = ix->r > 32 ? 4 : 2;
+    const int tiles = ix->deg0 > 32 ? 4 : 2;
+    const int64_t units = ix->n * tiles * hks * 32;
+    cudaError_t e = cudaMalloc(&ix->edge_h, sizeof(uint4) * (size_t)units + 16);
+    if (e != cudaSuccess) return e;
+    k_half_codes<<<(unsigned)((units + 255) / 256), 256>>>(ix->edge_u, ix->n, ix->deg0,
+                                                          ix->r_pad, tiles, hks,
+                                                          reinterpret_cast<uint4*>(ix->edge_h));
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    ix->hks = hks;
     return cudaDeviceSynchronize();
 }
 
@@ -770,7 +821,8 @@ finger_status build_tables(finger_index* ix, const finger_build_params* p, cudaS
     if (!ix->adj0) return FINGER_ERR_NOT_BUILT;
     const int r = p->r;
     if (r < 1 || r > MAX_R || r > ix->m) return FINGER_ERR_INVALID_ARG;
-    if (p->flags & ~(FINGER_BUILD_NO_MATCHING | FINGER_BUILD_NO_EPS)) return FINGER_ERR_INVALID_ARG;
+    if (p->flags & ~(FINGER_BUILD_NO_MATCHING | FINGER_BUILD_NO_EPS | FINGER_BUILD_HALF_CODES))
+        return FINGER_ERR_INVALID_ARG;
     const int spn = p->samples_per_node > 0 ? p->samples_per_node : 1;
     const int64_t n = ix->n;
     const int m = ix->m, m_pad = ix->m_pad, m4 = ix->m4, deg0 = ix->deg0;
@@ -837,8 +889,11 @@ finger_status build_tables(finger_index* ix, const finger_build_params* p, cudaS
     // reduced-precision tables
     cudaFree(ix->Xh);
     cudaFree(ix->edge_q);
+    cudaFree(ix->edge_h);
     ix->Xh = nullptr;
     ix->edge_q = nullptr;
+    ix->edge_h = nullptr;
+    ix->hks = 0;
 done:
     cudaFree(pairs);
     cudaFree(evals);
@@ -866,6 +921,10 @@ done:
     for (int i = 0; i < 5; ++i) ix->stats[i] = st[i];
     ix->corr = corr;
     if (p->build_lp && lp_rebuild(ix) != cudaSuccess) {
+        cudaGetLastError();
+        return FINGER_ERR_CUDA;
+    }
+    if ((p->flags & FINGER_BUILD_HALF_CODES) && half_rebuild(ix) != cudaSuccess) {
         cudaGetLastError();
         return FINGER_ERR_CUDA;
     }

@@ -7,6 +7,10 @@ oracle on >= 99 % of queries, per-pair distances within 1e-5 relative of FP64,
 recall@10 within 0.002 of the oracle's at the same ef, traversal counters
 identical on >= 97 % of the queries whose lists match.
 """
+import dataclasses
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -31,7 +35,7 @@ def cfg1():
     gt, gd = oracle.bruteforce(X, Q, 10)
     ix = fg.Index(X)
     ix.set_graph(g.adj0, g.level, g.up_off, g.up_adj, g.entry, g.maxlevel, g.M)
-    ix.build_tables(16, 4001, basis=fp.P, stats=fp.stats())
+    ix.build_tables(16, 4001, basis=fp.P, stats=fp.stats(), half_codes=True)
     q = torch.from_numpy(Q).cuda()
     yield dict(X=X, Q=Q, g=g, fp=fp, pairs=pairs, gt=gt, gd=gd, ix=ix, q=q)
     ix.close()
@@ -39,6 +43,15 @@ def cfg1():
 
 _gpu_search = parity_util.gpu_search
 _compare = parity_util.compare
+
+
+def _f16(fp):
+    """The oracle's FINGER parameters with the per-edge codes stored as binary16."""
+    return dataclasses.replace(fp, codes=16)
+
+
+def _modes(fp):
+    return ((fg.MODE_PLAIN, None), (fg.MODE_FINGER, fp), (fg.MODE_FINGER_F16, _f16(fp)))
 
 
 def test_bruteforce_knn_matches_oracle(cfg1):
@@ -62,6 +75,45 @@ def test_finger_search_parity(cfg1, ef):
     oi, od, oc = oracle.search(cfg1["g"], cfg1["X"], cfg1["Q"], 10, ef, cfg1["fp"])
     _compare(gi, gd, gc, oi, od, oc, cfg1["gt"], 10, f"finger ef={ef}")
     assert gc[:, 3].sum() > 0          # the gate skipped neighbours
+
+
+@pytest.mark.parametrize("ef", [10, 20, 50, 100])
+def test_finger_f16_search_parity(cfg1, ef):
+    """FINGER with the codes stored as binary16 (whole code block read with the
+    adjacency row) against the oracle's Algorithm 4 on binary16 codes."""
+    gi, gd, gc = _gpu_search(cfg1["ix"], cfg1["q"], 10, ef, fg.MODE_FINGER_F16)
+    oi, od, oc = oracle.search(cfg1["g"], cfg1["X"], cfg1["Q"], 10, ef, _f16(cfg1["fp"]))
+    _compare(gi, gd, gc, oi, od, oc, cfg1["gt"], 10, f"finger-f16 ef={ef}")
+    assert gc[:, 3].sum() > 0
+
+
+def test_alg4_hand_trace_on_gpu():
+    """The hand-traced Algorithm 4 instance (tests/golden/alg4_hand_trace.json:
+    one estimate exactly equal to ub) through both FINGER modes of the kernel."""
+    t = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "alg4_hand_trace.json")))
+    names = sorted(t["ids"], key=t["ids"].get)
+    X = np.array([t["points"][k] for k in names], np.float32)
+    adj = np.full((len(names), 2), -1, np.int32)
+    for k in names:
+        row = [t["ids"][v] for v in t["adjacency"][k]]
+        adj[t["ids"][k], :len(row)] = row
+    st = t["stats"]
+    stats = [st["mu"], st["sigma"], st["mu_hat"], st["sigma_hat"], st["eps"]]
+    ix = fg.Index(X)
+    ix.set_graph(adj, np.zeros(len(names), np.int32), np.full(len(names), -1, np.int64),
+                 np.zeros((0, 1), np.int32), t["ids"][t["entry"]], 0, 1)
+    ix.build_tables(1, 1, basis=np.array(t["P"], np.float32), stats=stats, half_codes=True)
+    q = torch.tensor([t["query"]], dtype=torch.float32, device="cuda")
+    for mode in (fg.MODE_FINGER, fg.MODE_FINGER_F16):
+        for key, warmup in (("warmup1_strict", 1), ("warmup2_strict", 2)):
+            exp = t["expected"][key]
+            ids, d, c = _gpu_search(ix, q, t["K"], t["ef"], mode, warmup)
+            assert [names[i] for i in ids[0]] == exp["ids"], (mode, key)
+            assert d[0].tolist() == exp["dists"], (mode, key)
+            got = dict(zip(fg.COUNTER_NAMES, c[0].tolist()))
+            for k in ("expansions", "examined", "estimates", "skipped", "exact", "admitted"):
+                assert got[k] == exp[k], (mode, key, k, got[k], exp[k])
+    ix.close()
 
 
 def test_finger_without_skipping_equals_plain(cfg1):
@@ -163,9 +215,9 @@ def test_ragged_batch_and_odd_dimension():
     fp, _ = oracle.build_tables(X, g, 10, 5)
     ix = fg.Index(X)
     ix.set_graph(g.adj0, g.level, g.up_off, g.up_adj, g.entry, g.maxlevel, g.M)
-    ix.build_tables(10, 5, basis=fp.P, stats=fp.stats())
+    ix.build_tables(10, 5, basis=fp.P, stats=fp.stats(), half_codes=True)
     q = torch.from_numpy(Q).cuda()
-    for mode, f in ((fg.MODE_PLAIN, None), (fg.MODE_FINGER, fp)):
+    for mode, f in _modes(fp):
         gi, gd, gc = _gpu_search(ix, q, 7, 33, mode)
         oi, od, oc = oracle.search(g, X, Q, 7, 33, f)
         gt, _ = oracle.bruteforce(X, Q, 7)
@@ -181,10 +233,10 @@ def test_two_neighbour_slots_per_lane():
     fp, _ = oracle.build_tables(X, g, 16, 12)
     ix = fg.Index(X)
     ix.set_graph(g.adj0, g.level, g.up_off, g.up_adj, g.entry, g.maxlevel, g.M)
-    ix.build_tables(16, 12, basis=fp.P, stats=fp.stats())
+    ix.build_tables(16, 12, basis=fp.P, stats=fp.stats(), half_codes=True)
     q = torch.from_numpy(Q).cuda()
     gt, _ = oracle.bruteforce(X, Q, 10)
-    for mode, f in ((fg.MODE_PLAIN, None), (fg.MODE_FINGER, fp)):
+    for mode, f in _modes(fp):
         gi, gd, gc = _gpu_search(ix, q, 10, 64, mode)
         oi, od, oc = oracle.search(g, X, Q, 10, 64, f)
         _compare(gi, gd, gc, oi, od, oc, gt, 10, f"deg0=48 mode={mode}")
@@ -201,14 +253,35 @@ def test_wide_rows_k1_and_ef_equal_k():
     fp, _ = oracle.build_tables(X, g, 32, 22)
     ix = fg.Index(X)
     ix.set_graph(g.adj0, g.level, g.up_off, g.up_adj, g.entry, g.maxlevel, g.M)
-    ix.build_tables(32, 22, basis=fp.P, stats=fp.stats())
+    ix.build_tables(32, 22, basis=fp.P, stats=fp.stats(), half_codes=True)
     q = torch.from_numpy(Q).cuda()
     for K, ef in ((1, 1), (1, 16), (10, 10), (10, 48)):
         gt, _ = oracle.bruteforce(X, Q, K)
-        for mode, f in ((fg.MODE_PLAIN, None), (fg.MODE_FINGER, fp)):
+        for mode, f in _modes(fp):
             gi, gd, gc = _gpu_search(ix, q, K, ef, mode)
             oi, od, oc = oracle.search(g, X, Q, K, ef, f)
             _compare(gi, gd, gc, oi, od, oc, gt, K, f"m=300 K={K} ef={ef} mode={mode}")
+    ix.close()
+
+
+def test_wide_codes_two_row_groups():
+    """deg0 = 64 (M = 32) with r = 64: the FP16 code block of a centre is 16
+    loads per lane, taken as two row groups of eight (the second once the
+    first is consumed)."""
+    X = workloads.base_vectors(2, 3000)
+    Q = workloads.query_vectors(2, 100)
+    g = oracle.hnsw_build(X, 32, 100, 41)
+    fp, _ = oracle.build_tables(X, g, 64, 42)
+    ix = fg.Index(X)
+    ix.set_graph(g.adj0, g.level, g.up_off, g.up_adj, g.entry, g.maxlevel, g.M)
+    ix.build_tables(64, 42, basis=fp.P, stats=fp.stats(), half_codes=True)
+    assert ix.info()["deg0"] == 64
+    q = torch.from_numpy(Q).cuda()
+    gt, _ = oracle.bruteforce(X, Q, 10)
+    for mode, f in _modes(fp)[1:]:
+        gi, gd, gc = _gpu_search(ix, q, 10, 80, mode)
+        oi, od, oc = oracle.search(g, X, Q, 10, 80, f)
+        _compare(gi, gd, gc, oi, od, oc, gt, 10, f"deg0=64 r=64 mode={mode}")
     ix.close()
 
 

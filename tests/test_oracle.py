@@ -79,6 +79,35 @@ def test_estimate_hand_example():
     assert oracle.estimate(q, c, d, _stats(P=np.array([[0, 0, 1.0]]), **st)) == pytest.approx(3.0, abs=1e-14)
 
 
+def test_half_codes_round_to_nearest_even_from_fp64():
+    """The binary16 rounding of the stored codes: IEEE round to nearest, ties to
+    even, in one step from FP64 (numpy's float64 -> float16 conversion)."""
+    cases = {1 + 2 ** -11: 1.0,                       # tie -> even
+             1 + 2 ** -11 + 2 ** -40: 1 + 2 ** -10,   # just above the tie (FP32 first would tie)
+             1 + 3 * 2 ** -11: 1 + 2 ** -9,           # tie -> even
+             0.6: 1229 * 2 ** -11, 0.8: 1638 * 2 ** -11,
+             2 ** -25: 0.0, 2 ** -25 + 2 ** -60: 2 ** -24}   # subnormal spacing 2^-24
+    for x, want in cases.items():
+        assert oracle.half_round(x) == want and oracle.half_round(-x) == -want
+    x = np.random.default_rng(5).uniform(-1, 1, 20000) * 10.0 ** np.random.default_rng(6).uniform(-8, 0, 20000)
+    assert all(oracle.half_round(v) == float(np.float16(v)) for v in x)
+
+
+def test_estimate_half_codes_hand_example():
+    """Algorithm 3 with the edge's unit residual projection stored as binary16.
+    c = e3, P = [e1; e2] (r = 2), d = (3,4,5): b = 5, d_res = (3,4,0), u_d =
+    (0.6, 0.8), stored as (1229, 1638) * 2^-11; q = (2,0,1): a = 1, q_res =
+    (2,0,0), u_q = (1, 0).  t_hat = 0.60009765625 instead of 0.6, so with the
+    identity matching the estimate 45 - 20 t is 32.998046875 instead of the
+    exact 33."""
+    P = np.array([[1.0, 0, 0], [0, 1.0, 0]])
+    q, c, d = np.array([2.0, 0, 1]), np.array([0, 0, 1.0]), np.array([3.0, 4, 5])
+    assert oracle.estimate(q, c, d, _stats(P=P)) == 33.0
+    fp = _stats(P=P)
+    fp.codes = 16
+    assert oracle.estimate(q, c, d, fp) == 32.998046875
+
+
 def test_estimate_full_rank_is_exact_distance():
     """Eq. (2): with an orthogonal P (r = m) and identity matching the estimate
     is ||q - d||^2 exactly (the cross term q_proj^T q_res vanishes)."""
