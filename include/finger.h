@@ -167,9 +167,13 @@ typedef struct {
 #define FINGER_BUILD_NO_MATCHING 1
 #define FINGER_BUILD_NO_EPS 2
 /* also store every edge's unit residual projection P d_res / ||P d_res|| as
- * FP16 codes (round to nearest even from FP32), rows of r rounded up to 8, 16,
- * 32 or 64 halves, for FINGER_MODE_FINGER_F16.  Not an ablation: the matching
- * statistics are those of the FP32 tables. */
+ * FP16 codes (round to nearest even from FP32) for FINGER_MODE_FINGER_F16:
+ * per node 32 (deg0 <= 32) or 64 slots x 32 or 64 codes (r <= 32 or 64),
+ * zero padded, in the tensor cores' operand order, plus a copy of the
+ * layer-0 adjacency whose ids carry one flag bit (the neighbour has more than
+ * half of deg0's slots' worth of neighbours).  Needs n < 2^30, else
+ * FINGER_ERR_UNSUPPORTED.  Not an ablation: the matching statistics are those
+ * of the FP32 tables. */
 #define FINGER_BUILD_HALF_CODES 4
 
 /* Algorithm 2 and Supplementary G on the device.  For every node c with at

@@ -56,7 +56,9 @@ int search_smem_per_warp(const DevIndex& ix, int mode, int ef_cap, int H, int NP
     const int r_pad = ix.r4 * 4;
     const int uq_len = search_uq_len(ix, mode);
     const int qs_len = mode == FINGER_MODE_FINGER_LP ? ix.m8 * 8 : ix.m4 * 4;
-    const int qs_bytes = mode == FINGER_MODE_FINGER_LP ? 4 * ((qs_len + 3) & ~3) : 0;
+    // LP and FP16-code modes keep the staged query in a region of its own
+    const bool own_qs = mode == FINGER_MODE_FINGER_LP || mode == FINGER_MODE_FINGER_F16;
+    const int qs_bytes = own_qs ? 4 * ((qs_len + 3) & ~3) : 0;
     const int tile = mode == FINGER_MODE_FINGER_MLP ? 2 * 16 * (ix.mlp_kp + MLP_PAD) : 0;
     int b = 8 * ef_cap + (h16 ? 2 : 4) * H + 4 * (uq_len + r_pad) + qs_bytes + 32 * 32 * NPL +
             32 + tile;
@@ -126,6 +128,7 @@ fg::DevIndex make_dev(const finger_index* ix) {
     d.code_inv = 1.0f / ix->code_scale;
     d.edge_h = reinterpret_cast<const uint4*>(ix->edge_h);
     d.hks = ix->hks;
+    d.adj_t = ix->adj_t;
     d.W1f = ix->W1f;
     d.W2f = ix->W2f;
     d.w3 = ix->w3;
@@ -199,8 +202,8 @@ finger_status make_plan(finger_index* ix, int mode, int ef_max, int64_t nq, Sear
     p->blk_smem = 0;
     if (p->blk_smem + (int64_t)p->smem_per_warp * wpb > 227 * 1024) return FINGER_ERR_UNSUPPORTED;
     // the kernel variant with the most resident blocks that shared memory admits:
-    // 8 blocks (64 registers, plain mode), 6 (80 registers, plain, FP32 FINGER
-    // and LP), else 5 (96 registers)
+    // 8 blocks (64 registers, plain mode), 6 (80 registers, plain, FP32 FINGER,
+    // LP and FP16 codes), else 5 (96 registers)
     int bps = 0;
     p->occ = 5;
     for (int occ : {8, 6}) {
@@ -252,7 +255,7 @@ finger_status check_mode_ready(const finger_index* ix, int mode) {
     if (!ix->adj0) return FINGER_ERR_NOT_BUILT;
     if (mode != FINGER_MODE_PLAIN && !ix->edge_u) return FINGER_ERR_NOT_BUILT;
     if (mode == FINGER_MODE_FINGER_LP && !ix->edge_q) return FINGER_ERR_NOT_BUILT;
-    if (mode == FINGER_MODE_FINGER_F16 && !ix->edge_h) return FINGER_ERR_NOT_BUILT;
+    if (mode == FINGER_MODE_FINGER_F16 && (!ix->edge_h || !ix->adj_t)) return FINGER_ERR_NOT_BUILT;
     if (mode == FINGER_MODE_FINGER_MLP && !ix->has_mlp) return FINGER_ERR_NOT_BUILT;
     return FINGER_OK;
 }
@@ -403,7 +406,7 @@ void finger_index_free(finger_index* ix) {
                     ix->edge_u, ix->edge_s, ix->Xh, ix->edge_q, ix->W1f, ix->W2f, ix->w3,
                     ix->b1, ix->b2, ix->work, ix->err, ix->cnt, ix->bitmap, ix->spill,
                     ix->stage_q, ix->stage_ids, ix->stage_d, ix->eig_G, ix->eig_V, ix->xs_hi,
-                    ix->xs_lo, ix->edge_h};
+                    ix->xs_lo, ix->edge_h, ix->adj_t};
     for (void* p : ptrs) cudaFree(p);
     delete ix;
 }
@@ -411,7 +414,7 @@ void finger_index_free(finger_index* ix) {
 static void drop_tables(finger_index* ix) {
     void* ptrs[] = {ix->P, ix->Pc, ix->edge_u, ix->edge_s, ix->Xh, ix->edge_q,
                     ix->W1f, ix->W2f, ix->w3, ix->b1, ix->b2, ix->eig_G, ix->eig_V,
-                    ix->edge_h};
+                    ix->edge_h, ix->adj_t};
     for (void* p : ptrs) cudaFree(p);
     ix->eig_G = ix->eig_V = nullptr;
     ix->corr = 0.0 / 0.0;
@@ -420,6 +423,7 @@ static void drop_tables(finger_index* ix) {
     ix->Xh = nullptr;
     ix->edge_q = nullptr;
     ix->edge_h = nullptr;
+    ix->adj_t = nullptr;
     ix->hks = 0;
     ix->W1f = ix->W2f = nullptr;
     ix->w3 = ix->b1 = ix->b2 = nullptr;
@@ -540,7 +544,7 @@ finger_status finger_get_info(const finger_index* ix, finger_info* out) {
     if (ix->adj0) b += ix->n * ix->deg0 * 4 + ix->n * 8 + ix->up_rows * ix->M * 4;
     if (ix->edge_u) b += ix->n * ix->r_pad * 4 + finger_table_bytes(ix->n, ix->deg0, ix->r_pad, 0);
     if (ix->edge_q) b += finger_table_bytes(ix->n, ix->deg0, ix->r, 1) + ix->n * ix->m8 * 16;
-    if (ix->edge_h) b += ix->n * (ix->deg0 > 32 ? 4 : 2) * ix->hks * 512;
+    if (ix->edge_h) b += ix->n * (ix->deg0 > 32 ? 4 : 2) * ix->hks * 512 + ix->n * ix->deg0 * 4;
     b += ix->bitmap_slots * ix->words * 4 + ix->bitmap_slots * ix->spill_cap * 4;
     out->device_bytes = b;
     return FINGER_OK;

@@ -53,6 +53,9 @@ struct DevIndex {
     // per node 2 NPL tiles of 16 slots x hks k steps x 32 lanes x 16 bytes
     const uint4* edge_h;
     int hks;                // k steps of 16 codes: 2 (r <= 32) or 4 (r <= 64)
+    // layer-0 adjacency for that mode: ids with bit 30 set when the neighbour
+    // has more than 16 NPL neighbours (second half of its code block needed)
+    const uint32_t* adj_t;
     // learned predictor: BF16 W1 (H x kp, zero padded beyond r+4) and W2 (H x H)
     // stored fragment-major for m16n8k16 B operands (uint2 per lane per
     // (n8 tile, k16 step)), w3 (H, BF16-valued FP32), FP32 biases
@@ -182,6 +185,7 @@ struct finger_index {
     // FP16 codes (fragment order, see DevIndex)
     uint16_t* edge_h = nullptr;
     int hks = 0;
+    uint32_t* adj_t = nullptr;    // tagged layer-0 adjacency (see DevIndex)
     float code_scale = 256.0f;
     // learned predictor
     int has_mlp = 0;

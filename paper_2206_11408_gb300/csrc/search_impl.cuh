@@ -135,11 +135,18 @@ __device__ __forceinline__ float row_partial(const QRegs<LP, VPL>& q, const DevI
     return acc;
 }
 
-// exact distances of the rows nbs[lst[i]], i < nlist, into xb[lst[i]]
-template <bool LP, int G, int VPL>
-__device__ __forceinline__ void exact_list(const QRegs<LP, VPL>& q, const DevIndex& ix,
-                                           const uint32_t* nbs, const int* lst, int nlist,
-                                           float* xb, int lane) {
+// exact distances of the rows nbs[lst[i]], i < nlist, into xb[lst[i]].  With
+// QS the lane's query chunks are read from the staged query qs (shared
+// memory) for this call only instead of living in registers for the whole
+// search (the FP16-code mode, whose code block needs the registers).
+template <bool LP, int G, int VPL, bool QS = false>
+__device__ __forceinline__ void exact_list(const QRegs<LP, VPL>& qr, const float* qs,
+                                           const DevIndex& ix, const uint32_t* nbs,
+                                           const int* lst, int nlist, float* xb, int lane,
+                                           uint32_t idm = 0xFFFFFFFFu) {
+    QRegs<LP, VPL> qt;
+    if constexpr (QS) load_qregs<LP, G, VPL>(qt, qs, LP ? ix.m8 : ix.m4, lane % G);
+    const QRegs<LP, VPL>& q = QS ? qt : qr;
     constexpr int RPW = 32 / G;
     constexpr int U = VPL >= 8 ? 1 : VPL >= 4 ? 2 : 4;   // rows per group in flight
     const int grp = lane / G, kin = lane % G;
@@ -153,7 +160,7 @@ __device__ __forceinline__ void exact_list(const QRegs<LP, VPL>& q, const DevInd
         }
 #pragma unroll
         for (int u = 0; u < U; ++u)
-            p[u] = o[u] >= 0 ? row_partial<LP, G, VPL>(q, ix, (uint32_t)CK(nbs[CK(o[u], 64, 1018)], ix.n, 1019), kin) : 0.f;
+            p[u] = o[u] >= 0 ? row_partial<LP, G, VPL>(q, ix, (uint32_t)CK(nbs[CK(o[u], 64, 1018)] & idm, ix.n, 1019), kin) : 0.f;
 #pragma unroll
         for (int off = G / 2; off > 0; off >>= 1)
 #pragma unroll
@@ -208,11 +215,12 @@ __device__ __forceinline__ int find_next(const uint32_t* Ti, int sz, int from, i
 // insert key (d, id) into the sorted list T (size sz <= ef), dropping the
 // worst entry when full.  Caller has checked admission.
 __device__ __forceinline__ void t_insert(float* Tk, uint32_t* Ti, int& sz, int ef, float d,
-                                         uint32_t id, int& cursor, int lane) {
+                                         uint32_t id, int& cursor, int lane,
+                                         uint32_t idm = ~EXP) {
     int p = 0;
     for (int b = 0; b < sz; b += 32) {
         const int i = b + lane;
-        const bool lt = i < sz && key_lt(Tk[i], Ti[i] & ~EXP, d, id);
+        const bool lt = i < sz && key_lt(Tk[i], Ti[i] & idm, d, id & idm);
         p += __popc(__ballot_sync(FULLMASK, lt));
     }
     const int last = sz < ef ? sz : ef - 1;
@@ -406,41 +414,55 @@ __device__ __forceinline__ uint32_t pack_half2(float lo, float hi) {
     return *reinterpret_cast<uint32_t*>(&v);
 }
 
-// one round: tiles t0 .. t0 + TPR - 1 (TPR = min(NT, 8 / KS)) into hx[T KS + ks]
+// one round: tiles t0 .. t0 + TPR - 1 (TPR = min(NT, 8 / KS)) into hx[T KS + ks].
+// The second half of the block (tiles NT/2 ..) holds slots 16 NT/2 .. and is
+// all zero rows for a centre of at most that degree; it is read only when
+// `full` (the centre's tag) says the centre has more neighbours, else zeros.
 template <int KS, int NT>
-__device__ __forceinline__ void wb_load(const DevIndex& ix, uint32_t c, int t0, uint4 (&hx)[8],
-                                        int lane) {
+__device__ __forceinline__ void wb_load(const DevIndex& ix, uint32_t c, int t0, bool full,
+                                        uint4 (&hx)[8], int lane) {
     constexpr int TPR = NT * KS <= 8 ? NT : 8 / KS;
     const uint4* base = ix.edge_h + ((size_t)c * NT + t0) * KS * 32 + lane;
 #pragma unroll
     for (int T = 0; T < TPR; ++T)
 #pragma unroll
-        for (int ks = 0; ks < KS; ++ks) hx[T * KS + ks] = __ldg(base + (T * KS + ks) * 32);
+        for (int ks = 0; ks < KS; ++ks) {
+            const bool need = TPR < NT || T < NT / 2 || full;   // (compile-time unless split)
+            hx[T * KS + ks] = need ? __ldg(base + (T * KS + ks) * 32) : make_uint4(0u, 0u, 0u, 0u);
+        }
+}
+
+// The B fragments live in shared memory as packed half2 words in fragment
+// order: word ((ks * 2 + p) * 4 + t) * 2 + w holds codes 16ks + 2t + 8w, +1 of
+// u_q's high (p = 0) or low (p = 1) part, so lane 4g + t reads its two words
+// of step ks (column g takes part g & 1) with one 8-byte load.  wb_bfrag_store
+// writes them from u_q's entries 2l, 2l + 1 formed by lane l.
+__device__ __forceinline__ void wb_bfrag_store(uint32_t* bsm, float u0, float u1, int ks_n, int lane) {
+    const __half2 h = __floats2half2_rn(u0, u1);
+    const float2 hf = __half22float2(h);
+    const __half2 l = __floats2half2_rn(u0 - hf.x, u1 - hf.y);
+    const int ks = lane >> 3, t = lane & 3, w = (lane >> 2) & 1;
+    if (ks < ks_n) {
+        bsm[((ks * 2 + 0) * 4 + t) * 2 + w] = *reinterpret_cast<const uint32_t*>(&h);
+        bsm[((ks * 2 + 1) * 4 + t) * 2 + w] = *reinterpret_cast<const uint32_t*>(&l);
+    }
 }
 
 // t_hat of rows 16(t0+T)+g (v[2(t0+T)]) and +8 (v[2(t0+T)+1]) for the round's
-// tiles.  k step outer: the B fragment of one step (lane 4g + t gives column g
-// at codes 16ks + 2t, +1 and +8, +9; even columns the high part, odd columns
-// the low part) serves every tile, and each code register dies at its MMA.
+// tiles; k step outer, so each code register dies at its MMA.
 template <int KS, int NT>
-__device__ __forceinline__ void wb_mma(const uint4 (&hx)[8], const float* uq, int t0,
+__device__ __forceinline__ void wb_mma(const uint4 (&hx)[8], const uint32_t* bsm, int t0,
                                        float (&v)[8], int lane) {
     constexpr int TPR = NT * KS <= 8 ? NT : 8 / KS;
-    const int g = lane >> 2, t = lane & 3;
-    const bool lo = g & 1;
+    const uint2* bf = reinterpret_cast<const uint2*>(bsm) + ((lane >> 2) & 1) * 4 + (lane & 3);
     float acc[TPR][4];
 #pragma unroll
     for (int T = 0; T < TPR; ++T) acc[T][0] = acc[T][1] = acc[T][2] = acc[T][3] = 0.f;
 #pragma unroll
     for (int ks = 0; ks < KS; ++ks) {
-        const float2 x01 = *reinterpret_cast<const float2*>(uq + 16 * ks + 2 * t);
-        const float2 x89 = *reinterpret_cast<const float2*>(uq + 16 * ks + 2 * t + 8);
-        const float2 h01 = __half22float2(__floats2half2_rn(x01.x, x01.y));
-        const float2 h89 = __half22float2(__floats2half2_rn(x89.x, x89.y));
-        const uint32_t b0 = lo ? pack_half2(x01.x - h01.x, x01.y - h01.y) : pack_half2(x01.x, x01.y);
-        const uint32_t b1 = lo ? pack_half2(x89.x - h89.x, x89.y - h89.y) : pack_half2(x89.x, x89.y);
+        const uint2 b = bf[ks * 8];
 #pragma unroll
-        for (int T = 0; T < TPR; ++T) mma_f16(acc[T], hx[T * KS + ks], b0, b1);
+        for (int T = 0; T < TPR; ++T) mma_f16(acc[T], hx[T * KS + ks], b.x, b.y);
     }
 #pragma unroll
     for (int T = 0; T < TPR; ++T) {
@@ -617,6 +639,10 @@ __global__ void __launch_bounds__(128, OCC) k_search(DevIndex ix, SearchArgs a) 
     constexpr bool WB = MODE == MODE_F16_K2 || MODE == MODE_F16_K4;
     constexpr int WKS = MODE == MODE_F16_K2 ? 2 : 4;
     constexpr int WNT = 2 * NPL;                            // tiles per node
+    // ids in T: FP16-code mode ids carry the tag TAG (the node has more than
+    // 16 NPL neighbours, so its code block's second half is needed) below EXP
+    constexpr uint32_t TAG = 0x40000000u;
+    constexpr uint32_t IDM = WB ? ~(EXP | TAG) : ~EXP;        // id without flags
     extern __shared__ __align__(16) unsigned char sm[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
@@ -632,13 +658,16 @@ __global__ void __launch_bounds__(128, OCC) k_search(DevIndex ix, SearchArgs a) 
     uint32_t* hash = Ti + a.ef_cap;
     const int hwords = a.h16 ? a.H >> 1 : a.H;   // 32-bit words of the visited hash
     float* uq = reinterpret_cast<float*>(hash + hwords);
-    const int uq_len = WB ? max(r_pad, 16 * WKS) : r_pad;   // FP16 codes: zero padded
+    // FP16 codes: the region holds u_q's B fragments, 16 KS packed words
+    const int uq_len = WB ? max(r_pad, 16 * WKS) : r_pad;
     float* pq = uq + uq_len;
     // the query staging buffer is only read before the visited hash is cleared,
-    // so outside the LP mode (which re-reads it for the FP32 re-rank) it lives
-    // inside the hash region (the plan keeps its words >= m_pad)
-    float* qs = LP ? pq + r_pad : reinterpret_cast<float*>(hash);
-    uint32_t* nbs = reinterpret_cast<uint32_t*>(LP ? qs + ((qs_len + 3) & ~3) : pq + r_pad);
+    // so outside the LP mode (which re-reads it for the FP32 re-rank) and the
+    // FP16-code mode (whose exact distances read it) it lives inside the hash
+    // region (the plan keeps its words >= m_pad)
+    constexpr bool QSM = LP || WB;   // query kept in its own region
+    float* qs = QSM ? pq + r_pad : reinterpret_cast<float*>(hash);
+    uint32_t* nbs = reinterpret_cast<uint32_t*>(QSM ? qs + ((qs_len + 3) & ~3) : pq + r_pad);
     float* es = reinterpret_cast<float*>(nbs + 32 * NPL);
     float* xb = es + 32 * NPL;
     int* lst = reinterpret_cast<int*>(xb + 32 * NPL);
@@ -668,7 +697,7 @@ __global__ void __launch_bounds__(128, OCC) k_search(DevIndex ix, SearchArgs a) 
         for (int i = lane; i < qs_len; i += 32) qs[i] = i < ix.m ? qg[i] : 0.f;
         __syncwarp();
         QRegs<LP, VPL> q;
-        load_qregs<LP, G, VPL>(q, qs, nchunks, lane % G);
+        if constexpr (!WB) load_qregs<LP, G, VPL>(q, qs, nchunks, lane % G);
         float qn2 = 0.f;
         for (int i = lane; i < ix.m; i += 32) qn2 = fmaf(qs[i], qs[i], qn2);
         qn2 = warp_sum(qn2);
@@ -689,8 +718,6 @@ __global__ void __launch_bounds__(128, OCC) k_search(DevIndex ix, SearchArgs a) 
             }
             __syncwarp();
         }
-        if constexpr (WB)
-            for (int i = r_pad + lane; i < uq_len; i += 32) uq[i] = 0.f;
         int c_exp = 0, c_exa = 0, c_est = 0, c_skip = 0, c_exact = 0, c_adm = 0, c_up = 0,
             c_gath = 0;
         bool fail = false;
@@ -702,7 +729,7 @@ __global__ void __launch_bounds__(128, OCC) k_search(DevIndex ix, SearchArgs a) 
             lst[0] = 0;
         }
         __syncwarp();
-        exact_list<LP, G, VPL>(q, ix, nbs, lst, 1, xb, lane);
+        exact_list<LP, G, VPL, WB>(q, qs, ix, nbs, lst, 1, xb, lane);
         float dcur = xb[0];
         c_up++;
         c_gath++;
@@ -721,7 +748,7 @@ __global__ void __launch_bounds__(128, OCC) k_search(DevIndex ix, SearchArgs a) 
                 if (v) lst[__popc(bm & ltmask)] = lane;
                 __syncwarp();
                 const int cv = __popc(bm);
-                exact_list<LP, G, VPL>(q, ix, nbs, lst, cv, xb, lane);
+                exact_list<LP, G, VPL, WB>(q, qs, ix, nbs, lst, cv, xb, lane);
                 c_up += cv;
                 c_gath += cv;
                 float bd = v ? xb[lane] : INFINITY;
@@ -751,7 +778,7 @@ __global__ void __launch_bounds__(128, OCC) k_search(DevIndex ix, SearchArgs a) 
         __syncwarp();
         if (lane == 0) {
             Tk[0] = dcur;
-            Ti[0] = cur;
+            Ti[0] = WB ? cur | TAG : cur;   // (its degree is not looked up: read both halves)
             if (a.h16) {   // the table is empty: distance 0, first slot
                 const uint32_t h = (cur * 0x9E3779B1u) & ((1u << (logNB + 15)) - 1u);
                 reinterpret_cast<uint16_t*>(hash)[8 * (h >> 15)] = (uint16_t)(h & 0x7FFFu);
@@ -770,25 +797,38 @@ __global__ void __launch_bounds__(128, OCC) k_search(DevIndex ix, SearchArgs a) 
                 fail = true;
                 break;
             }
-            const uint32_t c = Ti[CK(cursor, ef, 1001)];
+            const uint32_t craw = Ti[CK(cursor, ef, 1001)];
+            const uint32_t c = craw & IDM;
+            const bool cfull = craw & TAG;   // FP16 codes: second half of the block needed
             const float dc = Tk[CK(cursor, ef, 1002)];
             __syncwarp();
-            if (lane == 0) Ti[cursor] = c | EXP;
+            if (lane == 0) Ti[cursor] = craw | EXP;
             expansions++;
             const bool use_est = EST && expansions > a.warmup;
 
-            uint32_t nb[NPL];
+            uint32_t nb[NPL], nbt[NPL];   // neighbour ids; as stored (FP16 codes: tagged)
 #pragma unroll
             for (int s = 0; s < NPL; ++s) {
                 const int j = s * 32 + lane;
-                nb[s] = j < ix.deg0 ? __ldg(ix.adj0 + CK((size_t)c * ix.deg0 + j, ix.n * ix.deg0, 1003)) : PAD;
+                nbt[s] = j < ix.deg0 ? __ldg((WB ? ix.adj_t : ix.adj0) +
+                                             CK((size_t)c * ix.deg0 + j, ix.n * ix.deg0, 1003))
+                                     : PAD;
+                nb[s] = WB && nbt[s] != PAD ? nbt[s] & IDM : nbt[s];
             }
             float cc = 0.f, pc0 = 0.f, pc1 = 0.f;
             if (use_est) {
                 cc = __ldg(ix.xnorm2 + c);
                 const float* pcr = reinterpret_cast<const float*>(ix.Pc) + (size_t)c * r_pad;
-                if (lane < r_pad) pc0 = __ldg(pcr + lane);
-                if (lane + 32 < r_pad) pc1 = __ldg(pcr + lane + 32);
+                if constexpr (WB) {   // entries 2 lane, 2 lane + 1
+                    if (2 * lane < r_pad) {
+                        const float2 p2 = __ldg(reinterpret_cast<const float2*>(pcr) + lane);
+                        pc0 = p2.x;
+                        pc1 = p2.y;
+                    }
+                } else {
+                    if (lane < r_pad) pc0 = __ldg(pcr + lane);
+                    if (lane + 32 < r_pad) pc1 = __ldg(pcr + lane + 32);
+                }
             }
             // FP16 codes: c's code block and edge scalars, requested in the same
             // round trip as the adjacency row
@@ -804,25 +844,32 @@ __global__ void __launch_bounds__(128, OCC) k_search(DevIndex ix, SearchArgs a) 
                         scw[s] = j < ix.deg0 ? __ldg(ix.edge_s + (size_t)c * ix.deg0 + j)
                                              : make_float2(0.f, 0.f);
                     }
-                    wb_load<WKS, WNT>(ix, c, 0, hx, lane);
+                    wb_load<WKS, WNT>(ix, c, 0, cfull, hx, lane);
                     // per-centre prep (Sec. 3.2 identity for q^T c, Supplementary G),
                     // then the product: the codes arrive with the adjacency row
                     // and are consumed before the visited test
                     const float qc = 0.5f * (qn2 + cc - dc);
                     wac = cc > 0.f ? qc / cc : 0.f;
                     wqres2 = fmaxf(qn2 - wac * qc, 0.f);
-                    const float u0 = lane < r_pad ? pq[lane] - wac * pc0 : 0.f;
-                    const float u1 = lane + 32 < r_pad ? pq[lane + 32] - wac * pc1 : 0.f;
+                    // this lane's entries 2 lane, 2 lane + 1 of P q_res = P q - a P c
+                    float u0 = 0.f, u1 = 0.f;
+                    if (2 * lane < r_pad) {
+                        const float2 q2 = reinterpret_cast<const float2*>(pq)[lane];
+                        u0 = q2.x - wac * pc0;
+                        u1 = q2.y - wac * pc1;
+                    }
                     const float nrm = warp_sum(u0 * u0 + u1 * u1);
                     const float inv = nrm > 0.f ? rsqrtf(nrm) : 0.f;
-                    if (lane < r_pad) uq[lane] = u0 * inv;
-                    if (lane + 32 < r_pad) uq[lane + 32] = u1 * inv;
+                    uint32_t* bsm = reinterpret_cast<uint32_t*>(uq);
+                    wb_bfrag_store(bsm, u0 * inv, u1 * inv, WKS, lane);
                     __syncwarp();
                     float v[8];
-                    wb_mma<WKS, WNT>(hx, uq, 0, v, lane);
+                    wb_mma<WKS, WNT>(hx, bsm, 0, v, lane);
                     if constexpr (WNT * WKS > 8) {   // second round: tiles 2, 3
-                        wb_load<WKS, WNT>(ix, c, 2, hx, lane);
-                        wb_mma<WKS, WNT>(hx, uq, 2, v, lane);
+                        if (cfull) {
+                            wb_load<WKS, WNT>(ix, c, 2, true, hx, lane);
+                            wb_mma<WKS, WNT>(hx, bsm, 2, v, lane);
+                        }
                     }
                     wb_route<NPL>(v, th, lane);
                 }
@@ -853,7 +900,7 @@ __global__ void __launch_bounds__(128, OCC) k_search(DevIndex ix, SearchArgs a) 
                     nspill += __popc(sb);
                 }
                 hcount += __popc(__ballot_sync(FULLMASK, res == V_NEW));
-                nbs[s * 32 + lane] = nb[s];
+                nbs[s * 32 + lane] = nbt[s];
             }
             if (hcount > a.H - (a.H >> 2)) spill_mode = true;
 
@@ -1083,7 +1130,7 @@ __global__ void __launch_bounds__(128, OCC) k_search(DevIndex ix, SearchArgs a) 
             }
             __syncwarp();
             // a6: exact distances of the survivors
-            exact_list<LP, G, VPL>(q, ix, nbs, lst, nl, xb, lane);
+            exact_list<LP, G, VPL, WB>(q, qs, ix, nbs, lst, nl, xb, lane, IDM);
             c_gath += nl;
             if constexpr (HARV) {
                 // target cos(q_res, d_res) = (q^T d - a b ||c||^2) / (||q_res|| ||d_res||),
@@ -1110,7 +1157,7 @@ __global__ void __launch_bounds__(128, OCC) k_search(DevIndex ix, SearchArgs a) 
                 // over them with a running model of ub (top-ef of T and the admitted
                 // set A), then merge A into T once.
                 const float u0d = Tk[ef - 1];
-                const uint32_t u0i = Ti[ef - 1] & ~EXP;
+                const uint32_t u0i = Ti[ef - 1] & IDM;
                 unsigned cb[NPL], cskip[NPL];
 #pragma unroll
                 for (int s = 0; s < NPL; ++s) {
@@ -1137,31 +1184,32 @@ __global__ void __launch_bounds__(128, OCC) k_search(DevIndex ix, SearchArgs a) 
                                 continue;
                             }
                             const float d = xb[CK(o, 32 * NPL, 1008)];
-                            const uint32_t id = nbs[o];
+                            const uint32_t idt = nbs[o];   // as stored in T
+                            const uint32_t id = idt & IDM;
                             if (!key_lt(d, id, ubd, ubi)) continue;
                             // the current worst of the top ef leaves it
                             if (tk == 0 ||
-                                (na > 0 && key_lt(Tk[CK(tk - 1, ef, 1009)], Ti[tk - 1] & ~EXP,
-                                                  ak[CK(na - 1, 32 * NPL, 1010)], ai[na - 1])))
+                                (na > 0 && key_lt(Tk[CK(tk - 1, ef, 1009)], Ti[tk - 1] & IDM,
+                                                  ak[CK(na - 1, 32 * NPL, 1010)], ai[na - 1] & IDM)))
                                 na--;
                             else
                                 tk--;
                             // insert (d, id) into the sorted admitted list
                             int p = na;
-                            while (p > 0 && key_lt(d, id, ak[p - 1], ai[p - 1])) {
+                            while (p > 0 && key_lt(d, id, ak[p - 1], ai[p - 1] & IDM)) {
                                 ak[CK(p, 32 * NPL, 1011)] = ak[p - 1];
                                 ai[p] = ai[p - 1];
                                 --p;
                             }
                             ak[CK(p, 32 * NPL, 1012)] = d;
-                            ai[p] = id;
+                            ai[p] = idt;
                             na++;
                             // new ub: the larger of T[tk-1] and max(A)
                             ubd = ak[na - 1];
-                            ubi = ai[na - 1];
-                            if (tk > 0 && key_lt(ubd, ubi, Tk[tk - 1], Ti[tk - 1] & ~EXP)) {
+                            ubi = ai[na - 1] & IDM;
+                            if (tk > 0 && key_lt(ubd, ubi, Tk[tk - 1], Ti[tk - 1] & IDM)) {
                                 ubd = Tk[tk - 1];
-                                ubi = Ti[tk - 1] & ~EXP;
+                                ubi = Ti[tk - 1] & IDM;
                             }
                             apos[CK(nadm, 32 * NPL, 1013)] = o;
                             aub[nadm] = ubd;
@@ -1217,7 +1265,7 @@ __global__ void __launch_bounds__(128, OCC) k_search(DevIndex ix, SearchArgs a) 
                             int lo = 0, hi = tk;
                             while (lo < hi) {
                                 const int mid = (lo + hi) >> 1;
-                                if (key_lt(Tk[mid], Ti[mid] & ~EXP, akd[t], aki[t])) lo = mid + 1;
+                                if (key_lt(Tk[mid], Ti[mid] & IDM, akd[t], aki[t] & IDM)) lo = mid + 1;
                                 else hi = mid;
                             }
                             apt[t] = lo;
@@ -1233,7 +1281,7 @@ __global__ void __launch_bounds__(128, OCC) k_search(DevIndex ix, SearchArgs a) 
                         if (act) {
                             kd = Tk[i];
                             ki = Ti[i];
-                            for (int k = 0; k < na; ++k) sh += key_lt(ak[k], ai[k], kd, ki & ~EXP);
+                            for (int k = 0; k < na; ++k) sh += key_lt(ak[k], ai[k] & IDM, kd, ki & IDM);
                         }
                         __syncwarp();
                         if (act && sh) {
@@ -1272,11 +1320,11 @@ __global__ void __launch_bounds__(128, OCC) k_search(DevIndex ix, SearchArgs a) 
                             }
                         }
                         const float d = xb[o];
-                        const uint32_t id = nbs[o];
+                        const uint32_t idt = nbs[o];   // as stored in T
                         c_exact++;
-                        if (!full || key_lt(d, id, Tk[sz - 1], Ti[sz - 1] & ~EXP)) {
+                        if (!full || key_lt(d, idt & IDM, Tk[sz - 1], Ti[sz - 1] & IDM)) {
                             CK(sz, ef + 1, 1016);
-                            t_insert(Tk, Ti, sz, ef, d, id, cursor, lane);
+                            t_insert(Tk, Ti, sz, ef, d, idt, cursor, lane, IDM);
                             c_adm++;
                         }
                     }
@@ -1292,15 +1340,15 @@ __global__ void __launch_bounds__(128, OCC) k_search(DevIndex ix, SearchArgs a) 
             float* rk = reinterpret_cast<float*>(hash);
             uint32_t* ri = hash + a.ef_cap;   // the plan keeps 2 ef_cap words in the table
             for (int i = 0; i < R; ++i) {
-                const float d = exact_f32_row(qs, ix, Ti[i] & ~EXP, lane);
+                const float d = exact_f32_row(qs, ix, Ti[i] & IDM, lane);
                 if (lane == 0) Tk[i] = d;
             }
             __syncwarp();
             for (int i = lane; i < R; i += 32) {
                 const float d = Tk[i];
-                const uint32_t id = Ti[i] & ~EXP;
+                const uint32_t id = Ti[i] & IDM;
                 int rank = 0;
-                for (int j = 0; j < R; ++j) rank += key_lt(Tk[j], Ti[j] & ~EXP, d, id);
+                for (int j = 0; j < R; ++j) rank += key_lt(Tk[j], Ti[j] & IDM, d, id);
                 rk[rank] = d;
                 ri[rank] = id;
             }
@@ -1314,7 +1362,7 @@ __global__ void __launch_bounds__(128, OCC) k_search(DevIndex ix, SearchArgs a) 
 
         // ---- a7: output
         for (int k = lane; k < K; k += 32) {
-            a.out_ids[ooff + k] = k < sz ? (int64_t)(Ti[k] & ~EXP) : (int64_t)-1;
+            a.out_ids[ooff + k] = k < sz ? (int64_t)(Ti[k] & IDM) : (int64_t)-1;
             a.out_d[ooff + k] = k < sz ? Tk[k] : INFINITY;
         }
         for (int i = lane; i < nspill; i += 32) bitmap[spl[i] >> 5] = 0u;
@@ -1347,9 +1395,10 @@ __global__ void __launch_bounds__(128, OCC) k_search(DevIndex ix, SearchArgs a) 
 
 // instantiate and dispatch one mode over the (G, VPL, NPL) variants and the
 // resident-block target: 5 blocks of 4 warps (96 registers) everywhere, 6 (80
-// registers) for the plain, FP32 FINGER and LP modes, 8 (64 registers) for the
-// plain mode.  FINGER keeps its gathers in flight in registers, so it is
-// fastest at 6; plain search at 8.
+// registers) for the plain, FINGER, LP and FP16-code modes, 8 (64 registers)
+// for the plain mode.  The FINGER modes keep their gathers in flight in
+// registers and are fastest at 6 (the FP16-code mode measured slower at 7,
+// where it spills); plain search at 8.
 template <int MODE, int OCC>
 cudaError_t launch_occ(const DevIndex& ix, const SearchArgs& a, const SearchPlan& p,
                        cudaStream_t s) {

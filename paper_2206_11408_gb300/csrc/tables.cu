@@ -627,6 +627,24 @@ __global__ void k_half_codes(const float* edge_u, int64_t n, int deg0, int r_pad
     out[i] = *reinterpret_cast<const uint4*>(w);
 }
 
+// layer-0 degree of every node
+__global__ void k_degree(const uint32_t* adj0, int64_t n, int deg0, int32_t* deg) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    int d = 0;
+    for (int j = 0; j < deg0; ++j) d += adj0[v * deg0 + j] != PAD;
+    deg[v] = d;
+}
+
+// adjacency with each neighbour id tagged (bit 30) when its degree exceeds thr
+__global__ void k_tag_adj(const uint32_t* adj0, int64_t ne, const int32_t* deg, int thr,
+                          uint32_t* out) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= ne) return;
+    const uint32_t u = adj0[e];
+    out[e] = u == PAD ? PAD : (deg[u] > thr ? u | 0x40000000u : u);
+}
+
 template <class T>
 T* dalloc(size_t count) {
     void* p = nullptr;
@@ -679,23 +697,39 @@ cudaError_t lp_rebuild(finger_index* ix) {
 // tensor cores' A-fragment order: per node 2 tiles of 16 slots (4 when
 // deg0 > 32; rows beyond deg0 are zero) x 2 k steps of 16 codes (4 when
 // r > 32) x 512 bytes
+// The same mode reads a tagged copy of the layer-0 adjacency: a neighbour's id
+// has bit 30 set when its degree exceeds 16 (32 when deg0 > 32), i.e. when the
+// second half of its code block holds rows; ids must stay below 2^30.
 cudaError_t half_rebuild(finger_index* ix) {
     using namespace fg;
     cudaFree(ix->edge_h);
+    cudaFree(ix->adj_t);
     ix->edge_h = nullptr;
+    ix->adj_t = nullptr;
     ix->hks = 0;
+    if (ix->n >= (int64_t(1) << 30)) return cudaErrorInvalidValue;
     const int hks = ix->r > 32 ? 4 : 2;
     const int tiles = ix->deg0 > 32 ? 4 : 2;
-    const int64_t units = ix->n * tiles * hks * 32;
+    const int64_t units = ix->n * tiles * hks * 32, ne = ix->n * ix->deg0;
+    int32_t* deg = nullptr;
     cudaError_t e = cudaMalloc(&ix->edge_h, sizeof(uint4) * (size_t)units + 16);
-    if (e != cudaSuccess) return e;
+    if (e == cudaSuccess) e = cudaMalloc(&ix->adj_t, sizeof(uint32_t) * (size_t)ne + 16);
+    if (e == cudaSuccess) e = cudaMalloc(&deg, sizeof(int32_t) * (size_t)ix->n);
+    if (e != cudaSuccess) {
+        cudaFree(deg);
+        return e;
+    }
     k_half_codes<<<(unsigned)((units + 255) / 256), 256>>>(ix->edge_u, ix->n, ix->deg0,
                                                           ix->r_pad, tiles, hks,
                                                           reinterpret_cast<uint4*>(ix->edge_h));
+    k_degree<<<(unsigned)((ix->n + 255) / 256), 256>>>(ix->adj0, ix->n, ix->deg0, deg);
+    k_tag_adj<<<(unsigned)((ne + 255) / 256), 256>>>(ix->adj0, ne, deg, 8 * tiles, ix->adj_t);
     e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    cudaFree(deg);
     if (e != cudaSuccess) return e;
     ix->hks = hks;
-    return cudaDeviceSynchronize();
+    return cudaSuccess;
 }
 
 namespace fg {
@@ -823,6 +857,8 @@ finger_status build_tables(finger_index* ix, const finger_build_params* p, cudaS
     if (r < 1 || r > MAX_R || r > ix->m) return FINGER_ERR_INVALID_ARG;
     if (p->flags & ~(FINGER_BUILD_NO_MATCHING | FINGER_BUILD_NO_EPS | FINGER_BUILD_HALF_CODES))
         return FINGER_ERR_INVALID_ARG;
+    if ((p->flags & FINGER_BUILD_HALF_CODES) && ix->n >= (int64_t(1) << 30))
+        return FINGER_ERR_UNSUPPORTED;   // the FP16-code mode tags ids in bit 30
     const int spn = p->samples_per_node > 0 ? p->samples_per_node : 1;
     const int64_t n = ix->n;
     const int m = ix->m, m_pad = ix->m_pad, m4 = ix->m4, deg0 = ix->deg0;
@@ -890,9 +926,11 @@ finger_status build_tables(finger_index* ix, const finger_build_params* p, cudaS
     cudaFree(ix->Xh);
     cudaFree(ix->edge_q);
     cudaFree(ix->edge_h);
+    cudaFree(ix->adj_t);
     ix->Xh = nullptr;
     ix->edge_q = nullptr;
     ix->edge_h = nullptr;
+    ix->adj_t = nullptr;
     ix->hks = 0;
 done:
     cudaFree(pairs);
