@@ -653,7 +653,20 @@ __global__ void __launch_bounds__(128, OCC) k_search(DevIndex ix, SearchArgs a) 
     const int qs_len = LP ? ix.m8 * 8 : ix.m4 * 4;
 
     unsigned char* wb = sm + a.blk_smem + (size_t)wib * a.warp_smem;
-    float* Tk = reinterpret_cast<float*>(wb);
+    // Per-warp region: first the fixed-size staging of one expansion (compile-
+    // time offsets from wb, so its addresses need no pointer registers), then
+    // the regions whose sizes depend on the launch (result list, visited hash,
+    // projections, staged query, predictor tile).
+    uint32_t* nbs = reinterpret_cast<uint32_t*>(wb);           // neighbour of each slot
+    float* es = reinterpret_cast<float*>(nbs + 32 * NPL);      // estimate of each slot
+    float* xb = es + 32 * NPL;                                 // exact distance / t_hat
+    int* lst = reinterpret_cast<int*>(xb + 32 * NPL);          // compacted slot lists
+    float* ak = reinterpret_cast<float*>(lst + 32 * NPL);      // admitted keys (sorted)
+    uint32_t* ai = reinterpret_cast<uint32_t*>(ak + 32 * NPL);
+    int* apos = reinterpret_cast<int*>(ai + 32 * NPL);         // slot of each admission
+    float* aub = reinterpret_cast<float*>(apos + 32 * NPL);    // ub after it
+    int* meta = reinterpret_cast<int*>(aub + 32 * NPL);        // replay results (8 ints)
+    float* Tk = reinterpret_cast<float*>(meta + 8);
     uint32_t* Ti = reinterpret_cast<uint32_t*>(Tk + a.ef_cap);
     uint32_t* hash = Ti + a.ef_cap;
     const int hwords = a.h16 ? a.H >> 1 : a.H;   // 32-bit words of the visited hash
@@ -667,16 +680,7 @@ __global__ void __launch_bounds__(128, OCC) k_search(DevIndex ix, SearchArgs a) 
     // region (the plan keeps its words >= m_pad)
     constexpr bool QSM = LP || WB;   // query kept in its own region
     float* qs = QSM ? pq + r_pad : reinterpret_cast<float*>(hash);
-    uint32_t* nbs = reinterpret_cast<uint32_t*>(QSM ? qs + ((qs_len + 3) & ~3) : pq + r_pad);
-    float* es = reinterpret_cast<float*>(nbs + 32 * NPL);
-    float* xb = es + 32 * NPL;
-    int* lst = reinterpret_cast<int*>(xb + 32 * NPL);
-    float* ak = reinterpret_cast<float*>(lst + 32 * NPL);     // admitted keys (sorted)
-    uint32_t* ai = reinterpret_cast<uint32_t*>(ak + 32 * NPL);
-    int* apos = reinterpret_cast<int*>(ai + 32 * NPL);        // slot of each admission
-    float* aub = reinterpret_cast<float*>(apos + 32 * NPL);   // ub after it
-    int* meta = reinterpret_cast<int*>(aub + 32 * NPL);       // replay results (8 ints)
-    __nv_bfloat16* xt = reinterpret_cast<__nv_bfloat16*>(meta + 8);   // predictor input tile
+    __nv_bfloat16* xt = reinterpret_cast<__nv_bfloat16*>(QSM ? qs + ((qs_len + 3) & ~3) : pq + r_pad);   // predictor input tile
     if (FG_CHECKED) g_chk_err = a.err;   // same value from every thread
     const int64_t slot = (int64_t)blockIdx.x * wpb + wib;
     uint32_t* bitmap = a.bitmap + slot * a.words;
@@ -863,7 +867,7 @@ __global__ void __launch_bounds__(128, OCC) k_search(DevIndex ix, SearchArgs a) 
                     uint32_t* bsm = reinterpret_cast<uint32_t*>(uq);
                     wb_bfrag_store(bsm, u0 * inv, u1 * inv, WKS, lane);
                     __syncwarp();
-                    float v[8];
+                    float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
                     wb_mma<WKS, WNT>(hx, bsm, 0, v, lane);
                     if constexpr (WNT * WKS > 8) {   // second round: tiles 2, 3
                         if (cfull) {
