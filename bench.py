@@ -4,23 +4,26 @@
 Workload (default): n = 1,000,000 vectors, m = 128, integer values 0..255 from
 per-dimension gamma distributions in 64 clusters (a seeded stand-in with the
 shape of SIFT-1M); HNSW-style graph with M = 16 (layer-0 degree 32) built on the
-GPU from exact 64-nearest-neighbour candidates; FINGER rank r = 64; 10,000 fresh
-queries from the same mixture; K = 10.
+GPU from exact 200-nearest-neighbour candidates; FINGER rank r = 64; 10,000
+fresh queries from the same mixture; K = 10.
 
-Setup (untimed): data, graph, FINGER tables, exact ground truth by GPU brute
-force, then an ef sweep of both methods to find the smallest ef whose
-recall@10 reaches 0.95.  A step is one finger_search over the 10,000-query
-batch at that ef (one persistent kernel launch); `value` is queries/s of FINGER
-at its ef, `plain_qps` the same for plain greedy search at its own ef.  The
-index (~9 GB) is far larger than L2, so no flush is needed between steps.
+Setup (untimed): data, graph, FINGER tables (FP32, and the FP16 codes),
+exact ground truth by GPU brute force, then for every method an ef sweep and a
+step-2 refinement to find the smallest ef whose recall@10 reaches 0.95.  A
+step is one finger_search over the 10,000-query batch at that ef (one
+persistent kernel launch).  `value` is queries/s of FINGER with FP16 codes
+(the fastest FINGER form: the per-edge codes in FP16, estimates as one
+tensor-core matrix-vector product, FP32 vectors and distances); `plain_qps`
+the same for plain greedy search at its own ef, `finger_f32_qps` FINGER on
+the FP32 tables.  The index (~14 GB) is far larger than L2, so no flush is
+needed between steps.
 
 Multi-GPU (torchrun): every rank holds a replica of the index and searches its
 own batch of queries (weak scaling, no data-path collective); the barrier and
 the max-over-ranks timing use torch.distributed.
 
---impl reference times the CPU oracle instead (FP64 brute-force exact kNN, the
-one oracle function that runs on this workload without inputs from the CUDA
-path; recall 1.0), on a bounded sample of queries per step.
+--impl reference times the CPU oracle instead: its own FINGER search on an
+HNSW graph it builds on the first 20,000 rows, on bounded query samples.
 """
 from __future__ import annotations
 
@@ -142,7 +145,7 @@ def measured_peaks():
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("search_impl.cuh", "search_m1.cu"):
+    for f in ("search_impl.cuh", "search_f16_k4.cu"):
         h.update(open(os.path.join(ROOT, "paper_2206_11408_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -161,14 +164,17 @@ def profiled_traffic(workload: str, per_query_scale: float):
 
 def algorithmic_bytes(cnt: dict, nq: int, m: int, r: int, deg0: int, M: int, K: int,
                       warmup: int, finger: bool, lp: bool = False, rerank: int = 0,
-                      sector: int = 0) -> float:
+                      sector: int = 0, code_bytes: float | None = None) -> float:
     """Bytes the method must move per launch: the adjacency row of every
     layer-0 expansion (deg0 u32), the per-centre row (||c||^2 and P c, r+1
     floats) of every post-warm-up expansion, one edge row (r+2 floats; LP:
     r one-byte codes + 2 floats) per estimate, one vector row per exact distance
     (m floats; LP: m BF16) on layer 0 and on the upper levels, the FP32 rows of
-    the re-ranked entries (LP), the queries and the results.  ``sector`` > 0
-    rounds every row up to whole sectors of that many bytes."""
+    the re-ranked entries (LP), the queries and the results.  With
+    ``code_bytes`` (the FP16-code mode) the per-estimate rows are replaced by
+    what that mode reads per post-warm-up expansion: the edge scalars of all
+    deg0 slots and the FP16 code blocks, whose total the kernel counts.
+    ``sector`` > 0 rounds every row up to whole sectors of that many bytes."""
     def row(nbytes):
         return -(-nbytes // sector) * sector if sector else nbytes
 
@@ -180,7 +186,10 @@ def algorithmic_bytes(cnt: dict, nq: int, m: int, r: int, deg0: int, M: int, K: 
     if finger:
         post = max(E - warmup * nq, 0)
         b += post * (row(4 * r) + row(4))
-        b += cnt["estimates"] * ((row(r) if lp else row(4 * r)) + row(8))
+        if code_bytes is not None:
+            b += post * row(8 * deg0) + code_bytes
+        else:
+            b += cnt["estimates"] * ((row(r) if lp else row(4 * r)) + row(8))
     if lp:
         b += nq * rerank * row(4 * m)
     b += nq * 4 * m + nq * K * 12
@@ -214,7 +223,76 @@ def tie_recall(ids: np.ndarray, dists: np.ndarray, gt_d: np.ndarray, K: int) -> 
 
 # ---------------------------------------------------------------- reference
 
+CPU_PREFIX = 20_000   # rows of the workload the oracle builds its own HNSW graph on
+
+
+def oracle_search_timing(cfg: int, K: int, r: int, M: int, ef_construction: int,
+                         nq_sample: int = 2000, nq_single: int = 200, n: int = CPU_PREFIX):
+    """The FP64 CPU oracle's own FINGER search (Algorithm 4 on binary16 codes,
+    the mode the GPU headline runs) and plain greedy search (Algorithm 1), on
+    an HNSW graph the oracle builds itself on the first ``n`` rows of the
+    workload (the oracle never takes the GPU-built graph) with the workload's
+    M, efConstruction and rank.  For each method the smallest ef (step 10) whose
+    recall@K against the oracle's brute force reaches 0.95 on 400 queries is
+    timed on ``nq_sample`` queries with OpenMP over all host cores and on
+    ``nq_single`` queries with one thread.  Setup (graph, tables, ground truth)
+    is untimed."""
+    import dataclasses
+
+    import oracle
+    cores = os.cpu_count() or 1
+    X = workloads.base_vectors(cfg, n).astype(np.float64)
+    Q = workloads.query_vectors(cfg, max(nq_sample, 400)).astype(np.float64)
+    t = time.perf_counter()
+    g = oracle.hnsw_build(X, M, ef_construction, 3000 + cfg)
+    t_graph = time.perf_counter() - t
+    fp, _ = oracle.build_tables(X, g, r, 4000 + cfg)
+    fp16 = dataclasses.replace(fp, codes=16)
+    gt, _ = oracle.bruteforce(X, Q, K, threads=cores)
+    out = {}
+    for name, f in (("finger", fp16), ("plain", None)):
+        ef_ok, rec_ok = None, None
+        for ef in range(max(K, 10), 401, 10):
+            ids, _, _ = oracle.search(g, X, Q[:400], K, ef, f, threads=cores)
+            rec = recall_at(ids, gt[:400], K)
+            if rec >= TARGET_RECALL:
+                ef_ok, rec_ok = ef, rec
+                break
+        if ef_ok is None:
+            ef_ok, rec_ok = 400, rec
+        t = time.perf_counter()
+        ids, _, _ = oracle.search(g, X, Q[:nq_sample], K, ef_ok, f, threads=cores)
+        dt_all = time.perf_counter() - t
+        t = time.perf_counter()
+        oracle.search(g, X, Q[:nq_single], K, ef_ok, f, threads=1)
+        dt_one = time.perf_counter() - t
+        out[name] = {"ef": ef_ok, "recall_400q": rec_ok,
+                     "recall_sample": recall_at(ids, gt[:nq_sample], K),
+                     "qps_all_cores": nq_sample / dt_all, "qps_1_thread": nq_single / dt_one}
+    cpu = "unknown"
+    try:
+        for line in subprocess.run(["lscpu"], capture_output=True, text=True).stdout.splitlines():
+            if line.startswith("Model name"):
+                cpu = line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return {"value": out["finger"]["qps_all_cores"], "unit": "queries/s", "cores": cores,
+            "kind": "oracle", "cpu_model": cpu, "graph_build_s": t_graph,
+            "sample": f"oracle FINGER search (Algorithm 4, binary16 codes) and plain greedy "
+                      f"search (Algorithm 1) in FP64 on an oracle-built HNSW graph (M {M}, "
+                      f"efC {ef_construction}) of the first {n} rows, r = {r}, at the "
+                      f"smallest ef (step 10) reaching recall@{K} 0.95; {nq_sample} queries "
+                      f"on {cores} cores, {nq_single} on 1 thread",
+            "finger": out["finger"], "plain": out["plain"],
+            "finger_over_plain_cpu": out["finger"]["qps_all_cores"] / out["plain"]["qps_all_cores"]}
+
+
 def run_reference(args):
+    """The reference arm: the CPU oracle's FINGER search, timed step by step on
+    bounded samples of the same workload (the first CPU_PREFIX rows, an
+    oracle-built graph); see oracle_search_timing."""
+    import dataclasses
+
     from paper_2206_11408_gb300.replicas import world
 
     ws, rank, _ = world()
@@ -222,25 +300,31 @@ def run_reference(args):
         return 0
     import oracle
     c = workloads.config(args.cfg)
-    n = args.n or c.n
-    # the oracle's own input type (FP64), converted once before any timing
+    cores = os.cpu_count() or 1
+    n = min(args.n or c.n, CPU_PREFIX)
     X = workloads.base_vectors(args.cfg, n).astype(np.float64)
     Q = workloads.query_vectors(args.cfg, args.nq or c.nq).astype(np.float64)
-    cores = os.cpu_count() or 1
-    # bounded sample per step: as many queries (a multiple of the core count) as
-    # fit in the per-step budget, so the whole run stays within a few minutes
-    budget = min(1.0, 150.0 / max(1, args.warmup + args.steps))
+    g = oracle.hnsw_build(X, c.M, c.ef_construction, 3000 + args.cfg)
+    fp, _ = oracle.build_tables(X, g, c.r, 4000 + args.cfg)
+    fp16 = dataclasses.replace(fp, codes=16)
+    gt, _ = oracle.bruteforce(X, Q[:400], c.K, threads=cores)
+    ef_ok = 400
+    for ef in range(max(c.K, 10), 401, 10):
+        ids, _, _ = oracle.search(g, X, Q[:400], c.K, ef, fp16, threads=cores)
+        if recall_at(ids, gt, c.K) >= TARGET_RECALL:
+            ef_ok = ef
+            break
+    # bounded sample per step, sized from a probe so the run stays within minutes
     t = time.perf_counter()
-    oracle.bruteforce(X, Q[:cores], c.K, threads=cores)
-    per = time.perf_counter() - t
-    sample = cores * max(1, int(budget / max(per, 1e-6)))
-    sample = min(sample, Q.shape[0])
+    oracle.search(g, X, Q[:cores * 4], c.K, ef_ok, fp16, threads=cores)
+    per = (time.perf_counter() - t) / (cores * 4)
+    budget = min(2.0, 120.0 / max(1, args.warmup + args.steps))
+    sample = int(min(Q.shape[0], max(cores, budget / max(per, 1e-9))))
     steps_t = []
     for i in range(args.warmup + args.steps):
-        lo = (i * sample) % Q.shape[0]
-        qs = Q[lo:lo + sample]
+        lo = (i * sample) % max(1, Q.shape[0] - sample + 1)
         t = time.perf_counter()
-        oracle.bruteforce(X, qs, c.K, threads=cores)
+        oracle.search(g, X, Q[lo:lo + sample], c.K, ef_ok, fp16, threads=cores)
         dt = time.perf_counter() - t
         if i >= args.warmup:
             steps_t.append(dt)
@@ -250,34 +334,16 @@ def run_reference(args):
             "unit": "queries/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
-            "config": {"workload": c.name if n == c.n else f"{c.name}[:{n}]", "n": n, "m": c.m,
-                       "K": c.K, "method": "oracle brute-force exact kNN (recall 1.0)"},
+            "config": {"workload": c.name, "n": n, "m": c.m, "K": c.K, "M": c.M, "r": c.r,
+                       "ef": ef_ok, "method": "oracle FINGER search (Algorithm 4, binary16 "
+                       "codes), FP64, oracle-built HNSW graph of the first rows"},
             "cpu_baseline": {"value": v, "unit": "queries/s", "cores": cores, "kind": "oracle",
-                             "sample": f"{sample} queries per step, FP64 brute force over all "
-                                       f"{n} rows"},
+                             "sample": f"{sample} queries per step, oracle FINGER search at ef "
+                                       f"{ef_ok} on an oracle HNSW graph of the first {n} rows"},
             "e2e": {"value": v, "unit": "queries/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
-
-
-def cpu_baseline(X, Q, K, budget_s=12.0):
-    import oracle
-    cores = os.cpu_count() or 1
-    n = X.shape[0]
-    X, Q = X.astype(np.float64), Q.astype(np.float64)   # the oracle's input type, once
-    # size the sample from a short probe
-    t = time.perf_counter()
-    oracle.bruteforce(X, Q[:cores], K, threads=cores)
-    probe = time.perf_counter() - t
-    per_q = probe / cores
-    sample = int(max(cores, min(len(Q), budget_s / max(per_q, 1e-9))))
-    t = time.perf_counter()
-    oracle.bruteforce(X, Q[:sample], K, threads=cores)
-    dt = time.perf_counter() - t
-    return {"value": sample / dt, "unit": "queries/s", "cores": cores, "kind": "oracle",
-            "sample": f"{sample} of the {len(Q)} queries, FP64 brute-force exact kNN over all {n} "
-                      f"rows (recall 1.0), OpenMP over queries"}
 
 
 # ---------------------------------------------------------------------- ours
@@ -795,6 +861,27 @@ def leg_ablation(args):
             "variants": out, "setup_s": setup}
 
 
+def _refine(timed_fn, gt, K, nq, pts):
+    """The smallest ef (step 2) whose recall reaches the target between the
+    last coarse grid point below it and the first at or above it; the points
+    it measures are added to ``pts`` as (ef, recall, queries/s).  None when
+    the coarse sweep did not reach the target."""
+    srt = sorted(pts)
+    hi = next((i for i, p_ in enumerate(srt) if p_[1] >= TARGET_RECALL), None)
+    if hi is None:
+        return None
+    if hi == 0:
+        return srt[0][0], srt[0][1]
+    lo_ef, hi_ef = srt[hi - 1][0], srt[hi][0]
+    for ef in range(lo_ef + 2, hi_ef, 2):
+        ids, ms = timed_fn(ef)
+        rec = recall_at(ids, gt, K)
+        pts.append((ef, rec, nq / (ms / 1000)))
+        if rec >= TARGET_RECALL:
+            return ef, rec
+    return hi_ef, srt[hi][1]
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -839,13 +926,14 @@ def main():
     torch.cuda.synchronize()
     t_graph = time.perf_counter() - t0
     t0 = time.perf_counter()
-    ix.build_tables(c.r, 4000 + args.cfg)
+    ix.build_tables(c.r, 4000 + args.cfg, half_codes=True)
     torch.cuda.synchronize()
     t_tables = time.perf_counter() - t0
     info = ix.info()
     q = torch.from_numpy(Q).cuda()
+    MODES = {"plain": fg.MODE_PLAIN, "finger": fg.MODE_FINGER_F16, "finger_f32": fg.MODE_FINGER}
     if args.profile_ef:
-        ix.set_mode(fg.MODE_FINGER, 5)
+        ix.set_mode(fg.MODE_FINGER_F16, 5)
         ids, d = ix.search(q, K, args.profile_ef)
         for _ in range(args.warmup):
             ix.search(q, K, args.profile_ef, ids, d)
@@ -858,6 +946,7 @@ def main():
     gt = gt_ids.cpu().numpy()
     gt_d = gt_dt.cpu().numpy()
     stream = torch.cuda.current_stream()
+    last = {}
 
     def timed(mode, ef, reps=1):
         ix.set_mode(mode, 5)
@@ -874,11 +963,10 @@ def main():
         last[mode] = (ids.cpu().numpy(), d.cpu().numpy())
         return last[mode][0], best
 
-    curves = {}
-    choice = {}
-    tie = {}
-    last = {}
-    for name, mode in (("plain", fg.MODE_PLAIN), ("finger", fg.MODE_FINGER)):
+    # coarse ef sweep of every method, then the crossing of recall 0.95 refined
+    # on a step-2 grid, so each method is timed at the smallest ef that reaches it
+    curves, choice, tie = {}, {}, {}
+    for name, mode in MODES.items():
         pts = []
         for ef in c.ef_grid:
             if ef < K:
@@ -886,15 +974,18 @@ def main():
             ids, ms = timed(mode, ef)
             rec = recall_at(ids, gt, K)
             pts.append((ef, rec, nq / (ms / 1000)))
-            if rec >= TARGET_RECALL and name not in choice:
-                choice[name] = (ef, rec)
-                tie[name] = tie_recall(last[mode][0], last[mode][1], gt_d, K)
-            if name in choice and ef >= choice[name][0] + 40:
+            if rec >= TARGET_RECALL and ef >= max(p_[0] for p_ in pts):
                 break
-        curves[name] = pts
-        if name not in choice:
-            best = max(pts, key=lambda p: p[1])
+        fine = _refine(lambda e, m=mode: timed(m, e), gt, K, nq, pts)
+        pts.sort()
+        if fine is not None:
+            choice[name] = fine
+        else:
+            best = max(pts, key=lambda p_: p_[1])
             choice[name] = (best[0], best[1])
+        ids, _ = timed(mode, choice[name][0])
+        tie[name] = tie_recall(last[mode][0], last[mode][1], gt_d, K)
+        curves[name] = pts
     t_setup = time.perf_counter() - t_setup
 
     def step_loop(mode, ef, steps, warmup, clocks=None):
@@ -921,61 +1012,79 @@ def main():
         ck = clocks.stop() if clocks else None
         ix.sync()
         total = g0.elapsed_time(g1)
-        per = [a.elapsed_time(b) for a, b in evs]
+        per = [a_.elapsed_time(b_) for a_, b_ in evs]
         return total, per, ck
 
-    # FINGER timed region (the headline) and plain at its own ef; with several
-    # replicas the ef is the largest any rank needed for the recall target
-    ef_f, rec_f = choice["finger"]
-    ef_p, rec_p = choice["plain"]
+    # timed regions: FINGER (FP16 codes; the headline), plain, FINGER on FP32
+    # tables; with several replicas each ef is the largest any rank needed
+    efs = {k: v[0] for k, v in choice.items()}
+    recs = {k: v[1] for k, v in choice.items()}
     if ws > 1:
-        ef_f, ef_p = (int(v) for v in replicas.max_over_ranks([ef_f, ef_p], dev))
-        rec_f = recall_at(timed(fg.MODE_FINGER, ef_f)[0], gt, K)
-        rec_p = recall_at(timed(fg.MODE_PLAIN, ef_p)[0], gt, K)
-        rec_f, rec_p = (v / ws for v in replicas.sum_over_ranks([rec_f, rec_p], dev))
+        names = list(MODES)
+        vals = replicas.max_over_ranks([efs[k] for k in names], dev)
+        efs = {k: int(v) for k, v in zip(names, vals)}
+        rl = [recall_at(timed(MODES[k], efs[k])[0], gt, K) for k in names]
+        recs = dict(zip(names, (v / ws for v in replicas.sum_over_ranks(rl, dev))))
     clocks = Clocks(local)
-    total_f, per_f, ck = step_loop(fg.MODE_FINGER, ef_f, args.steps, args.warmup, clocks)
-    total_p, per_p, _ = step_loop(fg.MODE_PLAIN, ef_p, args.steps, args.warmup)
-    ms_f = total_f / args.steps
-    ms_p = total_p / args.steps
-    ms_f, ms_p = replicas.max_over_ranks([ms_f, ms_p], dev)
-    value = ws * nq / (ms_f / 1000)
-    plain_qps = ws * nq / (ms_p / 1000)
+    res = {}
+    for name, mode in MODES.items():
+        total, per, ck = step_loop(mode, efs[name], args.steps, args.warmup,
+                                   clocks if name == "finger" else None)
+        ms = total / args.steps
+        ms, = replicas.max_over_ranks([ms], dev)
+        res[name] = {"ms": ms, "qps": ws * nq / (ms / 1000), "per": per, "clocks": ck}
+    ms_f = res["finger"]["ms"]
+    value = res["finger"]["qps"]
+    plain_qps = res["plain"]["qps"]
 
-    # counters of one launch for the algorithmic bytes
-    cnt_t = torch.zeros((nq, 8), dtype=torch.int32, device="cuda")
-    ix.set_counters(cnt_t)
-    ix.set_mode(fg.MODE_FINGER, 5)
-    ix.search(q, K, ef_f)
-    torch.cuda.synchronize()
-    ix.set_counters(None)
-    csum = dict(zip(fg.COUNTER_NAMES, cnt_t.sum(0).cpu().numpy().astype(np.int64).tolist()))
-    algo = algorithmic_bytes(csum, nq, c.m, c.r, info["deg0"], c.M, K, 5, True)
-    algo32 = algorithmic_bytes(csum, nq, c.m, c.r, info["deg0"], c.M, K, 5, True, sector=32)
-    kern_ms = statistics.median(per_f)
+    # counters and code bytes of one launch for the algorithmic bytes
+    def counters(mode, ef):
+        cnt_t = torch.zeros((nq, 8), dtype=torch.int32, device="cuda")
+        ix.set_counters(cnt_t)
+        ix.set_mode(mode, 5)
+        ix.reset_stats()
+        ix.search(q, K, ef)
+        torch.cuda.synchronize()
+        ix.set_counters(None)
+        st = ix.stats()
+        return dict(zip(fg.COUNTER_NAMES, cnt_t.sum(0).cpu().numpy().astype(np.int64).tolist())), st
+
+    csum, st = counters(fg.MODE_FINGER_F16, efs["finger"])
+    algo = algorithmic_bytes(csum, nq, c.m, c.r, info["deg0"], c.M, K, 5, True,
+                             code_bytes=st["code_bytes"])
+    algo32 = algorithmic_bytes(csum, nq, c.m, c.r, info["deg0"], c.M, K, 5, True, sector=32,
+                               code_bytes=st["code_bytes"])
+    kern_ms = statistics.median(res["finger"]["per"])
     peak, peak_kind = measured_peaks()
     achieved = algo / (kern_ms / 1000) / 1e9
     workload = f"{c.name}" if n == c.n else f"{c.name}[:{n}]"
     traffic = profiled_traffic(workload, nq)
+    csum_p, _ = counters(fg.MODE_PLAIN, efs["plain"])
+    algo_p = algorithmic_bytes(csum_p, nq, c.m, c.r, info["deg0"], c.M, K, 5, False)
+    kern_p = statistics.median(res["plain"]["per"])
+    csum_32, _ = counters(fg.MODE_FINGER, efs["finger_f32"])
+    algo_32 = algorithmic_bytes(csum_32, nq, c.m, c.r, info["deg0"], c.M, K, 5, True)
+    kern_32 = statistics.median(res["finger_f32"]["per"])
 
     # end to end through the C ABI with host buffers (pinned), copies inside
     qh = torch.from_numpy(Q).pin_memory()
     ih = torch.empty((nq, K), dtype=torch.int64).pin_memory()
     dh = torch.empty((nq, K), dtype=torch.float32).pin_memory()
-    ix.set_mode(fg.MODE_FINGER, 5)
+    ix.set_mode(fg.MODE_FINGER_F16, 5)
     for _ in range(args.warmup):
-        ix.search_host(qh.numpy(), K, ef_f, ih.numpy(), dh.numpy())
+        ix.search_host(qh.numpy(), K, efs["finger"], ih.numpy(), dh.numpy())
     replicas.barrier()
     t = time.perf_counter()
     for _ in range(args.steps):
-        ix.search_host(qh.numpy(), K, ef_f, ih.numpy(), dh.numpy())
+        ix.search_host(qh.numpy(), K, efs["finger"], ih.numpy(), dh.numpy())
     e2e_ms = 1000 * (time.perf_counter() - t) / args.steps
     e2e_ms, = replicas.max_over_ranks([e2e_ms], dev)
     e2e_rec = recall_at(ih.numpy(), gt, K)
+    ix.close()
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
-        cpu = cpu_baseline(X, Q, K)
+        cpu = oracle_search_timing(args.cfg, K, c.r, c.M, c.ef_construction)
 
     if args.save_curves and rank == 0:
         json.dump({"curves": curves, "choice": choice}, open(args.save_curves, "w"))
@@ -987,33 +1096,48 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_f, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": workload, "n": n, "m": c.m, "nq_per_gpu": nq, "K": K,
-                       "M": c.M, "deg0": info["deg0"], "r": c.r, "ef_finger": ef_f,
-                       "ef_plain": ef_p,
+                       "M": c.M, "deg0": info["deg0"], "r": c.r, "ef_finger": efs["finger"],
+                       "ef_plain": efs["plain"], "ef_finger_f32": efs["finger_f32"],
+                       "finger": "FP16 unit residual codes (tensor-core matrix-vector "
+                                 "estimate, FP32 accumulation), FP32 vectors and distances",
                        "graph": f"GPU {'single-layer' if args.flat else 'HNSW'}, insertion "
                                 f"order, {cands} exact candidates + heuristic selection",
-                       "l2": "inputs larger than L2 (index ~9 GB), no flush",
+                       "ef_search": "coarse grid, then the smallest ef on a step-2 grid "
+                                    "reaching recall 0.95",
+                       "l2": "inputs larger than L2 (index ~14 GB), no flush",
                        "parallelism": f"replicas x{ws}, {nq} distinct queries per rank"},
-            "recall_finger": rec_f, "recall_plain": rec_p, "plain_qps": plain_qps,
+            "recall_finger": recs["finger"], "recall_plain": recs["plain"],
+            "recall_finger_f32": recs["finger_f32"], "plain_qps": plain_qps,
             "finger_over_plain": value / plain_qps,
+            "finger_f32_qps": res["finger_f32"]["qps"],
+            "finger_f32_over_plain": res["finger_f32"]["qps"] / plain_qps,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "peak_kind": peak_kind, "kernel": "k_search<FINGER> (search_m1.cu)",
+                         "peak_kind": peak_kind,
+                         "kernel": "k_search<FINGER_F16> (search_f16_k4.cu)",
                          "algorithmic_bytes_per_launch": algo,
-                         "algorithmic_bytes_sector32": algo32, "kernel_ms": kern_ms},
+                         "algorithmic_bytes_sector32": algo32, "kernel_ms": kern_ms,
+                         "code_bytes_per_launch": st["code_bytes"]},
+            "roofline_plain": {"achieved": algo_p / (kern_p / 1000) / 1e9, "peak": peak,
+                               "frac": algo_p / (kern_p / 1000) / 1e9 / peak,
+                               "algorithmic_bytes_per_launch": algo_p, "kernel_ms": kern_p},
+            "roofline_finger_f32": {"achieved": algo_32 / (kern_32 / 1000) / 1e9, "peak": peak,
+                                    "frac": algo_32 / (kern_32 / 1000) / 1e9 / peak,
+                                    "algorithmic_bytes_per_launch": algo_32,
+                                    "kernel_ms": kern_32},
             "qps_at_recall_interp": {k: qps_at(v) for k, v in curves.items()},
             "recall_tie_aware": tie,
             "cpu_baseline": cpu,
             "e2e": {"value": ws * nq / (e2e_ms / 1000), "unit": "queries/s",
                     "h2d_bytes_per_step": nq * c.m * 4, "d2h_bytes_per_step": nq * K * 12,
                     "recall": e2e_rec},
-            "clocks": ck, "gpu_launches": args.steps,
+            "clocks": res["finger"]["clocks"], "gpu_launches": args.steps,
             "counters_per_query": {k: v / nq for k, v in csum.items()},
             "setup_s": {"total": t_setup, "graph": t_graph, "tables": t_tables},
             "curves": {k: [[e, round(r_, 4), round(v_, 1)] for e, r_, v_ in pts]
                        for k, pts in curves.items()},
         }
         print(json.dumps(line), flush=True)
-    ix.close()
     if ws > 1:
         torch.distributed.destroy_process_group()
     return 0

@@ -395,6 +395,9 @@ typedef struct {
     double build_ms;        /* wall time of the last table build */
     double corr;            /* correlation of X and Y over the drawn pairs
                                (Supplementary E), NaN before a build */
+    int64_t code_bytes;     /* bytes of FP16 code blocks read by FINGER_MODE_FINGER_F16
+                               searches (a block's second half only for centres
+                               whose degree needs it) */
 } finger_stats;
 
 /* Synchronise the index's device and return the latched kernel status. */

@@ -69,7 +69,8 @@ class Stats(ctypes.Structure):
                 ("device_error", ctypes.c_int32), ("mu", ctypes.c_double),
                 ("sigma", ctypes.c_double), ("mu_hat", ctypes.c_double),
                 ("sigma_hat", ctypes.c_double), ("eps", ctypes.c_double),
-                ("build_ms", ctypes.c_double), ("corr", ctypes.c_double)]
+                ("build_ms", ctypes.c_double), ("corr", ctypes.c_double),
+                ("code_bytes", ctypes.c_int64)]
 
 
 # name -> (restype, argtypes); every symbol include/finger.h declares

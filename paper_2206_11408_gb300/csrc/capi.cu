@@ -377,7 +377,7 @@ finger_status finger_index_create(int device, int64_t n, int m, const float* vec
     if (st == FINGER_OK) st = dmalloc(&ix->xnorm2, (size_t)n);
     if (st == FINGER_OK) st = dmalloc(&ix->work, 4);
     if (st == FINGER_OK) st = dmalloc(&ix->err, 1);
-    if (st == FINGER_OK) st = dmalloc(&ix->cnt, 8);
+    if (st == FINGER_OK) st = dmalloc(&ix->cnt, 16);
     if (st != FINGER_OK) {
         finger_index_free(ix);
         return st;
@@ -386,7 +386,7 @@ finger_status finger_index_create(int device, int64_t n, int m, const float* vec
         cudaMemcpy2D(ix->X, sizeof(float) * ix->m_pad, vectors_host, sizeof(float) * m,
                      sizeof(float) * m, (size_t)n, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(ix->err, 0, sizeof(int)) != cudaSuccess ||
-        cudaMemset(ix->cnt, 0, sizeof(unsigned long long) * 8) != cudaSuccess ||
+        cudaMemset(ix->cnt, 0, sizeof(unsigned long long) * 16) != cudaSuccess ||
         launch_xnorm2(reinterpret_cast<const float4*>(ix->X), n, ix->m4, ix->xnorm2, 0) !=
             cudaSuccess ||
         cudaDeviceSynchronize() != cudaSuccess) {
@@ -720,7 +720,7 @@ finger_status finger_get_stats(finger_index* ix, finger_stats* out) {
         cudaGetLastError();
         return FINGER_ERR_CUDA;
     }
-    unsigned long long c[8];
+    unsigned long long c[9];
     int e = 0;
     CUDA_OK(cudaMemcpy(c, ix->cnt, sizeof(c), cudaMemcpyDeviceToHost));
     CUDA_OK(cudaMemcpy(&e, ix->err, sizeof(int), cudaMemcpyDeviceToHost));
@@ -734,13 +734,15 @@ finger_status finger_get_stats(finger_index* ix, finger_stats* out) {
     out->eps = ix->stats[4];
     out->build_ms = ix->build_ms;
     out->corr = ix->corr;
+    // halves of FP16 code blocks read x bytes of a half (tiles x k steps x 512)
+    out->code_bytes = (int64_t)c[8] * (ix->deg0 > 32 ? 2 : 1) * ix->hks * 512;
     return FINGER_OK;
 }
 
 finger_status finger_reset_stats(finger_index* ix) {
     if (!ix) return FINGER_ERR_INVALID_ARG;
     DeviceGuard g(ix->device);
-    CUDA_OK(cudaMemset(ix->cnt, 0, sizeof(unsigned long long) * 8));
+    CUDA_OK(cudaMemset(ix->cnt, 0, sizeof(unsigned long long) * 16));
     CUDA_OK(cudaMemset(ix->err, 0, sizeof(int)));
     ix->searches = 0;
     return FINGER_OK;

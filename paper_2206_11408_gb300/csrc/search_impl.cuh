@@ -723,7 +723,7 @@ __global__ void __launch_bounds__(128, OCC) k_search(DevIndex ix, SearchArgs a) 
             __syncwarp();
         }
         int c_exp = 0, c_exa = 0, c_est = 0, c_skip = 0, c_exact = 0, c_adm = 0, c_up = 0,
-            c_gath = 0;
+            c_gath = 0, c_half = 0;   // c_half: code-block halves read (FP16 codes)
         bool fail = false;
 
         // ---- a2: greedy descent through levels maxlevel..1 (exact distances)
@@ -849,6 +849,7 @@ __global__ void __launch_bounds__(128, OCC) k_search(DevIndex ix, SearchArgs a) 
                                              : make_float2(0.f, 0.f);
                     }
                     wb_load<WKS, WNT>(ix, c, 0, cfull, hx, lane);
+                    c_half += cfull ? 2 : 1;
                     // per-centre prep (Sec. 3.2 identity for q^T c, Supplementary G),
                     // then the product: the codes arrive with the adjacency row
                     // and are consumed before the visited test
@@ -1381,6 +1382,7 @@ __global__ void __launch_bounds__(128, OCC) k_search(DevIndex ix, SearchArgs a) 
             atomicAdd(g + 5, (unsigned long long)c_adm);
             atomicAdd(g + 6, (unsigned long long)c_up);
             atomicAdd(g + 7, (unsigned long long)c_gath);
+            if (WB) atomicAdd(g + 8, (unsigned long long)c_half);
             if (a.cnt_q) {
                 int32_t* cq = a.cnt_q + (size_t)qi * 8;
                 cq[0] = c_exp;
