@@ -350,7 +350,7 @@ def run_reference(args):
 
 # ------------------------------------------------------------ extension legs
 
-def _ext_setup(args, cfg, build_lp=False):
+def _ext_setup(args, cfg, build_lp=False, half_codes=False):
     import torch
 
     import paper_2206_11408_gb300 as fg
@@ -366,7 +366,7 @@ def _ext_setup(args, cfg, build_lp=False):
     torch.cuda.synchronize()
     tg = time.perf_counter() - tg
     tt = time.perf_counter()
-    ix.build_tables(c.r, 4000 + cfg, build_lp=build_lp)
+    ix.build_tables(c.r, 4000 + cfg, build_lp=build_lp, half_codes=half_codes)
     torch.cuda.synchronize()
     tt = time.perf_counter() - tt
     q = torch.from_numpy(Q).cuda()
@@ -468,10 +468,11 @@ def leg_lp(args):
     FINGER vs plain, QPS at recall@10 0.95, plus the distance error of the
     returned (FP32 re-ranked) distances and of the BF16 rows vs FP64."""
     import paper_2206_11408_gb300 as fg
-    c, n, nq, X, Q, ix, q, setup = _ext_setup(args, 3, build_lp=True)
+    c, n, nq, X, Q, ix, q, setup = _ext_setup(args, 3, build_lp=True, half_codes=True)
     gt_ids, _ = ix.knn(q, c.K)
     gt = gt_ids.cpu().numpy()
-    modes = {"plain": fg.MODE_PLAIN, "finger": fg.MODE_FINGER, "finger_lp": fg.MODE_FINGER_LP}
+    modes = {"plain": fg.MODE_PLAIN, "finger": fg.MODE_FINGER, "finger_f16": fg.MODE_FINGER_F16,
+             "finger_lp": fg.MODE_FINGER_LP}
     curves, choice = _sweep(ix, q, gt, c.K, modes, c.ef_grid, nq)
     res = {}
     ck = None
@@ -495,7 +496,9 @@ def leg_lp(args):
              "roofline": roof, "counters_per_query": cpq,
              "qps_at_recall_interp": {k: qps_at(v) for k, v in curves.items()},
              "finger_qps": res["finger"][0], "plain_qps": res["plain"][0],
+             "finger_f16_qps": res["finger_f16"][0],
              "lp_over_plain": res["finger_lp"][0] / res["plain"][0],
+             "f16_over_plain": res["finger_f16"][0] / res["plain"][0],
              "ef": {k: v[0] for k, v in choice.items()},
              "recall": {k: v[1] for k, v in choice.items()},
              "distance_error_vs_fp64": {"returned_fp32": {"max": float(rel32.max()),

@@ -13,11 +13,13 @@
 namespace fg {
 cudaError_t launch_mode0(const DevIndex&, const SearchArgs&, const SearchPlan&, cudaStream_t);
 cudaError_t launch_mode1(const DevIndex&, const SearchArgs&, const SearchPlan&, cudaStream_t);
-cudaError_t launch_mode2(const DevIndex&, const SearchArgs&, const SearchPlan&, cudaStream_t);
+cudaError_t launch_lp_k2(const DevIndex&, const SearchArgs&, const SearchPlan&, cudaStream_t);
+cudaError_t launch_lp_k4(const DevIndex&, const SearchArgs&, const SearchPlan&, cudaStream_t);
 cudaError_t launch_mode3(const DevIndex&, const SearchArgs&, const SearchPlan&, cudaStream_t);
 cudaError_t occupancy_mode0(const SearchPlan&, int*);
 cudaError_t occupancy_mode1(const SearchPlan&, int*);
-cudaError_t occupancy_mode2(const SearchPlan&, int*);
+cudaError_t occupancy_lp_k2(const SearchPlan&, int*);
+cudaError_t occupancy_lp_k4(const SearchPlan&, int*);
 cudaError_t occupancy_mode3(const SearchPlan&, int*);
 cudaError_t launch_f16_k2(const DevIndex&, const SearchArgs&, const SearchPlan&, cudaStream_t);
 cudaError_t launch_f16_k4(const DevIndex&, const SearchArgs&, const SearchPlan&, cudaStream_t);
@@ -49,7 +51,8 @@ void choose_groups(int nchunks, int* G, int* VPL) {
 // the FP16-code mode reads it in chunks of 8 per code chunk, zero padded
 int search_uq_len(const DevIndex& ix, int mode) {
     const int r_pad = ix.r4 * 4;
-    return mode == FINGER_MODE_FINGER_F16 ? std::max(r_pad, 16 * ix.hks) : r_pad;
+    return mode == FINGER_MODE_FINGER_F16 || mode == FINGER_MODE_FINGER_LP
+               ? std::max(r_pad, 16 * ix.hks) : r_pad;
 }
 
 int search_smem_per_warp(const DevIndex& ix, int mode, int ef_cap, int H, int NPL, int h16) {
@@ -70,7 +73,7 @@ cudaError_t launch_search(const DevIndex& ix, const SearchArgs& a, const SearchP
     switch (p.mode) {
         case 0: return launch_mode0(ix, a, p, s);
         case 1: return launch_mode1(ix, a, p, s);
-        case 2: return launch_mode2(ix, a, p, s);
+        case 2: return ix.hks == 2 ? launch_lp_k2(ix, a, p, s) : launch_lp_k4(ix, a, p, s);
         case 3: return launch_mode3(ix, a, p, s);
         case 4: return ix.hks == 2 ? launch_f16_k2(ix, a, p, s) : launch_f16_k4(ix, a, p, s);
         case MODE_HARVEST: return launch_mode_harvest(ix, a, p, s);
@@ -82,7 +85,7 @@ cudaError_t search_occupancy(const DevIndex& ix, const SearchPlan& p, int* bps) 
     switch (p.mode) {
         case 0: return occupancy_mode0(p, bps);
         case 1: return occupancy_mode1(p, bps);
-        case 2: return occupancy_mode2(p, bps);
+        case 2: return ix.hks == 2 ? occupancy_lp_k2(p, bps) : occupancy_lp_k4(p, bps);
         case 3: return occupancy_mode3(p, bps);
         case 4: return ix.hks == 2 ? occupancy_f16_k2(p, bps) : occupancy_f16_k4(p, bps);
         case MODE_HARVEST: return occupancy_mode_harvest(p, bps);
@@ -113,7 +116,6 @@ fg::DevIndex make_dev(const finger_index* ix) {
     d.up_adj = ix->up_adj;
     d.r = ix->r;
     d.r4 = ix->r_pad / 4;
-    d.r16 = ix->r16;
     d.P = reinterpret_cast<const float4*>(ix->P);
     d.Pc = reinterpret_cast<const float4*>(ix->Pc);
     d.edge_u = reinterpret_cast<const float4*>(ix->edge_u);
@@ -254,7 +256,7 @@ finger_status ensure_scratch(finger_index* ix, int64_t slots) {
 finger_status check_mode_ready(const finger_index* ix, int mode) {
     if (!ix->adj0) return FINGER_ERR_NOT_BUILT;
     if (mode != FINGER_MODE_PLAIN && !ix->edge_u) return FINGER_ERR_NOT_BUILT;
-    if (mode == FINGER_MODE_FINGER_LP && !ix->edge_q) return FINGER_ERR_NOT_BUILT;
+    if (mode == FINGER_MODE_FINGER_LP && (!ix->edge_q || !ix->adj_t)) return FINGER_ERR_NOT_BUILT;
     if (mode == FINGER_MODE_FINGER_F16 && (!ix->edge_h || !ix->adj_t)) return FINGER_ERR_NOT_BUILT;
     if (mode == FINGER_MODE_FINGER_MLP && !ix->has_mlp) return FINGER_ERR_NOT_BUILT;
     return FINGER_OK;
@@ -350,8 +352,10 @@ const char* finger_status_str(finger_status s) {
 int64_t finger_table_bytes(int64_t n, int deg0, int r, int lp) {
     if (n < 0 || deg0 < 0 || r < 0) return -1;
     if (!lp) return (int64_t)(r + 2) * n * deg0 * (int64_t)sizeof(float);
-    const int64_t r16 = ((r + 3) / 4 * 4 + 15) / 16 * 16;
-    return (r16 + 8) * n * deg0;
+    // FP8 codes: per node 32 (deg0 <= 32) or 64 slots x 32 or 64 codes, plus
+    // the FP32 edge scalars of every slot
+    const int64_t slots = deg0 > 32 ? 64 : 32, codes = r > 32 ? 64 : 32;
+    return n * slots * codes + 8 * n * deg0;
 }
 
 finger_status finger_index_create(int device, int64_t n, int m, const float* vectors_host,
@@ -427,7 +431,7 @@ static void drop_tables(finger_index* ix) {
     ix->hks = 0;
     ix->W1f = ix->W2f = nullptr;
     ix->w3 = ix->b1 = ix->b2 = nullptr;
-    ix->r = ix->r_pad = ix->r16 = 0;
+    ix->r = ix->r_pad = 0;
     ix->has_mlp = 0;
     ix->h_mlp.clear();
     ix->tuned.clear();

@@ -39,7 +39,7 @@ struct DevIndex {
     const int64_t* up_off;  // n
     const uint32_t* up_adj; // up_rows x Mup
     // FINGER tables
-    int r, r4, r16;         // rank; float4 chunks of r_pad; uint4 chunks of the FP8 codes
+    int r, r4;              // rank; float4 chunks of r_pad
     const float4* P;        // r_pad x m4
     const float4* Pc;       // n x r4
     const float4* edge_u;   // (n*deg0) x r4
@@ -47,7 +47,10 @@ struct DevIndex {
     float alpha, beta;      // t = t_hat * alpha + beta
     // reduced precision
     const uint4* Xh;        // n x m8 (BF16)
-    const uint4* edge_q;    // (n*deg0) x r16 FP8-e4m3 codes of edge_u * code_scale
+    // FP8-e4m3 codes of edge_u * code_scale (LP mode) in the same fragment order
+    // as edge_h, two k steps per 16 bytes: per node 2 NPL tiles x hks / 2 x 32
+    // lanes x 16 bytes
+    const uint4* edge_q;
     float code_inv;         // 1 / code_scale
     // FP16 unit residual codes (mode FINGER_F16) in m16n8k16 A-fragment order:
     // per node 2 NPL tiles of 16 slots x hks k steps x 32 lanes x 16 bytes
@@ -103,6 +106,9 @@ constexpr int MODE_HARVEST = 5;     // FINGER traversal that records predictor t
 // kernel instances of the public mode FINGER_F16 by k steps of the code table
 constexpr int MODE_F16_K2 = 6;      // r <= 32
 constexpr int MODE_F16_K4 = 7;      // r <= 64
+// kernel instances of the public mode FINGER_LP (FP8 codes) by k steps
+constexpr int MODE_LP_K2 = 8;
+constexpr int MODE_LP_K4 = 9;
 
 struct SearchPlan {
     int mode;
@@ -180,8 +186,7 @@ struct finger_index {
     int eig_spn = 0;
     // LP tables
     __nv_bfloat16* Xh = nullptr;
-    uint8_t* edge_q = nullptr;
-    int r16 = 0;
+    uint8_t* edge_q = nullptr;   // fragment-order FP8 codes (see DevIndex)
     // FP16 codes (fragment order, see DevIndex)
     uint16_t* edge_h = nullptr;
     int hks = 0;

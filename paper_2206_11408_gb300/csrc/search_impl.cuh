@@ -335,53 +335,29 @@ __device__ __forceinline__ int visit16(uint16_t* hash, int logNB, uint32_t id, b
 }
 
 // t_hat for one edge: r-dot of the stored unit residual projection with uq
-template <bool LP>
+// (harvest of the learned predictor's training data)
 __device__ __forceinline__ float edge_cos(const DevIndex& ix, size_t e, const float* uq) {
     float acc = 0.f;
-    if constexpr (!LP) {
-        const float4* u = ix.edge_u + e * ix.r4;
-        const float4* v = reinterpret_cast<const float4*>(uq);
-        // r <= 64: two halves of up to eight 16-byte loads, each half issued
-        // before its products (same summation order as a plain loop)
+    const float4* u = ix.edge_u + e * ix.r4;
+    const float4* v = reinterpret_cast<const float4*>(uq);
+    // r <= 64: two halves of up to eight 16-byte loads, each half issued
+    // before its products (same summation order as a plain loop)
 #pragma unroll
-        for (int h = 0; h < 16; h += 8) {
-            float4 x[8];
+    for (int h = 0; h < 16; h += 8) {
+        float4 x[8];
 #pragma unroll
-            for (int k = 0; k < 8; ++k)
-                if (h + k < ix.r4) x[k] = __ldg(u + h + k);
+        for (int k = 0; k < 8; ++k)
+            if (h + k < ix.r4) x[k] = __ldg(u + h + k);
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                if (h + k < ix.r4) {
-                    const float4 y = v[h + k];
-                    acc = fmaf(x[k].x, y.x, acc);
-                    acc = fmaf(x[k].y, y.y, acc);
-                    acc = fmaf(x[k].z, y.z, acc);
-                    acc = fmaf(x[k].w, y.w, acc);
-                }
+        for (int k = 0; k < 8; ++k) {
+            if (h + k < ix.r4) {
+                const float4 y = v[h + k];
+                acc = fmaf(x[k].x, y.x, acc);
+                acc = fmaf(x[k].y, y.y, acc);
+                acc = fmaf(x[k].z, y.z, acc);
+                acc = fmaf(x[k].w, y.w, acc);
             }
         }
-    } else {
-        const uint4* u = ix.edge_q + e * ix.r16;
-        for (int k = 0; k < ix.r16; ++k) {
-            const uint4 x = __ldg(u + k);
-            const uint32_t w[4] = {x.x, x.y, x.z, x.w};
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const __half2_raw lo = __nv_cvt_fp8x2_to_halfraw2(
-                    (__nv_fp8x2_storage_t)(w[i] & 0xFFFFu), __NV_E4M3);
-                const __half2_raw hi = __nv_cvt_fp8x2_to_halfraw2(
-                    (__nv_fp8x2_storage_t)(w[i] >> 16), __NV_E4M3);
-                const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&lo));
-                const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&hi));
-                const int k0 = k * 16 + i * 4;
-                const int rp = ix.r4 * 4;
-                acc = fmaf(a.x, k0 + 0 < rp ? uq[k0 + 0] : 0.f, acc);
-                acc = fmaf(a.y, k0 + 1 < rp ? uq[k0 + 1] : 0.f, acc);
-                acc = fmaf(b.x, k0 + 2 < rp ? uq[k0 + 2] : 0.f, acc);
-                acc = fmaf(b.y, k0 + 3 < rp ? uq[k0 + 3] : 0.f, acc);
-            }
-        }
-        acc *= ix.code_inv;
     }
     return acc;
 }
@@ -400,7 +376,10 @@ __device__ __forceinline__ float edge_cos(const DevIndex& ix, size_t e, const fl
 // (hi = fp16(u), lo = fp16(u - hi)) for the even and odd columns of B, so
 // columns 2t and 2t+1 of the product sum to A u_q with u_q kept to about 22
 // bits; the codes are exact FP16 values.  KS and NT are compile-time, so the
-// whole product is straight-line code.
+// whole product is straight-line code.  The reduced-precision mode (LP) keeps
+// the same fragments as FP8-e4m3 codes of 256 u: one 16-byte load per lane
+// holds two k steps of a tile, and each FP8 pair becomes one FP16 pair of the A
+// operand by a single conversion (e4m3 values are exact in FP16).
 __device__ __forceinline__ void mma_f16(float* d, const uint4& a, uint32_t b0, uint32_t b1) {
     asm volatile(
         "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
@@ -418,9 +397,21 @@ __device__ __forceinline__ uint32_t pack_half2(float lo, float hi) {
 // The second half of the block (tiles NT/2 ..) holds slots 16 NT/2 .. and is
 // all zero rows for a centre of at most that degree; it is read only when
 // `full` (the centre's tag) says the centre has more neighbours, else zeros.
-template <int KS, int NT>
+template <int KS, int NT, bool W8 = false>
 __device__ __forceinline__ void wb_load(const DevIndex& ix, uint32_t c, int t0, bool full,
                                         uint4 (&hx)[8], int lane) {
+    if constexpr (W8) {   // FP8 storage: KS / 2 loads per tile, every tile in one round
+        constexpr int KP = KS / 2;
+        const uint4* base = ix.edge_q + (size_t)c * NT * KP * 32 + lane;
+#pragma unroll
+        for (int T = 0; T < NT; ++T)
+#pragma unroll
+            for (int p = 0; p < KP; ++p) {
+                const bool need = T < NT / 2 || full;
+                hx[T * KP + p] = need ? __ldg(base + (T * KP + p) * 32) : make_uint4(0u, 0u, 0u, 0u);
+            }
+        return;
+    }
     constexpr int TPR = NT * KS <= 8 ? NT : 8 / KS;
     const uint4* base = ix.edge_h + ((size_t)c * NT + t0) * KS * 32 + lane;
 #pragma unroll
@@ -450,9 +441,41 @@ __device__ __forceinline__ void wb_bfrag_store(uint32_t* bsm, float u0, float u1
 
 // t_hat of rows 16(t0+T)+g (v[2(t0+T)]) and +8 (v[2(t0+T)+1]) for the round's
 // tiles; k step outer, so each code register dies at its MMA.
-template <int KS, int NT>
+__device__ __forceinline__ uint32_t e4m3x2_to_half2(uint32_t pair) {
+    const __half2_raw h = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)pair, __NV_E4M3);
+    return (uint32_t)h.x | ((uint32_t)h.y << 16);
+}
+
+// the A fragment of k step (2p + h) from a 16-byte FP8 load (h: which half)
+__device__ __forceinline__ uint4 e4m3_frag(const uint4& x, int h) {
+    const uint32_t lo = h ? x.z : x.x, hi = h ? x.w : x.y;
+    return make_uint4(e4m3x2_to_half2(lo & 0xFFFFu), e4m3x2_to_half2(lo >> 16),
+                      e4m3x2_to_half2(hi & 0xFFFFu), e4m3x2_to_half2(hi >> 16));
+}
+
+template <int KS, int NT, bool W8 = false>
 __device__ __forceinline__ void wb_mma(const uint4 (&hx)[8], const uint32_t* bsm, int t0,
                                        float (&v)[8], int lane) {
+    if constexpr (W8) {   // every tile, FP8 fragments converted to FP16 in registers
+        constexpr int KP = KS / 2;
+        const uint2* bf = reinterpret_cast<const uint2*>(bsm) + ((lane >> 2) & 1) * 4 + (lane & 3);
+        float acc[NT][4];
+#pragma unroll
+        for (int T = 0; T < NT; ++T) acc[T][0] = acc[T][1] = acc[T][2] = acc[T][3] = 0.f;
+#pragma unroll
+        for (int ks = 0; ks < KS; ++ks) {
+            const uint2 b = bf[ks * 8];
+#pragma unroll
+            for (int T = 0; T < NT; ++T)
+                mma_f16(acc[T], e4m3_frag(hx[T * KP + ks / 2], ks & 1), b.x, b.y);
+        }
+#pragma unroll
+        for (int T = 0; T < NT; ++T) {
+            v[2 * T] = acc[T][0] + acc[T][1];
+            v[2 * T + 1] = acc[T][2] + acc[T][3];
+        }
+        return;
+    }
     constexpr int TPR = NT * KS <= 8 ? NT : 8 / KS;
     const uint2* bf = reinterpret_cast<const uint2*>(bsm) + ((lane >> 2) & 1) * 4 + (lane & 3);
     float acc[TPR][4];
@@ -631,13 +654,13 @@ __device__ __forceinline__ void mlp_tile(const __nv_bfloat16* xt, int kp, const 
 
 template <int MODE, int G, int VPL, int NPL, int OCC>
 __global__ void __launch_bounds__(128, OCC) k_search(DevIndex ix, SearchArgs a) {
-    constexpr bool LP = MODE == FINGER_MODE_FINGER_LP;
+    constexpr bool LP = MODE == MODE_LP_K2 || MODE == MODE_LP_K4;   // BF16 rows, FP8 codes
     constexpr bool EST = MODE != FINGER_MODE_PLAIN;
     constexpr bool MLP = MODE == FINGER_MODE_FINGER_MLP;
     constexpr bool HARV = MODE == MODE_HARVEST;
-    // FP16 codes, product on the tensor cores (public mode FINGER_F16), k steps
-    constexpr bool WB = MODE == MODE_F16_K2 || MODE == MODE_F16_K4;
-    constexpr int WKS = MODE == MODE_F16_K2 ? 2 : 4;
+    // FP16 (FINGER_F16) or FP8 (LP) codes, product on the tensor cores; k steps
+    constexpr bool WB = MODE == MODE_F16_K2 || MODE == MODE_F16_K4 || LP;
+    constexpr int WKS = MODE == MODE_F16_K2 || MODE == MODE_LP_K2 ? 2 : 4;
     constexpr int WNT = 2 * NPL;                            // tiles per node
     // ids in T: FP16-code mode ids carry the tag TAG (the node has more than
     // 16 NPL neighbours, so its code block's second half is needed) below EXP
@@ -848,7 +871,7 @@ __global__ void __launch_bounds__(128, OCC) k_search(DevIndex ix, SearchArgs a) 
                         scw[s] = j < ix.deg0 ? __ldg(ix.edge_s + (size_t)c * ix.deg0 + j)
                                              : make_float2(0.f, 0.f);
                     }
-                    wb_load<WKS, WNT>(ix, c, 0, cfull, hx, lane);
+                    wb_load<WKS, WNT, LP>(ix, c, 0, cfull, hx, lane);
                     c_half += cfull ? 2 : 1;
                     // per-centre prep (Sec. 3.2 identity for q^T c, Supplementary G),
                     // then the product: the codes arrive with the adjacency row
@@ -869,14 +892,18 @@ __global__ void __launch_bounds__(128, OCC) k_search(DevIndex ix, SearchArgs a) 
                     wb_bfrag_store(bsm, u0 * inv, u1 * inv, WKS, lane);
                     __syncwarp();
                     float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-                    wb_mma<WKS, WNT>(hx, bsm, 0, v, lane);
-                    if constexpr (WNT * WKS > 8) {   // second round: tiles 2, 3
+                    wb_mma<WKS, WNT, LP>(hx, bsm, 0, v, lane);
+                    if constexpr (!LP && WNT * WKS > 8) {   // second round: tiles 2, 3
                         if (cfull) {
                             wb_load<WKS, WNT>(ix, c, 2, true, hx, lane);
                             wb_mma<WKS, WNT>(hx, bsm, 2, v, lane);
                         }
                     }
                     wb_route<NPL>(v, th, lane);
+                    if constexpr (LP) {   // the FP8 codes hold 256 u
+#pragma unroll
+                        for (int s = 0; s < NPL; ++s) th[s] *= ix.code_inv;
+                    }
                 }
             }
             // In FINGER mode a bitmap test-and-set is resolved only after the
@@ -972,7 +999,7 @@ __global__ void __launch_bounds__(128, OCC) k_search(DevIndex ix, SearchArgs a) 
                             const float th =
                                 pos >= 0 ? features_row(ix, e, uq, sc, cc, ac, qres_n, qn2,
                                                         a.hv_feat + pos * (ix.r + 4))
-                                         : edge_cos<false>(ix, e, uq);
+                                         : edge_cos(ix, e, uq);
                             tr[s] = fmaf(th, ix.alpha, ix.beta);
                         }
                     }
@@ -1111,7 +1138,7 @@ __global__ void __launch_bounds__(128, OCC) k_search(DevIndex ix, SearchArgs a) 
                     } else if constexpr (HARV) {
                         t = tr[s];
                     } else {
-                        t = fmaf(edge_cos<LP>(ix, e, uq), ix.alpha, ix.beta);
+                        t = fmaf(edge_cos(ix, e, uq), ix.alpha, ix.beta);
                     }
                     const float dd = ac - sc.y;
                     est = dd * dd * cc + qres2 + sc.x * sc.x - 2.f * qres_n * sc.x * t;
@@ -1405,6 +1432,8 @@ __global__ void __launch_bounds__(128, OCC) k_search(DevIndex ix, SearchArgs a) 
 // for the plain mode.  The FINGER modes keep their gathers in flight in
 // registers and are fastest at 6 (the FP16-code mode measured slower at 7,
 // where it spills); plain search at 8.
+#define LP_MODE(m) ((m) == MODE_LP_K2 || (m) == MODE_LP_K4)
+
 template <int MODE, int OCC>
 cudaError_t launch_occ(const DevIndex& ix, const SearchArgs& a, const SearchPlan& p,
                        cudaStream_t s) {
@@ -1454,7 +1483,7 @@ cudaError_t launch_mode(const DevIndex& ix, const SearchArgs& a, const SearchPla
     if constexpr (MODE == FINGER_MODE_PLAIN)
         if (p.occ == 8) return launch_occ<MODE, 8>(ix, a, p, s);
     if constexpr (MODE == FINGER_MODE_PLAIN || MODE == FINGER_MODE_FINGER ||
-                  MODE == FINGER_MODE_FINGER_LP || MODE == MODE_F16_K2 || MODE == MODE_F16_K4)
+                  LP_MODE(MODE) || MODE == MODE_F16_K2 || MODE == MODE_F16_K4)
         if (p.occ == 6) return launch_occ<MODE, 6>(ix, a, p, s);
     if (p.occ != 5) return cudaErrorInvalidValue;
     return launch_occ<MODE, 5>(ix, a, p, s);
@@ -1467,7 +1496,7 @@ cudaError_t occupancy_mode(const SearchPlan& p, int* blocks) {
     if constexpr (MODE == FINGER_MODE_PLAIN)
         if (p.occ == 8) return occupancy_occ<MODE, 8>(p, blocks);
     if constexpr (MODE == FINGER_MODE_PLAIN || MODE == FINGER_MODE_FINGER ||
-                  MODE == FINGER_MODE_FINGER_LP || MODE == MODE_F16_K2 || MODE == MODE_F16_K4)
+                  LP_MODE(MODE) || MODE == MODE_F16_K2 || MODE == MODE_F16_K4)
         if (p.occ == 6) return occupancy_occ<MODE, 6>(p, blocks);
     if (p.occ != 5) {
         *blocks = 0;

@@ -14,7 +14,7 @@
 //   k_pair_cos    X = cos(d_res, d'_res) (explicit residuals), Y = u_d . u_d'
 //   k_sum*        deterministic block reductions for mu, sigma, mu_hat,
 //                 sigma_hat (standard deviations, 1/N) and eps
-//   k_lp_codes    FP8-e4m3 codes of u * code_scale (reduced-precision tables)
+//   k_lp_codes    FP8-e4m3 codes of u * code_scale in fragment order (reduced precision)
 #include <cooperative_groups.h>
 #include <math.h>
 
@@ -589,14 +589,33 @@ __global__ void k_sum_final(const double* part, int nb, double* out) {
     out[2] = c;
 }
 
-__global__ void k_lp_codes(const float* edge_u, int64_t ne, int r_pad, int r16b, float scale,
-                           uint8_t* out) {
+// FP8-e4m3 codes of scale * u in the FP16 codes' fragment order, two k steps
+// per 16 bytes: thread i writes lane l = i % 32 of (node c, tile T, k pair p) =
+// i / 32: bytes 0..7 for k step 2p, 8..15 for 2p + 1, each as rows 16T + g and
+// 16T + g + 8 (g = l / 4) at codes 16ks + 2t, +1, +8, +9 (t = l % 4).
+__global__ void k_lp_codes(const float* edge_u, int64_t n, int deg0, int r_pad, int tiles,
+                           int kp_n, float scale, uint4* out) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= ne * r16b) return;
-    const int64_t e = i / r16b;
-    const int k = (int)(i % r16b);
-    const float v = k < r_pad ? edge_u[e * r_pad + k] * scale : 0.f;
-    out[i] = (uint8_t)__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
+    if (i >= n * tiles * kp_n * 32) return;
+    const int l = (int)(i & 31);
+    int64_t f = i >> 5;
+    const int kp = (int)(f % kp_n);
+    f /= kp_n;
+    const int T = (int)(f % tiles);
+    const int64_t c = f / tiles;
+    const int g = l >> 2, t = l & 3;
+    auto code = [&](int row, int k) -> uint32_t {
+        const float v = row < deg0 && k < r_pad ? edge_u[((size_t)c * deg0 + row) * r_pad + k] * scale : 0.f;
+        return (uint32_t)__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
+    };
+    uint32_t w[4];
+    for (int h = 0; h < 2; ++h) {
+        const int ks = 2 * kp + h;
+        const int r0 = 16 * T + g, r1 = r0 + 8, k0 = 16 * ks + 2 * t, k1 = k0 + 8;
+        w[2 * h] = code(r0, k0) | code(r0, k0 + 1) << 8 | code(r1, k0) << 16 | code(r1, k0 + 1) << 24;
+        w[2 * h + 1] = code(r0, k1) | code(r0, k1 + 1) << 8 | code(r1, k1) << 16 | code(r1, k1 + 1) << 24;
+    }
+    out[i] = make_uint4(w[0], w[1], w[2], w[3]);
 }
 
 // FP16 codes in m16n8k16 A-fragment order: thread i writes the 16 bytes of
@@ -670,66 +689,89 @@ cudaError_t launch_to_bf16(const float* X, int64_t n, int m_pad, int m8, __nv_bf
 
 }  // namespace fg
 
-// BF16 rows and FP8-e4m3 residual codes from the FP32 tables (mode LP)
+// The modes that read a centre's whole code block (FP16 and LP) take its layer-0
+// adjacency from a tagged copy: a neighbour's id has bit 30 set when its
+// degree exceeds 16 (32 when deg0 > 32), i.e. when the second half of its code
+// block holds rows; ids must stay below 2^30.  Built once for both modes.
+cudaError_t build_tagged_adj(finger_index* ix) {
+    using namespace fg;
+    if (ix->adj_t) return cudaSuccess;
+    if (ix->n >= (int64_t(1) << 30)) return cudaErrorInvalidValue;
+    const int tiles = ix->deg0 > 32 ? 4 : 2;
+    const int64_t ne = ix->n * ix->deg0;
+    int32_t* deg = nullptr;
+    cudaError_t e = cudaMalloc(&ix->adj_t, sizeof(uint32_t) * (size_t)ne + 16);
+    if (e == cudaSuccess) e = cudaMalloc(&deg, sizeof(int32_t) * (size_t)ix->n);
+    if (e != cudaSuccess) {
+        cudaFree(deg);
+        cudaFree(ix->adj_t);
+        ix->adj_t = nullptr;
+        return e;
+    }
+    k_degree<<<(unsigned)((ix->n + 255) / 256), 256>>>(ix->adj0, ix->n, ix->deg0, deg);
+    k_tag_adj<<<(unsigned)((ne + 255) / 256), 256>>>(ix->adj0, ne, deg, 8 * tiles, ix->adj_t);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    cudaFree(deg);
+    if (e != cudaSuccess) {
+        cudaFree(ix->adj_t);
+        ix->adj_t = nullptr;
+    }
+    return e;
+}
+
+// BF16 rows and FP8-e4m3 residual codes from the FP32 tables (mode LP): codes
+// of code_scale * u in the tensor cores' fragment order, per node 2 tiles of 16
+// slots (4 when deg0 > 32) x 1 (r <= 32) or 2 k pairs x 512 bytes
 cudaError_t lp_rebuild(finger_index* ix) {
     using namespace fg;
     cudaFree(ix->Xh);
     cudaFree(ix->edge_q);
     ix->Xh = nullptr;
     ix->edge_q = nullptr;
-    const int64_t n = ix->n, ne = n * ix->deg0;
-    const int r16b = ((ix->r_pad + 15) / 16) * 16;
+    const int64_t n = ix->n;
+    const int hks = ix->r > 32 ? 4 : 2;
+    const int tiles = ix->deg0 > 32 ? 4 : 2;
+    const int64_t units = n * tiles * (hks / 2) * 32;
     cudaError_t e = cudaMalloc(&ix->Xh, sizeof(__nv_bfloat16) * (size_t)n * ix->m8 * 8 + 16);
     if (e != cudaSuccess) return e;
-    e = cudaMalloc(&ix->edge_q, (size_t)ne * r16b + 16);
+    e = cudaMalloc(&ix->edge_q, sizeof(uint4) * (size_t)units + 16);
     if (e != cudaSuccess) return e;
     e = launch_to_bf16(ix->X, n, ix->m_pad, ix->m8, ix->Xh, 0);
     if (e != cudaSuccess) return e;
-    k_lp_codes<<<(unsigned)((ne * r16b + 255) / 256), 256>>>(ix->edge_u, ne, ix->r_pad, r16b,
-                                                             ix->code_scale, ix->edge_q);
+    k_lp_codes<<<(unsigned)((units + 255) / 256), 256>>>(ix->edge_u, n, ix->deg0, ix->r_pad, tiles,
+                                                         hks / 2, ix->code_scale,
+                                                         reinterpret_cast<uint4*>(ix->edge_q));
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    ix->r16 = r16b / 16;
-    return cudaDeviceSynchronize();
+    ix->hks = hks;
+    e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return e;
+    return build_tagged_adj(ix);
 }
 
 // FP16 unit residual codes from the FP32 tables (mode FINGER_F16), in the
 // tensor cores' A-fragment order: per node 2 tiles of 16 slots (4 when
 // deg0 > 32; rows beyond deg0 are zero) x 2 k steps of 16 codes (4 when
 // r > 32) x 512 bytes
-// The same mode reads a tagged copy of the layer-0 adjacency: a neighbour's id
-// has bit 30 set when its degree exceeds 16 (32 when deg0 > 32), i.e. when the
-// second half of its code block holds rows; ids must stay below 2^30.
 cudaError_t half_rebuild(finger_index* ix) {
     using namespace fg;
     cudaFree(ix->edge_h);
-    cudaFree(ix->adj_t);
     ix->edge_h = nullptr;
-    ix->adj_t = nullptr;
-    ix->hks = 0;
     if (ix->n >= (int64_t(1) << 30)) return cudaErrorInvalidValue;
     const int hks = ix->r > 32 ? 4 : 2;
     const int tiles = ix->deg0 > 32 ? 4 : 2;
-    const int64_t units = ix->n * tiles * hks * 32, ne = ix->n * ix->deg0;
-    int32_t* deg = nullptr;
+    const int64_t units = ix->n * tiles * hks * 32;
     cudaError_t e = cudaMalloc(&ix->edge_h, sizeof(uint4) * (size_t)units + 16);
-    if (e == cudaSuccess) e = cudaMalloc(&ix->adj_t, sizeof(uint32_t) * (size_t)ne + 16);
-    if (e == cudaSuccess) e = cudaMalloc(&deg, sizeof(int32_t) * (size_t)ix->n);
-    if (e != cudaSuccess) {
-        cudaFree(deg);
-        return e;
-    }
+    if (e != cudaSuccess) return e;
     k_half_codes<<<(unsigned)((units + 255) / 256), 256>>>(ix->edge_u, ix->n, ix->deg0,
                                                           ix->r_pad, tiles, hks,
                                                           reinterpret_cast<uint4*>(ix->edge_h));
-    k_degree<<<(unsigned)((ix->n + 255) / 256), 256>>>(ix->adj0, ix->n, ix->deg0, deg);
-    k_tag_adj<<<(unsigned)((ne + 255) / 256), 256>>>(ix->adj0, ne, deg, 8 * tiles, ix->adj_t);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
-    cudaFree(deg);
     if (e != cudaSuccess) return e;
     ix->hks = hks;
-    return cudaSuccess;
+    return build_tagged_adj(ix);
 }
 
 namespace fg {
@@ -857,8 +899,8 @@ finger_status build_tables(finger_index* ix, const finger_build_params* p, cudaS
     if (r < 1 || r > MAX_R || r > ix->m) return FINGER_ERR_INVALID_ARG;
     if (p->flags & ~(FINGER_BUILD_NO_MATCHING | FINGER_BUILD_NO_EPS | FINGER_BUILD_HALF_CODES))
         return FINGER_ERR_INVALID_ARG;
-    if ((p->flags & FINGER_BUILD_HALF_CODES) && ix->n >= (int64_t(1) << 30))
-        return FINGER_ERR_UNSUPPORTED;   // the FP16-code mode tags ids in bit 30
+    if ((p->flags & FINGER_BUILD_HALF_CODES || p->build_lp) && ix->n >= (int64_t(1) << 30))
+        return FINGER_ERR_UNSUPPORTED;   // the FP16-code and LP modes tag ids in bit 30
     const int spn = p->samples_per_node > 0 ? p->samples_per_node : 1;
     const int64_t n = ix->n;
     const int m = ix->m, m_pad = ix->m_pad, m4 = ix->m4, deg0 = ix->deg0;
