@@ -210,7 +210,8 @@ finger_status finger_get_tables(const finger_index* ix, float* P, double* stats,
 
 /* Bytes of the per-edge FINGER tables for n nodes, layer-0 degree deg0 and
  * rank r: (r + 2) * n * deg0 * 4 for FP32 (Supplementary F); for the LP
- * tables r_pad16 bytes of FP8 codes + 8 bytes of scalars per edge slot. */
+ * tables FP8 codes of 32 (deg0 <= 32) or 64 slots x 32 (r <= 32) or 64 codes
+ * per node, plus 8 bytes of scalars per edge slot. */
 int64_t finger_table_bytes(int64_t n, int deg0, int r, int lp);
 
 /* -------------------------------------------------------------- search */

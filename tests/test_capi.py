@@ -38,7 +38,10 @@ def test_table_bytes_is_r_plus_2_floats_per_edge():
     assert fg.table_bytes(1_000_000, 32, 64) == 66 * 32_000_000 * 4
     assert fg.table_bytes(10_000, 32, 16) == 18 * 320_000 * 4
     # reduced precision: 16-byte aligned FP8 codes + two FP32 scalars
-    assert fg.table_bytes(1_200_000, 48, 32, lp=True) == (32 + 8) * 1_200_000 * 48
+    # LP: FP8 codes of 64 slots (deg0 > 32) x 32 codes per node in the tensor
+    # cores' operand order, plus the FP32 scalars of every edge slot
+    assert fg.table_bytes(1_200_000, 48, 32, lp=True) == 64 * 32 * 1_200_000 + 8 * 1_200_000 * 48
+    assert fg.table_bytes(1_000_000, 32, 64, lp=True) == 32 * 64 * 1_000_000 + 8 * 1_000_000 * 32
 
 
 def test_status_strings():
