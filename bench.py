@@ -586,13 +586,14 @@ def leg_batch(args):
     import torch
 
     import paper_2206_11408_gb300 as fg
-    c, n, nq, X, Q, ix, q, setup = _ext_setup(args, 5)
+    c, n, nq, X, Q, ix, q, setup = _ext_setup(args, 5, half_codes=True)
     stream = torch.cuda.current_stream()
     nu = min(nq, 10_000)
     qu = q[:nu]
     gt_ids, _ = ix.knn(q, 100)
     gt = gt_ids.cpu().numpy()
-    modes = {"plain": fg.MODE_PLAIN, "finger": fg.MODE_FINGER}
+    # "finger" is the FP16-code form (the stream's FINGER); FP32 tables beside it
+    modes = {"plain": fg.MODE_PLAIN, "finger": fg.MODE_FINGER_F16, "finger_f32": fg.MODE_FINGER}
     curves, choice = _sweep(ix, qu, gt[:nu], c.K, modes, c.ef_grid, nu)
     uni = {}
     ck = None
@@ -601,12 +602,13 @@ def leg_batch(args):
                              Clocks(0) if name == "finger" else None)
         uni[name] = (v, ms)
         ck = k or ck
-    roof, cpq = _leg_roofline(fg, ix, qu, c, choice["finger"][0], fg.MODE_FINGER, uni["finger"][1])
+    roof, cpq = _leg_roofline(fg, ix, qu, c, choice["finger"][0], fg.MODE_FINGER_F16,
+                              uni["finger"][1])
     alpha = choice["finger"][0] / choice["plain"][0]
 
     plan = workloads.uneven_batches(nq)
     out = {}
-    for name, mode in modes.items():
+    for name, mode in (("plain", fg.MODE_PLAIN), ("finger", fg.MODE_FINGER_F16)):
         scale = alpha if name == "finger" else 1.0
         batches = []
         for start, size, K, ef in plan:
@@ -650,10 +652,12 @@ def leg_batch(args):
         out[name] = {"qps": nq / (total_ms / 1000), "total_ms": total_ms, "ef_scale": scale,
                      "p50_batch_ms": float(np.percentile(lat, 50)),
                      "p99_batch_ms": float(np.percentile(lat, 99)), "recall": hits / tot_k}
-    extra = {"impl_mode": "FINGER; uniform K=10 sweep + uneven batches (graph-captured, "
-                          "autotuned persistent launch)",
+    extra = {"impl_mode": "FINGER with FP16 codes; uniform K=10 sweep + uneven batches "
+                          "(graph-captured, autotuned persistent launch)",
              "finger_qps": uni["finger"][0], "plain_qps": uni["plain"][0],
+             "finger_f32_qps": uni["finger_f32"][0],
              "finger_over_plain": uni["finger"][0] / uni["plain"][0],
+             "finger_f32_over_plain": uni["finger_f32"][0] / uni["plain"][0],
              "ef": {k: v[0] for k, v in choice.items()},
              "recall": {k: v[1] for k, v in choice.items()},
              "roofline": roof, "counters_per_query": cpq,
