@@ -59,6 +59,10 @@ def parse():
     ap.add_argument("--candidates", type=int, default=0,
                     help="graph build candidates per node (default: the workload's efConstruction)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
+    ap.add_argument("--no-ext", action="store_true",
+                    help="skip the extension legs (configurations 3-5) of the default run")
+    ap.add_argument("--ext-nq", type=int, default=10000,
+                    help="queries of each extension leg in the default run")
     ap.add_argument("--save-curves", default="")
     ap.add_argument("--flat", action="store_true",
                     help="single-layer graph (no HNSW hierarchy) instead of HNSW")
@@ -889,6 +893,55 @@ def _refine(timed_fn, gt, K, nq, pts):
     return hi_ef, srt[hi][1]
 
 
+def extensions(args):
+    """Bounded runs of the three extension configurations, summarised for the
+    default line: reduced precision (configuration 3), the learned predictor
+    (4), FP16-code FINGER at m = 960 and the uneven stream (5).  Each leg builds
+    its own index and frees it; sizes are the configurations' own except the
+    query counts (``--ext-nq``)."""
+    import copy
+    import gc
+
+    import torch
+    out = {}
+    legs = (("cfg3_reduced_precision", 3, leg_lp), ("cfg4_learned_predictor", 4, leg_mlp),
+            ("cfg5_gist_like_and_stream", 5, leg_batch))
+    for key, cfg, fn in legs:
+        a = copy.copy(args)
+        a.cfg, a.n, a.nq, a.steps, a.warmup = cfg, 0, args.ext_nq, 5, 3
+        t = time.perf_counter()
+        try:
+            line = fn(a)
+        except Exception as e:   # a failed leg is reported, the headline stands
+            out[key] = {"error": f"{type(e).__name__}: {e}"}
+            continue
+        finally:
+            gc.collect()
+            torch.cuda.empty_cache()
+        keep = {k: line.get(k) for k in (
+            "value", "plain_qps", "finger_qps", "finger_f16_qps", "finger_f32_qps",
+            "lp_over_plain", "f16_over_plain", "mlp_over_plain", "mlp_over_finger",
+            "finger_over_plain", "finger_f32_over_plain", "ef", "recall",
+            "qps_at_recall_interp", "distance_error_vs_fp64") if k in line}
+        keep["workload"] = line["config"]["workload"]
+        keep["nq"] = line["config"].get("nq")
+        keep["impl_mode"] = line.get("impl_mode")
+        if "stream" in line:
+            st = line["stream"]
+            keep["stream"] = {"queries": st["queries"], "batches": st["batches"],
+                              "finger_over_plain": st["finger_over_plain"],
+                              "plain": {k: st["plain"][k] for k in ("qps", "p50_batch_ms",
+                                                                    "p99_batch_ms", "recall")},
+                              "finger": {k: st["finger"][k] for k in ("qps", "p50_batch_ms",
+                                                                      "p99_batch_ms", "recall")}}
+        if "predictor" in line:
+            keep["predictor"] = {k: line["predictor"][k] for k in ("triples", "eps_prime",
+                                                                  "heldout_cos_mae")}
+        keep["seconds"] = time.perf_counter() - t
+        out[key] = keep
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -1092,6 +1145,9 @@ def main():
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
         cpu = oracle_search_timing(args.cfg, K, c.r, c.M, c.ef_construction)
+    ext = None
+    if rank == 0 and ws == 1 and not args.no_ext and not args.n and not args.nq:
+        ext = extensions(args)
 
     if args.save_curves and rank == 0:
         json.dump({"curves": curves, "choice": choice}, open(args.save_curves, "w"))
@@ -1135,6 +1191,7 @@ def main():
             "qps_at_recall_interp": {k: qps_at(v) for k, v in curves.items()},
             "recall_tie_aware": tie,
             "cpu_baseline": cpu,
+            "extensions": ext,
             "e2e": {"value": ws * nq / (e2e_ms / 1000), "unit": "queries/s",
                     "h2d_bytes_per_step": nq * c.m * 4, "d2h_bytes_per_step": nq * K * 12,
                     "recall": e2e_rec},
