@@ -45,6 +45,9 @@ sys.path.insert(0, ROOT)
 import workloads  # noqa: E402
 
 TARGET_RECALL = 0.95
+# learned predictor gate: the network runs where the matched estimate lies
+# within MLP_GATE * ub of the upper bound (fixed before measuring)
+MLP_GATE = 0.1
 
 
 def parse():
@@ -546,22 +549,33 @@ def leg_mlp(args):
     st = ix.stats()
     ratio = st["sigma"] / st["sigma_hat"] if st["sigma_hat"] > 0 else 0.0
     matched = (fv[:, c.r].cpu().numpy() - st["mu_hat"]) * ratio + st["mu"]
-    modes = {"plain": fg.MODE_PLAIN, "finger": fg.MODE_FINGER, "finger_mlp": fg.MODE_FINGER_MLP}
-    curves, choice = _sweep(ix, q, gt, c.K, modes, c.ef_grid, nq)
-    res, ck = {}, None
-    for name, mode in modes.items():
+    # the predictor on every estimate (delta < 0) and gated to the margin
+    # MLP_GATE * ub around the upper bound
+    variants = {"plain": (fg.MODE_PLAIN, -1.0), "finger": (fg.MODE_FINGER, -1.0),
+                "finger_mlp": (fg.MODE_FINGER_MLP, -1.0),
+                "finger_mlp_gated": (fg.MODE_FINGER_MLP, MLP_GATE)}
+    curves, choice, res, ck = {}, {}, {}, None
+    for name, (mode, delta) in variants.items():
+        ix.set_predictor_gate(delta)
+        cv, ch = _sweep(ix, q, gt, c.K, {name: mode}, c.ef_grid, nq)
+        curves.update(cv)
+        choice.update(ch)
         v, ms, ids, k = _timed(ix, q, c.K, choice[name][0], mode, args.steps, args.warmup, nq,
-                               Clocks(0) if name == "finger_mlp" else None)
+                               Clocks(0) if name == "finger_mlp_gated" else None)
         res[name] = (v, ms)
         ck = k or ck
-    roof, cpq = _leg_roofline(fg, ix, q, c, choice["finger_mlp"][0], fg.MODE_FINGER_MLP,
-                              res["finger_mlp"][1])
-    extra = {"impl_mode": "FINGER_MLP (learned angle predictor, BF16 tensor-core inference)",
+    ix.set_predictor_gate(MLP_GATE)
+    roof, cpq = _leg_roofline(fg, ix, q, c, choice["finger_mlp_gated"][0], fg.MODE_FINGER_MLP,
+                              res["finger_mlp_gated"][1])
+    extra = {"impl_mode": f"FINGER_MLP (learned angle predictor, BF16 tensor-core inference), "
+                          f"gated to the margin {MLP_GATE} ub around ub",
              "roofline": roof, "counters_per_query": cpq,
              "qps_at_recall_interp": {k: qps_at(v) for k, v in curves.items()},
              "finger_qps": res["finger"][0], "plain_qps": res["plain"][0],
-             "mlp_over_plain": res["finger_mlp"][0] / res["plain"][0],
-             "mlp_over_finger": res["finger_mlp"][0] / res["finger"][0],
+             "mlp_all_qps": res["finger_mlp"][0], "mlp_gate": MLP_GATE,
+             "mlp_over_plain": res["finger_mlp_gated"][0] / res["plain"][0],
+             "mlp_over_finger": res["finger_mlp_gated"][0] / res["finger"][0],
+             "mlp_all_over_finger": res["finger_mlp"][0] / res["finger"][0],
              "ef": {k: v[0] for k, v in choice.items()},
              "recall": {k: v[1] for k, v in choice.items()},
              "predictor": {"triples": int(nrec), "harvest_expansions": expansions,
@@ -574,8 +588,8 @@ def leg_mlp(args):
              "setup_s": setup,
              "curves": {k: [[e, round(r_, 4), round(v_, 1)] for e, r_, v_ in pts]
                         for k, pts in curves.items()}}
-    return _line(c, n, nq, res["finger_mlp"][0], res["finger_mlp"][1], args.steps, args.warmup,
-                 extra, ck)
+    return _line(c, n, nq, res["finger_mlp_gated"][0], res["finger_mlp_gated"][1], args.steps,
+                 args.warmup, extra, ck)
 
 
 def leg_batch(args):
@@ -921,6 +935,7 @@ def extensions(args):
         keep = {k: line.get(k) for k in (
             "value", "plain_qps", "finger_qps", "finger_f16_qps", "finger_f32_qps",
             "lp_over_plain", "f16_over_plain", "mlp_over_plain", "mlp_over_finger",
+            "mlp_all_over_finger", "mlp_gate",
             "finger_over_plain", "finger_f32_over_plain", "ef", "recall",
             "qps_at_recall_interp", "distance_error_vs_fp64") if k in line}
         keep["workload"] = line["config"]["workload"]

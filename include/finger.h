@@ -341,6 +341,15 @@ finger_status finger_set_predictor(finger_index* ix, const float* weights, int64
                                    float eps);
 finger_status finger_get_predictor(const finger_index* ix, float* weights, float* eps);
 
+/* Where the predictor runs in FINGER_MODE_FINGER_MLP.  delta < 0 (default):
+ * on every estimate.  delta >= 0: only for a neighbour whose distribution-
+ * matched estimate (Algorithm 3) lies within delta * ub of the upper bound ub
+ * at the start of its centre's expansion (and only while the result list is
+ * full then); elsewhere the matched estimate stands.  The network's cost is
+ * then paid where its better cosine can change the gate.  NaN returns
+ * FINGER_ERR_INVALID_ARG. */
+finger_status finger_set_predictor_gate(finger_index* ix, float delta);
+
 /* Mean squared error and its gradient (host, finger_mlp_size floats) of the
  * predictor with the given flat weights (host, nf = r + 4 inputs) on n device
  * rows, computed by the training kernels (gradient checks). Synchronous. */

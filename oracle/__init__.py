@@ -62,7 +62,8 @@ def lib():
         L.orc_hnsw_build.argtypes = [P, i64, i32, i32, i32, P, P, i64, P, P, P, P]
         L.orc_hnsw_build.restype = i32
         L.orc_search.argtypes = [P, i64, i32, P, i32, P, P, i32, i32, i32, P, i64, i32, i32, P,
-                                 i32, P, i32, i32, P, P, P, i32, P, ctypes.c_double, i32]
+                                 i32, P, i32, i32, P, P, P, i32, P, ctypes.c_double, i32,
+                                 ctypes.c_double]
         L.orc_search.restype = i32
         L.orc_sample_pairs.argtypes = [P, i64, i32, u64, i32, P]
         L.orc_estimate.argtypes = [P, P, P, i32, P, i32, P, i32]
@@ -198,10 +199,13 @@ class FingerParams:
 
 
 def search(g: Graph, X, Q, K: int, ef: int, finger: FingerParams | None = None, warmup: int = 5,
-           threads: int = 0, mlp_weights=None, mlp_eps: float = 0.0):
+           threads: int = 0, mlp_weights=None, mlp_eps: float = 0.0, mlp_delta: float = -1.0):
     """Descent on levels >= 1, then Algorithm 1 (finger=None) or Algorithm 4.
     With mlp_weights (flat, see oracle.mlp) the learned predictor replaces the
-    distribution matching in Algorithm 3 (extension, not in the paper).
+    distribution matching in Algorithm 3 (extension, not in the paper): on
+    every estimate when mlp_delta < 0, else only where the matched estimate
+    lies within mlp_delta * ub of the ub at the start of the centre's expansion
+    (with the result list full then).
 
     Returns ids (nq, K) int64, dists (nq, K) float64 and per-query counters
     (nq, 8) int64 in the order of CNT_NAMES.
@@ -226,7 +230,7 @@ def search(g: Graph, X, Q, K: int, ef: int, finger: FingerParams | None = None, 
     rc = lib().orc_search(_p(X), n, m, _p(adj0), adj0.shape[1], _p(up_off), _p(up_adj), g.M,
                           g.entry, g.maxlevel, _p(Q), nq, K, ef, _p(P), r, _p(st), warmup, fl,
                           _p(ids), _p(d), _p(cnt), threads, _p(mw) if mw is not None else None,
-                          float(mlp_eps), codes)
+                          float(mlp_eps), codes, float(mlp_delta))
     if rc != 0:
         raise ValueError("orc_search rejected its arguments")
     return ids, d, cnt

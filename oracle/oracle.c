@@ -369,7 +369,8 @@ static double appx_dist(const double* xc, const double* xd, int m, double cc, co
                         const double* q_res, double qres_n2, const double* Pq, const double* P,
                         int r, const double* st, double* d_proj, double* d_res, double* diff,
                         double* Pd, const double* q, const double* mlp, double mlp_eps,
-                        double* f_out, double* y_out, int codes) {
+                        double* f_out, double* y_out, int codes, int full_c, double ub_c,
+                        double mlp_delta) {
     double mu = st[0], sigma = st[1], muh = st[2], sigmah = st[3], eps = st[4];
     double ratio = sigmah > 0 ? sigma / sigmah : 0.0;
     double b = cc > 0 ? dot(xc, xd, m) / cc : 0.0;
@@ -390,7 +391,16 @@ static double appx_dist(const double* xc, const double* xd, int m, double cc, co
     }
     double t = (that - muh) * ratio + mu;
     t = t + eps;
-    if (mlp) {
+    int use_mlp = mlp != NULL;
+    if (use_mlp && mlp_delta >= 0) {
+        /* gated predictor (extension): only where the matched estimate lies
+         * within mlp_delta * ub of the ub at the start of the expansion, and
+         * only when the result list was full then */
+        double est_m = dot(diff, diff, m) + qres_n2 + dres_n2 -
+                       2.0 * sqrt(qres_n2) * sqrt(dres_n2) * t;
+        use_mlp = full_c && fabs(est_m - ub_c) <= mlp_delta * ub_c;
+    }
+    if (use_mlp) {
         /* learned predictor in place of distribution matching (extension) */
         double f[80];
         double a = cc > 0 ? dot(xc, q, m) / cc : 0.0;
@@ -439,7 +449,7 @@ double orc_estimate(const double* q, const double* xc, const double* xd, int m, 
     double qres_n2;
     double cc = centre_parts(xc, q, m, P, r, q_proj, q_res, &qres_n2, Pq);
     double e = appx_dist(xc, xd, m, cc, q_proj, q_res, qres_n2, Pq, P, r, stats, d_proj, d_res,
-                         diff, Pd, q, NULL, 0.0, NULL, NULL, codes);
+                         diff, Pd, q, NULL, 0.0, NULL, NULL, codes, 0, 0.0, -1.0);
     free(w);
     return e;
 }
@@ -461,7 +471,7 @@ double orc_estimate_mlp(const double* q, const double* xc, const double* xd, int
     double qres_n2;
     double cc = centre_parts(xc, q, m, P, r, q_proj, q_res, &qres_n2, Pq);
     double e = appx_dist(xc, xd, m, cc, q_proj, q_res, qres_n2, Pq, P, r, stats, d_proj, d_res,
-                         diff, Pd, q, mlp, mlp_eps, f_out, y_out, 0);
+                         diff, Pd, q, mlp, mlp_eps, f_out, y_out, 0, 0, 0.0, -1.0);
     free(w);
     return e;
 }
@@ -473,7 +483,7 @@ static void search_one(const double* X, int m, const int32_t* adj0, int deg0, co
                        int K, int ef, const double* P, int r, const double* st, int warmup,
                        int finger, int64_t* out_ids, double* out_d, int64_t* cnt, char* visited,
                        int32_t* touched, tent_t* T, double* work, const double* mlp,
-                       double mlp_eps, int codes) {
+                       double mlp_eps, int codes, double mlp_delta) {
     for (int i = 0; i < CNT_N; ++i) cnt[i] = 0;
     /* ---- upper layers: greedy descent (search-layer with ef = 1) */
     int32_t cur = entry;
@@ -527,6 +537,9 @@ static void search_one(const double* X, int m, const int32_t* adj0, int deg0, co
         expansions++;
         const double* xc = X + (size_t)c * m;
         int use_est = finger && expansions > warmup;
+        /* the upper bound when this centre is expanded (gated predictor) */
+        const int full_c = tlen == ef;
+        const double ub_c = T[tlen - 1].kv.d;
         double cc = 0, qres_n2 = 0;
         if (use_est) cc = centre_parts(xc, q, m, P, r, q_proj, q_res, &qres_n2, Pq);
         const int32_t* row = adj0 + (size_t)c * deg0;
@@ -542,7 +555,7 @@ static void search_one(const double* X, int m, const int32_t* adj0, int deg0, co
             if (use_est && full) {
                 double est = appx_dist(xc, xd, m, cc, q_proj, q_res, qres_n2, Pq, P, r, st,
                                        d_proj, d_res, diff, Pd, q, mlp, mlp_eps, NULL, NULL,
-                                       codes);
+                                       codes, full_c, ub_c, mlp_delta);
                 cnt[CNT_ESTIMATES]++;
                 double ub = T[tlen - 1].kv.d;
                 if (est > ub) {
@@ -577,7 +590,8 @@ int orc_search(const double* X, int64_t n, int m, const int32_t* adj0, int deg0,
                const int64_t* up_off, const int32_t* up_adj, int Mup, int entry, int maxlevel,
                const double* Q, int64_t nq, int K, int ef, const double* P, int r,
                const double* stats, int warmup, int finger, int64_t* ids, double* dists,
-               int64_t* counters, int nthreads, const double* mlp, double mlp_eps, int codes) {
+               int64_t* counters, int nthreads, const double* mlp, double mlp_eps, int codes,
+               double mlp_delta) {
     if (ef < 1 || K < 1) return -1;
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
@@ -596,7 +610,7 @@ int orc_search(const double* X, int64_t n, int m, const int32_t* adj0, int deg0,
             search_one(X, m, adj0, deg0, up_off, up_adj, Mup, entry, maxlevel, Q + (size_t)qi * m,
                        K, ef, P, r, stats, warmup, finger, ids + qi * K, dists + qi * K,
                        counters ? counters + qi * CNT_N : cnt_local, visited, touched, T, work,
-                       mlp, mlp_eps, codes);
+                       mlp, mlp_eps, codes, mlp_delta);
         }
         free(visited);
         free(touched);

@@ -108,6 +108,7 @@ SIGNATURES = {
     "finger_train_predictor": (_I, [_P, _P, _P, _P]),
     "finger_set_predictor": (_I, [_P, _P, _I64, _F]),
     "finger_get_predictor": (_I, [_P, _P, _P]),
+    "finger_set_predictor_gate": (_I, [_P, _F]),
     "finger_mlp_loss_grad": (_I, [_P, _I, _P, _P, _P, _I64, _P, _P, _P]),
     "finger_mlp_predict": (_I, [_P, _P, _I64, _P, _P]),
     "finger_merge_topk": (_I, [_P, _P, _I, _I64, _I, _P, _P, _P, _P]),
@@ -463,6 +464,12 @@ class Index:
         w = np.ascontiguousarray(weights, dtype=np.float32)
         _check(self._lib.finger_set_predictor(self._h, _np_ptr(w), w.size, eps),
                "finger_set_predictor")
+
+    def set_predictor_gate(self, delta: float):
+        """finger_set_predictor_gate: the learned predictor runs only where the
+        matched estimate lies within delta * ub of ub (delta < 0: everywhere)."""
+        _check(self._lib.finger_set_predictor_gate(self._h, float(delta)),
+               "finger_set_predictor_gate")
 
     def get_predictor(self):
         w = np.empty(self.mlp_size(), np.float32)

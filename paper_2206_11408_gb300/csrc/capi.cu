@@ -138,6 +138,7 @@ fg::DevIndex make_dev(const finger_index* ix) {
     d.b2 = ix->b2;
     d.b3 = ix->b3;
     d.mlp_eps = ix->mlp_eps;
+    d.mlp_delta = ix->mlp_delta;
     d.mlp_kp = ix->mlp_kp;
     return d;
 }

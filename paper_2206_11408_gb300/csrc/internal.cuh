@@ -68,6 +68,7 @@ struct DevIndex {
     const float* b1;
     const float* b2;
     float b3, mlp_eps;
+    float mlp_delta;        // predictor only within mlp_delta * ub of ub; < 0: everywhere
     int mlp_kp;
 };
 
@@ -201,6 +202,7 @@ struct finger_index {
     float* b1 = nullptr;
     float* b2 = nullptr;
     float b3 = 0.f, mlp_eps = 0.f;
+    float mlp_delta = -1.f;       // see DevIndex
     std::vector<float> h_mlp;     // FP32 master copy (W1, b1, W2, b2, w3, b3)
     // search state
     int mode = FINGER_MODE_PLAIN;

@@ -300,6 +300,13 @@ finger_status finger_set_predictor(finger_index* ix, const float* weights, int64
     return finger_load_mlp_internal(ix, weights, count, eps);
 }
 
+finger_status finger_set_predictor_gate(finger_index* ix, float delta) {
+    if (!ix || !(delta == delta)) return FINGER_ERR_INVALID_ARG;
+    if (ix->mlp_delta != delta) fg_drop_captures(ix);   // captured launches hold the index view
+    ix->mlp_delta = delta;
+    return FINGER_OK;
+}
+
 finger_status finger_get_predictor(const finger_index* ix, float* weights, float* eps) {
     if (!ix) return FINGER_ERR_INVALID_ARG;
     if (!ix->has_mlp) return FINGER_ERR_NOT_BUILT;

@@ -968,17 +968,9 @@ __global__ void __launch_bounds__(128, OCC) k_search(DevIndex ix, SearchArgs a) 
                 tr[s] = 0.f;
                 hpos[s] = -1;
             }
-            int crow[NPL];          // MLP: compact feature row of each new slot
-            int ncomp = 0;
+            int crow[NPL];          // MLP: compact feature row of each predicted slot (-1: none)
 #pragma unroll
-            for (int s = 0; s < NPL; ++s) {
-                crow[s] = -1;
-                if constexpr (MLP) {
-                    const unsigned bm = __ballot_sync(FULLMASK, isnew[s]);
-                    if (isnew[s]) crow[s] = ncomp + __popc(bm & ltmask);
-                    ncomp += __popc(bm);
-                }
-            }
+            for (int s = 0; s < NPL; ++s) crow[s] = -1;
             if constexpr (HARV) {
                 if (use_est) {
 #pragma unroll
@@ -1005,41 +997,13 @@ __global__ void __launch_bounds__(128, OCC) k_search(DevIndex ix, SearchArgs a) 
                     }
                 }
             }
-            if constexpr (MLP) {
-                // the new neighbours' feature rows go through the predictor 16 at a
-                // time (one m16 tile per round); outputs land in `ak` (free until
-                // the admission replay) at the neighbour's compact row
-                if (use_est) {
-                    uint32_t* xw = reinterpret_cast<uint32_t*>(xt);
-                    const int xs = ix.mlp_kp + MLP_PAD;
-                    const int wpr = xs >> 1;
-                    for (int base = 0; base < ncomp; base += 16) {
-#pragma unroll
-                        for (int s = 0; s < NPL; ++s) {
-                            if (isnew[s] && crow[s] >= base && crow[s] < base + 16) {
-                                const size_t e = (size_t)c * ix.deg0 + s * 32 + lane;
-                                const float2 sc = __ldg(ix.edge_s + e);
-                                const float th = features_tile(ix, e, uq, sc, cc, ac, qres_n, qn2,
-                                                               xt + (size_t)(crow[s] - base) * xs);
-                                tr[s] = fmaf(th, ix.alpha, ix.beta);
-                            }
-                        }
-                        const int rows = min(16, ncomp - base);
-                        for (int i = rows * wpr + lane; i < 16 * wpr; i += 32) xw[i] = 0u;
-                        __syncwarp();
-                        mlp_tile(xt, ix.mlp_kp, ix.W1f, ix.W2f, ix.b1, ix.b2, ix.w3, ix.b3,
-                                 ak + base, lane);
-                        __syncwarp();
-                    }
-                }
-            }
             // FP32 FINGER: t_hat of every new neighbour by one balanced gather.
             // The new neighbours are compacted and lpr lanes share an edge row
             // (lpr = r/4 rounded up to a power of two, at most 16), so one
             // 16-byte load per lane covers 32 / lpr rows and eight loads per
             // lane are in flight at once; the row sums come from a
             // transpose-reduce over the row's lanes (a butterfly for lpr = 4).
-            constexpr bool BAL = MODE == FINGER_MODE_FINGER;
+            constexpr bool BAL = MODE == FINGER_MODE_FINGER || MLP;
             constexpr int GS = 8;
             float2 scv[NPL];
             if constexpr (BAL) {
@@ -1117,6 +1081,52 @@ __global__ void __launch_bounds__(128, OCC) k_search(DevIndex ix, SearchArgs a) 
                     __syncwarp();
                 }
             }
+            if constexpr (MLP) {
+                // learned predictor (an extension): the matched estimate of every
+                // new slot from the gather above; a slot whose matched estimate lies
+                // within the margin mlp_delta * ub of the ub at the expansion start
+                // (every slot when mlp_delta < 0) gets the predictor.  Its feature
+                // rows go through the network 16 at a time (one m16 tile per
+                // round); outputs land in `ak` (free until the admission replay)
+                // at the slot's compact row.
+                if (use_est) {
+                    int nunc = 0;
+#pragma unroll
+                    for (int s = 0; s < NPL; ++s) {
+                        bool unc = false;
+                        if (isnew[s]) {
+                            tr[s] = fmaf(xb[s * 32 + lane], ix.alpha, ix.beta);
+                            const float dd = ac - scv[s].y;
+                            const float est_m = dd * dd * cc + qres2 + scv[s].x * scv[s].x -
+                                                2.f * qres_n * scv[s].x * tr[s];
+                            unc = ix.mlp_delta < 0.f ||
+                                  (full0 && fabsf(est_m - ub0) <= ix.mlp_delta * ub0);
+                        }
+                        const unsigned bm = __ballot_sync(FULLMASK, unc);
+                        if (unc) crow[s] = nunc + __popc(bm & ltmask);
+                        nunc += __popc(bm);
+                    }
+                    uint32_t* xw = reinterpret_cast<uint32_t*>(xt);
+                    const int xs = ix.mlp_kp + MLP_PAD;
+                    const int wpr = xs >> 1;
+                    for (int base = 0; base < nunc; base += 16) {
+#pragma unroll
+                        for (int s = 0; s < NPL; ++s) {
+                            if (crow[s] >= base && crow[s] < base + 16) {
+                                const size_t e = (size_t)c * ix.deg0 + s * 32 + lane;
+                                features_tile(ix, e, uq, scv[s], cc, ac, qres_n, qn2,
+                                              xt + (size_t)(crow[s] - base) * xs);
+                            }
+                        }
+                        const int rows = min(16, nunc - base);
+                        for (int i = rows * wpr + lane; i < 16 * wpr; i += 32) xw[i] = 0u;
+                        __syncwarp();
+                        mlp_tile(xt, ix.mlp_kp, ix.W1f, ix.W2f, ix.b1, ix.b2, ix.w3, ix.b3,
+                                 ak + base, lane);
+                        __syncwarp();
+                    }
+                }
+            }
             int nl = 0;
             bool needr[NPL];
 #pragma unroll
@@ -1126,15 +1136,18 @@ __global__ void __launch_bounds__(128, OCC) k_search(DevIndex ix, SearchArgs a) 
                     const size_t e = (size_t)c * ix.deg0 + s * 32 + lane;
                     const float2 sc = BAL ? scv[s] : WB ? scw[s] : __ldg(ix.edge_s + e);
                     float t;
-                    if constexpr (BAL) {
+                    if constexpr (MLP) {
+                        // the predictor's cosine where it ran (the matched cosine is
+                        // the fallback for a non-finite output), else the matched one
+                        t = tr[s];
+                        if (crow[s] >= 0) {
+                            const float y = ak[crow[s]];
+                            if (isfinite(y)) t = y + ix.mlp_eps;
+                        }
+                    } else if constexpr (BAL) {
                         t = fmaf(xb[s * 32 + lane], ix.alpha, ix.beta);
                     } else if constexpr (WB) {
                         t = fmaf(th[s], ix.alpha, ix.beta);
-                    } else if constexpr (MLP) {
-                        // learned predictor in place of distribution matching;
-                        // the matched cosine is the fallback for a non-finite output
-                        const float y = ak[crow[s]];
-                        t = isfinite(y) ? y + ix.mlp_eps : tr[s];
                     } else if constexpr (HARV) {
                         t = tr[s];
                     } else {

@@ -6,7 +6,8 @@
 * harvested features and targets against the oracle's definitions computed on
   the same (query, centre, neighbour) triples;
 * the MLP-gated search against the oracle's MLP-gated Algorithm 4 with the same
-  (seeded, oracle-initialised) predictor;
+  (seeded, oracle-initialised) predictor, on every estimate and with the
+  predictor gated to the margin around ub;
 * what training buys: on held-out harvested triples the trained network's
   cosine error is below that of distribution matching.
 """
@@ -81,20 +82,28 @@ def test_mlp_search_matches_oracle(deep_like):
     ix.set_mode(fg.MODE_FINGER_MLP, 5)
     q = torch.from_numpy(Q).cuda()
     gt, _ = oracle.bruteforce(X, Q, 10)
-    for ef in (20, 60):
-        cnt = torch.zeros((Q.shape[0], 8), dtype=torch.int32, device="cuda")
-        ix.set_counters(cnt)
-        ids, d = ix.search(q, 10, ef)
-        torch.cuda.synchronize()
-        ix.sync()
-        ix.set_counters(None)
-        gi, gd, gc = ids.cpu().numpy(), d.cpu().numpy(), cnt.cpu().numpy()
-        oi, od, oc = oracle.search(g, X, Q, 10, ef, fp, mlp_weights=wq, mlp_eps=eps)
-        match = (gi == oi).all(axis=1)
-        assert match.mean() >= 0.99, (ef, match.mean())
-        np.testing.assert_allclose(gd[match], od[match], rtol=1e-5)
-        assert oc[:, 3].sum() > 0                       # the predictor gates
-        assert abs(oracle.recall(gi, gt, 10) - oracle.recall(oi, gt, 10)) <= 0.002
+    # delta < 0: the predictor on every estimate; delta >= 0: only where the
+    # matched estimate lies within delta * ub of ub (the gated rule)
+    for delta in (-1.0, 0.1, 0.3):
+        ix.set_predictor_gate(delta)
+        for ef in (20, 60):
+            cnt = torch.zeros((Q.shape[0], 8), dtype=torch.int32, device="cuda")
+            ix.set_counters(cnt)
+            ids, d = ix.search(q, 10, ef)
+            torch.cuda.synchronize()
+            ix.sync()
+            ix.set_counters(None)
+            gi, gd, gc = ids.cpu().numpy(), d.cpu().numpy(), cnt.cpu().numpy()
+            oi, od, oc = oracle.search(g, X, Q, 10, ef, fp, mlp_weights=wq, mlp_eps=eps,
+                                       mlp_delta=delta)
+            match = (gi == oi).all(axis=1)
+            assert match.mean() >= 0.99, (delta, ef, match.mean())
+            np.testing.assert_allclose(gd[match], od[match], rtol=1e-5)
+            same = (gc[match][:, :7] == oc[match][:, :7]).all(axis=1)
+            assert same.mean() >= 0.97, (delta, ef, same.mean())
+            assert oc[:, 3].sum() > 0                       # the gate skips
+            assert abs(oracle.recall(gi, gt, 10) - oracle.recall(oi, gt, 10)) <= 0.002
+    ix.set_predictor_gate(-1.0)
 
 
 def test_trained_predictor_beats_matching(deep_like):

@@ -132,3 +132,26 @@ def test_c_predictor_matches_numpy_forward():
         assert est == pytest.approx(ref, rel=1e-12, abs=1e-12)
         outs.append(y_c)
     assert np.std(outs) > 1e-3          # the network is not constant on these inputs
+
+
+def test_predictor_gate(small):
+    """The gated predictor (extension): it runs only where the matched estimate
+    lies within delta * ub of the ub at the start of the centre's expansion.
+    delta = 0 leaves every matched estimate (an exact tie with ub has measure
+    zero): the traversal of FINGER without a predictor.  With a predictor that
+    says cos = 1e6 (its estimates never skip), the skipped neighbours fall
+    from distribution matching's count (delta = 0) through a gated count to
+    none (ungated), and widening the margin only removes skips."""
+    X, Q, g, fp = small
+    nf = fp.P.shape[0] + 4
+    big = _const_predictor(nf, 1e6)
+    i0, d0, c0 = oracle.search(g, X, Q, 10, 30, fp)
+    i1, d1, c1 = oracle.search(g, X, Q, 10, 30, fp, mlp_weights=big, mlp_delta=0.0)
+    assert (i0 == i1).all() and (d0 == d1).all() and (c0 == c1).all()
+    skips = [c0[:, 3].sum()]
+    for delta in (0.05, 0.5):
+        _, _, c = oracle.search(g, X, Q, 10, 30, fp, mlp_weights=big, mlp_delta=delta)
+        skips.append(c[:, 3].sum())
+    _, _, c = oracle.search(g, X, Q, 10, 30, fp, mlp_weights=big, mlp_delta=-1.0)
+    skips.append(c[:, 3].sum())
+    assert skips[0] > skips[1] > skips[2] > skips[3] == 0, skips
