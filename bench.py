@@ -637,10 +637,14 @@ def leg_batch(args):
                             int(efm.max()), K, torch.from_numpy(off).cuda(), int(K.sum())))
         ix.set_mode(mode, 5)
         # autotune each ef bucket on a sample batch at the bucket's largest ef
+        picks = {}
         for bkt in (16, 32, 64, 128, 256, 512, 1024):
             lo = bkt // 2 if bkt > 16 else 10
             if any(lo < b[4] <= bkt for b in batches):
                 ix.autotune(q[:2048], 10, min(bkt, 1000))
+                pk = ix.tuned(min(bkt, 1000))
+                picks[str(bkt)] = [pk["warps_per_block"], pk["hash_slots"], pk["resident_warps"],
+                                   round(pk["best_ms"], 3)]
         for start, size, Kt, eft, mx, _, off, tot in batches:   # warm-up pass: captures graphs
             ix.search_batch(q[start:start + size], Kt, eft, max_ef=mx, offsets=off, total=tot)
         torch.cuda.synchronize()
@@ -669,7 +673,8 @@ def leg_batch(args):
                 tot_k += k
         out[name] = {"qps": nq / (total_ms / 1000), "total_ms": total_ms, "ef_scale": scale,
                      "p50_batch_ms": float(np.percentile(lat, 50)),
-                     "p99_batch_ms": float(np.percentile(lat, 99)), "recall": hits / tot_k}
+                     "p99_batch_ms": float(np.percentile(lat, 99)), "recall": hits / tot_k,
+                     "tuned": picks}
     extra = {"impl_mode": "FINGER with FP16 codes; uniform K=10 sweep + uneven batches "
                           "(graph-captured, autotuned persistent launch)",
              "finger_qps": uni["finger"][0], "plain_qps": uni["plain"][0],
@@ -680,6 +685,7 @@ def leg_batch(args):
              "recall": {k: v[1] for k, v in choice.items()},
              "roofline": roof, "counters_per_query": cpq,
              "qps_at_recall_interp": {k: qps_at(v) for k, v in curves.items()},
+             # per ef bucket: [warps per block, hash slots, resident warps per SM, best ms]
              "stream": {"queries": nq, "batches": len(plan), "plain": out["plain"],
                         "finger": out["finger"],
                         "finger_over_plain": out["finger"]["qps"] / out["plain"]["qps"]},

@@ -53,13 +53,18 @@ enum {
                                    FP32 accumulation, final top-K re-ranked in FP32 */
     FINGER_MODE_FINGER_MLP = 3, /* Algorithm 4 with a learned angle predictor in place of
                                    distribution matching; matching is the fallback */
-    FINGER_MODE_FINGER_F16 = 4  /* Algorithm 4 with the per-edge unit residual projections
+    FINGER_MODE_FINGER_F16 = 4, /* Algorithm 4 with the per-edge unit residual projections
                                    (Supplementary G) stored as FP16 codes; FP32 vectors and
                                    FP32 arithmetic.  Needs tables built with
                                    FINGER_BUILD_HALF_CODES.  The whole code block of the
                                    expanded node (deg0 rows, contiguous) is read together
                                    with its adjacency row, so an expansion needs one
                                    dependent round trip to memory fewer than in mode FINGER */
+    FINGER_MODE_FINGER_F8 = 5   /* as FINGER_F16 with the codes stored as FP8-e4m3 of
+                                   256 u (the LP mode's code table: half the bytes and
+                                   half the registers per code block); FP32 vectors,
+                                   FP32 accumulation.  Needs tables built with
+                                   FINGER_BUILD_FP8_CODES or build_lp */
 };
 
 /* --------------------------------------------------------------- index */
@@ -125,9 +130,11 @@ typedef struct {
     int entry;
     int64_t up_rows;
     int r;               /* FINGER rank, 0 before finger_build_tables */
-    int has_lp;          /* BF16/FP8 tables present */
+    int has_lp;          /* BF16 rows and FP8 codes present (mode LP) */
     int has_mlp;         /* learned predictor present */
     int64_t device_bytes;/* device memory held by the index */
+    int has_half_codes;  /* FP16 codes present (mode FINGER_F16) */
+    int has_fp8_codes;   /* FP8 codes present (mode FINGER_F8) */
 } finger_info;
 
 finger_status finger_get_info(const finger_index* ix, finger_info* out);
@@ -161,7 +168,8 @@ typedef struct {
                                  (stored as mu = mu_hat = 0, sigma = sigma_hat
                                  = 1; eps = mean |Y - X|);
                                  FINGER_BUILD_NO_EPS: eps = 0;
-                                 and FINGER_BUILD_HALF_CODES (below) */
+                                 and FINGER_BUILD_HALF_CODES /
+                                 FINGER_BUILD_FP8_CODES (below) */
 } finger_build_params;
 
 #define FINGER_BUILD_NO_MATCHING 1
@@ -175,6 +183,11 @@ typedef struct {
  * FINGER_ERR_UNSUPPORTED.  Not an ablation: the matching statistics are those
  * of the FP32 tables. */
 #define FINGER_BUILD_HALF_CODES 4
+/* also store the same unit projections as FP8-e4m3 codes of 256 u (round to
+ * nearest even, saturating) for FINGER_MODE_FINGER_F8, in the same operand
+ * order with two k steps per 16 bytes, plus the tagged adjacency; build_lp
+ * builds them as well.  Needs n < 2^30, else FINGER_ERR_UNSUPPORTED. */
+#define FINGER_BUILD_FP8_CODES 8
 
 /* Algorithm 2 and Supplementary G on the device.  For every node c with at
  * least two layer-0 neighbours a pair (d, d') is drawn with the counter rule
@@ -264,14 +277,26 @@ finger_status finger_search_batch(finger_index* ix, const float* queries, int64_
                                   const int64_t* out_off, int64_t* out_ids, float* out_dists,
                                   void* stream);
 
-/* Autotuner for finger_search_batch: times the candidate launch shapes (warps
- * per block x visited-hash size) of the power-of-two ef bucket of `ef` on a
+/* Autotuner: times the candidate launch shapes (warps per block x visited-hash
+ * size x the kernel's register variant: the one with the most resident warps
+ * that shared memory admits and each one with fewer that the mode has) on a
  * sample batch (device queries, nq x m, uniform K and ef; scratch outputs of
- * nq x K) and keeps the fastest for later batches of that bucket.  The best
- * time in milliseconds is written to *best_ms when it is not NULL. */
+ * nq x K) in the current mode, and keeps the fastest for that mode and the
+ * power-of-two ef bucket of `ef` (16, 32, ..., 1024).  finger_search,
+ * finger_search_host and finger_search_batch then launch with it at any ef of
+ * that bucket where it fits (a batch plans for the bucket's largest ef), else
+ * with the default shape.  The best time in milliseconds is written to
+ * *best_ms when it is not NULL. */
 finger_status finger_autotune(finger_index* ix, const float* queries, int64_t nq, int K, int ef,
                               int64_t* scratch_ids, float* scratch_dists, float* best_ms,
                               void* stream);
+
+/* The autotuner's pick for the ef bucket of `ef` (any pointer may be NULL):
+ * warps per block, visited-hash slots, resident warps per SM and the best
+ * sample-batch time in milliseconds.  FINGER_ERR_NOT_BUILT when that bucket
+ * was not tuned (it then uses the default plan). */
+finger_status finger_get_tuned(const finger_index* ix, int ef, int* warps_per_block,
+                               int* hash_slots, int* resident_warps, float* best_ms);
 
 /* Cap on the layer-0 expansions (and upper-layer steps) of one query; a query
  * that reaches it stops, keeps its results so far and latches
@@ -405,9 +430,9 @@ typedef struct {
     double build_ms;        /* wall time of the last table build */
     double corr;            /* correlation of X and Y over the drawn pairs
                                (Supplementary E), NaN before a build */
-    int64_t code_bytes;     /* bytes of FP16 code blocks read by FINGER_MODE_FINGER_F16
-                               searches (a block's second half only for centres
-                               whose degree needs it) */
+    int64_t code_bytes;     /* bytes of code blocks read by the FINGER_F16, FINGER_F8
+                               and LP searches (a block's second half only for
+                               centres whose degree needs it) */
 } finger_stats;
 
 /* Synchronise the index's device and return the latched kernel status. */

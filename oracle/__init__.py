@@ -69,6 +69,8 @@ def lib():
         L.orc_estimate.argtypes = [P, P, P, i32, P, i32, P, i32]
         L.orc_half_round.argtypes = [ctypes.c_double]
         L.orc_half_round.restype = ctypes.c_double
+        L.orc_e4m3_round.argtypes = [ctypes.c_double]
+        L.orc_e4m3_round.restype = ctypes.c_double
         L.orc_estimate.restype = ctypes.c_double
         L.orc_estimate_mlp.argtypes = [P, P, P, i32, P, i32, P, P, ctypes.c_double, P, P]
         L.orc_estimate_mlp.restype = ctypes.c_double
@@ -192,7 +194,8 @@ class FingerParams:
     sigma_hat: float
     eps: float
     corr: float = float("nan")      # Pearson correlation of X and Y over S (Supp. E)
-    codes: int = 0                  # 16: the per-edge unit P d_res stored as binary16 codes
+    codes: int = 0                  # 16: the per-edge unit P d_res stored as binary16 codes;
+                                    # 8: 256 times it stored as FP8 E4M3 codes
 
     def stats(self):
         return np.array([self.mu, self.sigma, self.mu_hat, self.sigma_hat, self.eps], np.float64)
@@ -249,6 +252,13 @@ def half_round(x: float) -> float:
     """The oracle's rounding of a code to the nearest binary16 value (ties to
     even), as FINGER_F16 stores the per-edge unit residual projections."""
     return float(lib().orc_half_round(float(x)))
+
+
+def e4m3_round(x: float) -> float:
+    """The oracle's rounding to the nearest FP8 E4M3 value (ties to even,
+    saturating at +-448), as FINGER_F8 stores 256 times each unit residual
+    projection."""
+    return float(lib().orc_e4m3_round(float(x)))
 
 
 def estimate_mlp(q, c, d, fp: FingerParams, mlp_weights, mlp_eps: float = 0.0):

@@ -325,6 +325,25 @@ static double half_rne(double x) {
 
 double orc_half_round(double x) { return half_rne(x); }
 
+/* round to the nearest FP8 E4M3 value (ties to even), saturating at +-448:
+ * 4 exponent bits with bias 7 and 3 fraction bits, so the values in
+ * [2^e, 2^(e+1)) are spaced 2^(e-3) for e >= -6, and below 2^-6 the
+ * subnormals are spaced 2^-9 */
+static double e4m3_rne(double x) {
+    if (x == 0.0 || !isfinite(x)) return x;
+    int e;
+    frexp(fabs(x), &e);              /* |x| in [2^(e-1), 2^e) */
+    int q = e - 4;
+    if (q < -9) q = -9;
+    const double sp = ldexp(1.0, q);
+    double v = nearbyint(x / sp) * sp;
+    if (v > 448.0) v = 448.0;
+    if (v < -448.0) v = -448.0;
+    return v;
+}
+
+double orc_e4m3_round(double x) { return e4m3_rne(x); }
+
 /* round to the nearest bfloat16 (ties to even) through FP32 */
 static double bf16r(double x) {
     float f = (float)x;
@@ -388,6 +407,12 @@ static double appx_dist(const double* xc, const double* xd, int m, double cc, co
          * t_hat is its dot with the unit P q_res */
         that = 0.0;
         for (int k = 0; k < r; ++k) that += (Pq[k] / nq_) * half_rne(Pd[k] / nd_);
+    }
+    if (codes == 8 && nq_ > 0 && nd_ > 0) {
+        /* the stored code is 256 times the unit P d_res rounded to FP8 E4M3 */
+        that = 0.0;
+        for (int k = 0; k < r; ++k) that += (Pq[k] / nq_) * e4m3_rne(256.0 * Pd[k] / nd_);
+        that /= 256.0;
     }
     double t = (that - muh) * ratio + mu;
     t = t + eps;

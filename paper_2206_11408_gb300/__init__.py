@@ -18,10 +18,11 @@ import numpy as np
 from . import _build
 
 __all__ = ["Index", "lib", "MODE_PLAIN", "MODE_FINGER", "MODE_FINGER_LP", "MODE_FINGER_MLP",
-           "MODE_FINGER_F16",
+           "MODE_FINGER_F16", "MODE_FINGER_F8",
            "FingerError", "COUNTER_NAMES", "table_bytes"]
 
 MODE_PLAIN, MODE_FINGER, MODE_FINGER_LP, MODE_FINGER_MLP, MODE_FINGER_F16 = 0, 1, 2, 3, 4
+MODE_FINGER_F8 = 5
 COUNTER_NAMES = ("expansions", "examined", "estimates", "skipped", "exact", "admitted", "upper",
                  "gathered")
 STATUS = {0: "ok", 1: "invalid argument", 2: "i/o error", 3: "bad index file format",
@@ -48,7 +49,7 @@ class BuildParams(ctypes.Structure):
                 ("basis_host", ctypes.c_void_p), ("stats_host", ctypes.c_void_p),
                 ("build_lp", ctypes.c_int), ("flags", ctypes.c_int)]
 
-BUILD_NO_MATCHING, BUILD_NO_EPS, BUILD_HALF_CODES = 1, 2, 4
+BUILD_NO_MATCHING, BUILD_NO_EPS, BUILD_HALF_CODES, BUILD_FP8_CODES = 1, 2, 4, 8
 
 
 class TrainParams(ctypes.Structure):
@@ -61,7 +62,8 @@ class Info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("m", ctypes.c_int), ("deg0", ctypes.c_int),
                 ("M", ctypes.c_int), ("maxlevel", ctypes.c_int), ("entry", ctypes.c_int),
                 ("up_rows", ctypes.c_int64), ("r", ctypes.c_int), ("has_lp", ctypes.c_int),
-                ("has_mlp", ctypes.c_int), ("device_bytes", ctypes.c_int64)]
+                ("has_mlp", ctypes.c_int), ("device_bytes", ctypes.c_int64),
+                ("has_half_codes", ctypes.c_int), ("has_fp8_codes", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -109,6 +111,7 @@ SIGNATURES = {
     "finger_set_predictor": (_I, [_P, _P, _I64, _F]),
     "finger_get_predictor": (_I, [_P, _P, _P]),
     "finger_set_predictor_gate": (_I, [_P, _F]),
+    "finger_get_tuned": (_I, [_P, _I, _P, _P, _P, _P]),
     "finger_mlp_loss_grad": (_I, [_P, _I, _P, _P, _P, _I64, _P, _P, _P]),
     "finger_mlp_predict": (_I, [_P, _P, _I64, _P, _P]),
     "finger_merge_topk": (_I, [_P, _P, _I, _I64, _I, _P, _P, _P, _P]),
@@ -272,12 +275,13 @@ class Index:
     # ------------------------------------------------------------- tables
     def build_tables(self, r: int, seed: int, samples_per_node: int = 1, basis=None, stats=None,
                      build_lp: bool = False, matching: bool = True, use_eps: bool = True,
-                     half_codes: bool = False, stream=None):
+                     half_codes: bool = False, fp8_codes: bool = False, stream=None):
         """finger_build_tables.  ``basis`` (r x m) replaces the SVD basis (e.g.
         a random Gaussian matrix: the RPLSH comparison of Sec. 4.3); ``matching``
         and ``use_eps`` False are the ablations of FINGER_BUILD_NO_MATCHING and
         FINGER_BUILD_NO_EPS; ``half_codes`` also stores the FP16 codes of
-        MODE_FINGER_F16 (FINGER_BUILD_HALF_CODES)."""
+        MODE_FINGER_F16 (FINGER_BUILD_HALF_CODES), ``fp8_codes`` the FP8 codes
+        of MODE_FINGER_F8 (FINGER_BUILD_FP8_CODES)."""
         keep = []
         bp = None
         sp = None
@@ -290,18 +294,19 @@ class Index:
             keep.append(s)
             sp = _np_ptr(s)
         flags = ((0 if matching else BUILD_NO_MATCHING) | (0 if use_eps else BUILD_NO_EPS) |
-                 (BUILD_HALF_CODES if half_codes else 0))
+                 (BUILD_HALF_CODES if half_codes else 0) | (BUILD_FP8_CODES if fp8_codes else 0))
         p = BuildParams(r, seed, samples_per_node, bp, sp, int(build_lp), flags)
         _check(self._lib.finger_build_tables(self._h, ctypes.byref(p), _stream_ptr(stream)),
                "finger_build_tables")
 
     def select_rank(self, seed: int, threshold: float = 0.7, r_step: int = 8, r_max: int = 64,
                     samples_per_node: int = 1, build_lp: bool = False, half_codes: bool = False,
-                    stream=None):
+                    fp8_codes: bool = False, stream=None):
         """finger_select_rank: rank rule of Supplementary E, then the tables at
         that rank.  Returns (r, [correlation of each candidate tried])."""
         p = BuildParams(0, seed, samples_per_node, None, None, int(build_lp),
-                        BUILD_HALF_CODES if half_codes else 0)
+                        (BUILD_HALF_CODES if half_codes else 0) |
+                        (BUILD_FP8_CODES if fp8_codes else 0))
         r_out = ctypes.c_int()
         trace = np.full(-(-r_max // r_step), np.nan)
         _check(self._lib.finger_select_rank(self._h, ctypes.byref(p), ctypes.c_double(threshold),
@@ -415,6 +420,17 @@ class Index:
                                          _stream_ptr(stream)), "finger_autotune")
         return best.value
 
+
+    def tuned(self, ef: int) -> dict | None:
+        """finger_get_tuned: the autotuner's pick for ef's bucket, or None."""
+        w, h, o, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_float()
+        st = self._lib.finger_get_tuned(self._h, ef, ctypes.byref(w), ctypes.byref(h),
+                                        ctypes.byref(o), ctypes.byref(ms))
+        if st == 6:      # FINGER_ERR_NOT_BUILT: not tuned
+            return None
+        _check(st, "finger_get_tuned")
+        return {"warps_per_block": w.value, "hash_slots": h.value, "resident_warps": o.value,
+                "best_ms": ms.value}
     def knn(self, queries, K: int, stream=None):
         """Exact K nearest neighbours by brute force on the GPU."""
         import torch

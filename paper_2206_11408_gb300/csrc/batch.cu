@@ -21,7 +21,7 @@
 using namespace fg;
 
 finger_status fg_make_plan(finger_index* ix, int mode, int ef_max, int64_t nq, SearchPlan* p,
-                           int wpb, int H);
+                           int wpb, int H, int occ = 0);
 finger_status fg_run_search(finger_index* ix, const SearchPlan& p, SearchArgs& a, cudaStream_t s);
 SearchArgs fg_base_args(finger_index* ix, const SearchPlan& p);
 finger_status fg_check_mode_ready(const finger_index* ix, int mode);
@@ -99,7 +99,11 @@ finger_status finger_search_batch(finger_index* ix, const float* queries, int64_
     auto tit = ix->tuned.find(bucket);
     if (tit != ix->tuned.end() && tit->second.mode == ix->mode) {
         p = tit->second;
-        st = fg_make_plan(ix, ix->mode, bucket, nqb, &p, p.wpb, p.H);
+        st = fg_make_plan(ix, ix->mode, bucket, nqb, &p, p.wpb, p.H, p.occ);
+        if (st != FINGER_OK) {   // (not expected: the tuner ran this shape)
+            cudaGetLastError();
+            st = fg_make_plan(ix, ix->mode, bucket, nqb, &p, 4, 0);
+        }
     } else {
         st = fg_make_plan(ix, ix->mode, bucket, nqb, &p, 4, 0);
     }
@@ -191,7 +195,11 @@ finger_status finger_search_batch(finger_index* ix, const float* queries, int64_
 // Autotuner: time the candidate launch shapes of an ef bucket on a sample batch
 // (device queries, uniform K/ef) and keep the fastest for finger_search_batch.
 // Candidates: warps per block {2, 4, 8} x visited-hash slots {H/2, H, 2H}
-// around the default H.  Returns the best time in *best_ms (may be NULL).
+// around the default H x the kernel's register variants (the one with the
+// most resident warps that shared memory admits, and each one the mode has
+// with fewer: 64 / 80 / 96 registers, compiled for 32 / 24 / 20 resident
+// warps).  Returns the best time in *best_ms (may be NULL); finger_get_tuned
+// reads the pick back.
 finger_status finger_autotune(finger_index* ix, const float* queries, int64_t nq, int K, int ef,
                               int64_t* scratch_ids, float* scratch_dists, float* best_ms,
                               void* stream) {
@@ -205,8 +213,9 @@ finger_status finger_autotune(finger_index* ix, const float* queries, int64_t nq
     if (prev != ix->device) cudaSetDevice(ix->device);
     cudaStream_t s = (cudaStream_t)stream;
     const int bucket = std::min(bucket_of(ef), MAX_EF);
+    // planned at the sample's ef: the shape a uniform search at that ef uses
     SearchPlan def;
-    st = fg_make_plan(ix, ix->mode, bucket, nq, &def, 4, 0);
+    st = fg_make_plan(ix, ix->mode, ef, nq, &def, 4, 0);
     if (st != FINGER_OK) {
         if (prev != ix->device) cudaSetDevice(prev);
         return st;
@@ -218,10 +227,22 @@ finger_status finger_autotune(finger_index* ix, const float* queries, int64_t nq
     SearchPlan bestp = def;
     const int Hs[3] = {std::max(256, def.H / 2), def.H, std::min(16384, def.H * 2)};
     const int Ws[3] = {2, 4, 8};
+    const int Os[4] = {0, 8, 6, 5};   // 0: the largest variant that fits
     for (int wi = 0; wi < 3; ++wi)
-        for (int hi = 0; hi < 3; ++hi) {
+        for (int hi = 0; hi < 3; ++hi)
+            for (int oi = 0; oi < 4; ++oi) {
             SearchPlan p;
-            if (fg_make_plan(ix, ix->mode, bucket, nq, &p, Ws[wi], Hs[hi]) != FINGER_OK) continue;
+            if (fg_make_plan(ix, ix->mode, ef, nq, &p, Ws[wi], Hs[hi], Os[oi]) != FINGER_OK) {
+                cudaGetLastError();
+                continue;
+            }
+            if (oi > 0) {
+                // a forced variant only when it is smaller than the automatic one
+                SearchPlan a0;
+                if (fg_make_plan(ix, ix->mode, ef, nq, &a0, Ws[wi], Hs[hi], 0) == FINGER_OK &&
+                    Os[oi] >= a0.occ)
+                    continue;
+            }
             SearchArgs a = fg_base_args(ix, p);
             a.Q = queries;
             a.nq = nq;
@@ -244,14 +265,31 @@ finger_status finger_autotune(finger_index* ix, const float* queries, int64_t nq
                 best = tbest;
                 bestp = p;
             }
-        }
+            }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     ix->tuned[bucket] = bestp;
+    ix->tuned_ms[bucket] = best;
     fg_drop_captures(ix);
     if (best_ms) *best_ms = best;
     if (prev != ix->device) cudaSetDevice(prev);
     return cudaGetLastError() == cudaSuccess ? FINGER_OK : FINGER_ERR_CUDA;
+}
+
+finger_status finger_get_tuned(const finger_index* ix, int ef, int* warps_per_block,
+                               int* hash_slots, int* resident_warps, float* best_ms) {
+    if (!ix || ef < 1 || ef > MAX_EF) return FINGER_ERR_INVALID_ARG;
+    const int bucket = std::min(bucket_of(ef), MAX_EF);
+    auto it = ix->tuned.find(bucket);
+    if (it == ix->tuned.end() || it->second.mode != ix->mode) return FINGER_ERR_NOT_BUILT;
+    if (warps_per_block) *warps_per_block = it->second.wpb;
+    if (hash_slots) *hash_slots = it->second.H;
+    if (resident_warps) *resident_warps = it->second.bps * it->second.wpb;
+    if (best_ms) {
+        auto mt = ix->tuned_ms.find(bucket);
+        *best_ms = mt == ix->tuned_ms.end() ? 0.f : mt->second;
+    }
+    return FINGER_OK;
 }
 
 }  // extern "C"

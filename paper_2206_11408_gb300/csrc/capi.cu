@@ -25,6 +25,10 @@ cudaError_t launch_f16_k2(const DevIndex&, const SearchArgs&, const SearchPlan&,
 cudaError_t launch_f16_k4(const DevIndex&, const SearchArgs&, const SearchPlan&, cudaStream_t);
 cudaError_t occupancy_f16_k2(const SearchPlan&, int*);
 cudaError_t occupancy_f16_k4(const SearchPlan&, int*);
+cudaError_t launch_f8_k2(const DevIndex&, const SearchArgs&, const SearchPlan&, cudaStream_t);
+cudaError_t launch_f8_k4(const DevIndex&, const SearchArgs&, const SearchPlan&, cudaStream_t);
+cudaError_t occupancy_f8_k2(const SearchPlan&, int*);
+cudaError_t occupancy_f8_k4(const SearchPlan&, int*);
 cudaError_t launch_mode_harvest(const DevIndex&, const SearchArgs&, const SearchPlan&,
                                 cudaStream_t);
 cudaError_t occupancy_mode_harvest(const SearchPlan&, int*);
@@ -47,20 +51,25 @@ void choose_groups(int nchunks, int* G, int* VPL) {
     }
 }
 
+// the modes whose estimates are a tensor-core product with FP16 or FP8 codes
+bool code_mode(int mode) {
+    return mode == FINGER_MODE_FINGER_F16 || mode == FINGER_MODE_FINGER_LP ||
+           mode == FINGER_MODE_FINGER_F8;
+}
+
 // length (floats) of the unit query-residual projection u_q in shared memory:
-// the FP16-code mode reads it in chunks of 8 per code chunk, zero padded
+// the code modes hold its B fragments there, 16 words per k step
 int search_uq_len(const DevIndex& ix, int mode) {
     const int r_pad = ix.r4 * 4;
-    return mode == FINGER_MODE_FINGER_F16 || mode == FINGER_MODE_FINGER_LP
-               ? std::max(r_pad, 16 * ix.hks) : r_pad;
+    return code_mode(mode) ? std::max(r_pad, 16 * ix.hks) : r_pad;
 }
 
 int search_smem_per_warp(const DevIndex& ix, int mode, int ef_cap, int H, int NPL, int h16) {
     const int r_pad = ix.r4 * 4;
     const int uq_len = search_uq_len(ix, mode);
     const int qs_len = mode == FINGER_MODE_FINGER_LP ? ix.m8 * 8 : ix.m4 * 4;
-    // LP and FP16-code modes keep the staged query in a region of its own
-    const bool own_qs = mode == FINGER_MODE_FINGER_LP || mode == FINGER_MODE_FINGER_F16;
+    // the code modes keep the staged query in a region of its own
+    const bool own_qs = code_mode(mode);
     const int qs_bytes = own_qs ? 4 * ((qs_len + 3) & ~3) : 0;
     const int tile = mode == FINGER_MODE_FINGER_MLP ? 2 * 16 * (ix.mlp_kp + MLP_PAD) : 0;
     int b = 8 * ef_cap + (h16 ? 2 : 4) * H + 4 * (uq_len + r_pad) + qs_bytes + 32 * 32 * NPL +
@@ -76,6 +85,7 @@ cudaError_t launch_search(const DevIndex& ix, const SearchArgs& a, const SearchP
         case 2: return ix.hks == 2 ? launch_lp_k2(ix, a, p, s) : launch_lp_k4(ix, a, p, s);
         case 3: return launch_mode3(ix, a, p, s);
         case 4: return ix.hks == 2 ? launch_f16_k2(ix, a, p, s) : launch_f16_k4(ix, a, p, s);
+        case 5: return ix.hks == 2 ? launch_f8_k2(ix, a, p, s) : launch_f8_k4(ix, a, p, s);
         case MODE_HARVEST: return launch_mode_harvest(ix, a, p, s);
     }
     return cudaErrorInvalidValue;
@@ -88,6 +98,7 @@ cudaError_t search_occupancy(const DevIndex& ix, const SearchPlan& p, int* bps) 
         case 2: return ix.hks == 2 ? occupancy_lp_k2(p, bps) : occupancy_lp_k4(p, bps);
         case 3: return occupancy_mode3(p, bps);
         case 4: return ix.hks == 2 ? occupancy_f16_k2(p, bps) : occupancy_f16_k4(p, bps);
+        case 5: return ix.hks == 2 ? occupancy_f8_k2(p, bps) : occupancy_f8_k4(p, bps);
         case MODE_HARVEST: return occupancy_mode_harvest(p, bps);
     }
     return cudaErrorInvalidValue;
@@ -183,8 +194,11 @@ struct DeviceGuard {
 };
 
 // default launch plan for a mode and a bound on ef
+// default launch plan for a mode and a bound on ef; occ_force > 0 takes that
+// resident-block variant (the autotuner's choice) instead of the largest one
+// shared memory admits
 finger_status make_plan(finger_index* ix, int mode, int ef_max, int64_t nq, SearchPlan* p,
-                        int wpb = 4, int H = 0) {
+                        int wpb = 4, int H = 0, int occ_force = 0) {
     const DevIndex d = make_dev(ix);
     p->mode = mode;
     choose_groups(mode == FINGER_MODE_FINGER_LP ? ix->m8 : ix->m4, &p->G, &p->VPL);
@@ -209,25 +223,58 @@ finger_status make_plan(finger_index* ix, int mode, int ef_max, int64_t nq, Sear
     // LP and FP16 codes), else 5 (96 registers)
     int bps = 0;
     p->occ = 5;
-    for (int occ : {8, 6}) {
+    if (occ_force > 0) {
+        // the forced variant, at as many blocks as it admits
         SearchPlan t = *p;
-        t.occ = occ;
+        t.occ = occ_force;
         int b = 0;
-        if (search_occupancy(d, t, &b) == cudaSuccess && b >= occ) {
-            p->occ = occ;
-            bps = b;
-            break;
+        if (search_occupancy(d, t, &b) != cudaSuccess || b < 1) {
+            cudaGetLastError();
+            return FINGER_ERR_UNSUPPORTED;
         }
-        cudaGetLastError();
+        p->occ = occ_force;
+        bps = b;
+    } else {
+        for (int occ : {8, 6}) {
+            SearchPlan t = *p;
+            t.occ = occ;
+            int b = 0;
+            if (search_occupancy(d, t, &b) == cudaSuccess && b >= occ) {
+                p->occ = occ;
+                bps = b;
+                break;
+            }
+            cudaGetLastError();
+        }
     }
     if (p->occ == 5 && (search_occupancy(d, *p, &bps) != cudaSuccess || bps < 1)) {
         cudaGetLastError();
         return FINGER_ERR_UNSUPPORTED;
     }
+    p->bps = bps;
     int64_t blocks = (int64_t)ix->num_sms * bps;
     blocks = std::min<int64_t>(blocks, (nq + wpb - 1) / wpb);
     p->blocks = (int)std::max<int64_t>(blocks, 1);
     return FINGER_OK;
+}
+
+// The plan of a uniform search: the autotuner's launch shape when one was
+// kept for this mode and the power-of-two ef bucket of ef (finger_autotune),
+// else the default.
+finger_status make_search_plan(finger_index* ix, int ef, int64_t nq, SearchPlan* p) {
+    int bucket = 16;
+    while (bucket < ef) bucket <<= 1;
+    bucket = std::min(bucket, MAX_EF);
+    auto it = ix->tuned.find(bucket);
+    if (it != ix->tuned.end() && it->second.mode == ix->mode) {
+        SearchPlan t = it->second;
+        if (make_plan(ix, ix->mode, ef, nq, &t, t.wpb, t.H, t.occ) == FINGER_OK) {
+            *p = t;
+            return FINGER_OK;
+        }
+        cudaGetLastError();
+    }
+    return make_plan(ix, ix->mode, ef, nq, p);
 }
 
 finger_status ensure_scratch(finger_index* ix, int64_t slots) {
@@ -257,7 +304,9 @@ finger_status ensure_scratch(finger_index* ix, int64_t slots) {
 finger_status check_mode_ready(const finger_index* ix, int mode) {
     if (!ix->adj0) return FINGER_ERR_NOT_BUILT;
     if (mode != FINGER_MODE_PLAIN && !ix->edge_u) return FINGER_ERR_NOT_BUILT;
-    if (mode == FINGER_MODE_FINGER_LP && (!ix->edge_q || !ix->adj_t)) return FINGER_ERR_NOT_BUILT;
+    if (mode == FINGER_MODE_FINGER_LP && (!ix->Xh || !ix->edge_q || !ix->adj_t))
+        return FINGER_ERR_NOT_BUILT;
+    if (mode == FINGER_MODE_FINGER_F8 && (!ix->edge_q || !ix->adj_t)) return FINGER_ERR_NOT_BUILT;
     if (mode == FINGER_MODE_FINGER_F16 && (!ix->edge_h || !ix->adj_t)) return FINGER_ERR_NOT_BUILT;
     if (mode == FINGER_MODE_FINGER_MLP && !ix->has_mlp) return FINGER_ERR_NOT_BUILT;
     return FINGER_OK;
@@ -319,8 +368,8 @@ uint64_t wsum64(const void* p, size_t bytes) {
 
 // entry points shared with batch.cu
 finger_status fg_make_plan(finger_index* ix, int mode, int ef_max, int64_t nq, SearchPlan* p,
-                           int wpb, int H) {
-    return make_plan(ix, mode, ef_max, nq, p, wpb, H);
+                           int wpb, int H, int occ) {
+    return make_plan(ix, mode, ef_max, nq, p, wpb, H, occ);
 }
 finger_status fg_run_search(finger_index* ix, const SearchPlan& p, SearchArgs& a, cudaStream_t s) {
     return run_search(ix, p, a, s);
@@ -436,6 +485,7 @@ static void drop_tables(finger_index* ix) {
     ix->has_mlp = 0;
     ix->h_mlp.clear();
     ix->tuned.clear();
+    ix->tuned_ms.clear();
     fg_drop_captures(ix);
 }
 
@@ -543,13 +593,18 @@ finger_status finger_get_info(const finger_index* ix, finger_info* out) {
     out->entry = ix->entry;
     out->up_rows = ix->up_rows;
     out->r = ix->r;
-    out->has_lp = ix->edge_q != nullptr;
+    out->has_lp = ix->Xh != nullptr && ix->edge_q != nullptr;
+    out->has_half_codes = ix->edge_h != nullptr;
+    out->has_fp8_codes = ix->edge_q != nullptr;
     out->has_mlp = ix->has_mlp;
     int64_t b = ix->n * (ix->m_pad + 1) * 4;
     if (ix->adj0) b += ix->n * ix->deg0 * 4 + ix->n * 8 + ix->up_rows * ix->M * 4;
     if (ix->edge_u) b += ix->n * ix->r_pad * 4 + finger_table_bytes(ix->n, ix->deg0, ix->r_pad, 0);
-    if (ix->edge_q) b += finger_table_bytes(ix->n, ix->deg0, ix->r, 1) + ix->n * ix->m8 * 16;
-    if (ix->edge_h) b += ix->n * (ix->deg0 > 32 ? 4 : 2) * ix->hks * 512 + ix->n * ix->deg0 * 4;
+    const int64_t tiles = ix->deg0 > 32 ? 4 : 2;
+    if (ix->Xh) b += ix->n * ix->m8 * 16;
+    if (ix->edge_q) b += ix->n * tiles * ix->hks * 256;
+    if (ix->edge_h) b += ix->n * tiles * ix->hks * 512;
+    if (ix->adj_t) b += ix->n * ix->deg0 * 4;
     b += ix->bitmap_slots * ix->words * 4 + ix->bitmap_slots * ix->spill_cap * 4;
     out->device_bytes = b;
     return FINGER_OK;
@@ -560,6 +615,7 @@ finger_status finger_build_tables(finger_index* ix, const finger_build_params* p
     DeviceGuard g(ix->device);
     fg_drop_captures(ix);
     ix->tuned.clear();
+    ix->tuned_ms.clear();
     ix->has_mlp = 0;
     ix->h_mlp.clear();
     return build_tables(ix, p, (cudaStream_t)stream);
@@ -572,6 +628,7 @@ finger_status finger_select_rank(finger_index* ix, const finger_build_params* p,
     DeviceGuard g(ix->device);
     fg_drop_captures(ix);
     ix->tuned.clear();
+    ix->tuned_ms.clear();
     ix->has_mlp = 0;
     ix->h_mlp.clear();
     return select_rank(ix, p, threshold, r_step, r_max, r_out, corr_trace, (cudaStream_t)stream);
@@ -601,7 +658,7 @@ finger_status finger_get_tables(const finger_index* ix, float* P, double* stats,
 }
 
 finger_status finger_set_mode(finger_index* ix, int mode, int warmup) {
-    if (!ix || mode < 0 || mode > FINGER_MODE_FINGER_F16) return FINGER_ERR_INVALID_ARG;
+    if (!ix || mode < 0 || mode > FINGER_MODE_FINGER_F8) return FINGER_ERR_INVALID_ARG;
     ix->mode = mode;
     if (warmup >= 0) ix->warmup = warmup;
     return FINGER_OK;
@@ -635,7 +692,7 @@ finger_status finger_search(finger_index* ix, const float* queries, int64_t nq, 
     if (st != FINGER_OK) return st;
     DeviceGuard g(ix->device);
     SearchPlan p;
-    st = make_plan(ix, ix->mode, ef, nq, &p);
+    st = make_search_plan(ix, ef, nq, &p);
     if (st != FINGER_OK) return st;
     SearchArgs a = base_args(ix, p);
     a.Q = queries;
@@ -739,8 +796,8 @@ finger_status finger_get_stats(finger_index* ix, finger_stats* out) {
     out->eps = ix->stats[4];
     out->build_ms = ix->build_ms;
     out->corr = ix->corr;
-    // halves of FP16 code blocks read x bytes of a half (tiles x k steps x 512)
-    out->code_bytes = (int64_t)c[8] * (ix->deg0 > 32 ? 2 : 1) * ix->hks * 512;
+    // bytes of FP16 / FP8 code blocks read (the kernel counts them per half block)
+    out->code_bytes = (int64_t)c[8];
     return FINGER_OK;
 }
 

@@ -47,7 +47,7 @@ struct DevIndex {
     float alpha, beta;      // t = t_hat * alpha + beta
     // reduced precision
     const uint4* Xh;        // n x m8 (BF16)
-    // FP8-e4m3 codes of edge_u * code_scale (LP mode) in the same fragment order
+    // FP8-e4m3 codes of edge_u * code_scale (modes LP and FINGER_F8) in the same fragment order
     // as edge_h, two k steps per 16 bytes: per node 2 NPL tiles x hks / 2 x 32
     // lanes x 16 bytes
     const uint4* edge_q;
@@ -103,13 +103,16 @@ struct SearchArgs {
     int64_t hv_cap;
 };
 
-constexpr int MODE_HARVEST = 5;     // FINGER traversal that records predictor training data
+constexpr int MODE_HARVEST = 12;    // FINGER traversal that records predictor training data
 // kernel instances of the public mode FINGER_F16 by k steps of the code table
 constexpr int MODE_F16_K2 = 6;      // r <= 32
 constexpr int MODE_F16_K4 = 7;      // r <= 64
 // kernel instances of the public mode FINGER_LP (FP8 codes) by k steps
 constexpr int MODE_LP_K2 = 8;
 constexpr int MODE_LP_K4 = 9;
+// kernel instances of the public mode FINGER_F8 (FP32 rows, FP8 codes) by k steps
+constexpr int MODE_F8_K2 = 10;
+constexpr int MODE_F8_K4 = 11;
 
 struct SearchPlan {
     int mode;
@@ -118,7 +121,8 @@ struct SearchPlan {
     int blocks;
     int ef_cap, H;
     int h16;            // visited hash in 16-bit slots
-    int occ;            // resident blocks per SM the kernel variant is compiled for
+    int occ;            // resident blocks of 4 warps per SM the kernel variant is compiled for
+    int bps;            // resident blocks per SM of this plan (its register and shared-memory limit)
     int smem_per_warp;
     int blk_smem;       // per-block shared memory before the warp regions
 };
@@ -186,8 +190,8 @@ struct finger_index {
     uint64_t eig_seed = 0;
     int eig_spn = 0;
     // LP tables
-    __nv_bfloat16* Xh = nullptr;
-    uint8_t* edge_q = nullptr;   // fragment-order FP8 codes (see DevIndex)
+    __nv_bfloat16* Xh = nullptr;  // BF16 rows (mode LP)
+    uint8_t* edge_q = nullptr;   // fragment-order FP8 codes (modes LP and FINGER_F8, see DevIndex)
     // FP16 codes (fragment order, see DevIndex)
     uint16_t* edge_h = nullptr;
     int hks = 0;
@@ -224,6 +228,7 @@ struct finger_index {
     float* stage_d = nullptr;
     int64_t stage_cap_q = 0, stage_cap_o = 0;
     std::map<int, fg::SearchPlan> tuned;     // autotuned plans keyed by ef bucket
+    std::map<int, float> tuned_ms;           // their best sample-batch time
     int64_t searches = 0;
     double build_ms = 0;
     int64_t device_bytes = 0;

@@ -2,14 +2,14 @@
 //
 // File layout (little endian): a 128-byte header
 //   magic "FINGERIX", u32 version, u32 flags (1 = graph, 2 = tables, 4 = LP, 8 = MLP,
-//   16 = FP16 codes),
+//   16 = FP16 codes, 32 = FP8 codes without the LP rows),
 //   i64 n, i32 m, i32 deg0, i32 M, i32 maxlevel, i32 entry, i32 r, i64 up_rows,
 //   f64 stats[5], u64 checksum of the payload, zero padding
 // followed by the sections, each written only when its flag is set:
 //   vectors n*m f32 | level n i32, up_off n i64, adj0 n*deg0 i32, up_adj up_rows*M i32 |
 //   P r*m f32, node_proj n*r f32, edge_u (n*deg0)*r f32, edge_s (n*deg0)*2 f32 |
 //   mlp master weights (f32, count u64 first) and mlp_eps.
-// The LP tables and the FP16 codes are rebuilt from the FP32 tables on load.
+// The LP tables and the FP16 / FP8 codes are rebuilt from the FP32 tables on load.
 #include <stdio.h>
 #include <string.h>
 
@@ -23,6 +23,7 @@ using namespace fg;
 finger_status finger_load_mlp_internal(finger_index* ix, const float* w, int64_t count, float eps);
 cudaError_t lp_rebuild(finger_index* ix);
 cudaError_t half_rebuild(finger_index* ix);
+cudaError_t fp8_rebuild(finger_index* ix);
 
 namespace {
 
@@ -101,8 +102,9 @@ finger_status finger_index_save(const finger_index* ix, const char* path) {
     Header h{};
     memcpy(h.magic, "FINGERIX", 8);
     h.version = VERSION;
-    h.flags = (ix->adj0 ? 1u : 0u) | (ix->edge_u ? 2u : 0u) | (ix->edge_q ? 4u : 0u) |
-              (ix->has_mlp ? 8u : 0u) | (ix->edge_h ? 16u : 0u);
+    h.flags = (ix->adj0 ? 1u : 0u) | (ix->edge_u ? 2u : 0u) | (ix->Xh && ix->edge_q ? 4u : 0u) |
+              (ix->has_mlp ? 8u : 0u) | (ix->edge_h ? 16u : 0u) |
+              (!ix->Xh && ix->edge_q ? 32u : 0u);
     h.n = ix->n;
     h.m = ix->m;
     h.deg0 = ix->deg0;
@@ -262,6 +264,7 @@ finger_status finger_index_load(const char* path, int device, finger_index** out
         for (int i = 0; i < 5; ++i) ix->stats[i] = h.stats[i];
         if (ok && (h.flags & 4u)) ok = lp_rebuild(ix) == cudaSuccess;
         if (ok && (h.flags & 16u)) ok = half_rebuild(ix) == cudaSuccess;
+        if (ok && (h.flags & 32u)) ok = fp8_rebuild(ix) == cudaSuccess;
         cudaSetDevice(prev);
         if (!ok) {
             cudaGetLastError();

@@ -655,12 +655,15 @@ __device__ __forceinline__ void mlp_tile(const __nv_bfloat16* xt, int kp, const 
 template <int MODE, int G, int VPL, int NPL, int OCC>
 __global__ void __launch_bounds__(128, OCC) k_search(DevIndex ix, SearchArgs a) {
     constexpr bool LP = MODE == MODE_LP_K2 || MODE == MODE_LP_K4;   // BF16 rows, FP8 codes
+    constexpr bool W8 = LP || MODE == MODE_F8_K2 || MODE == MODE_F8_K4;   // FP8 codes
     constexpr bool EST = MODE != FINGER_MODE_PLAIN;
     constexpr bool MLP = MODE == FINGER_MODE_FINGER_MLP;
     constexpr bool HARV = MODE == MODE_HARVEST;
-    // FP16 (FINGER_F16) or FP8 (LP) codes, product on the tensor cores; k steps
-    constexpr bool WB = MODE == MODE_F16_K2 || MODE == MODE_F16_K4 || LP;
-    constexpr int WKS = MODE == MODE_F16_K2 || MODE == MODE_LP_K2 ? 2 : 4;
+    // FP16 (FINGER_F16) or FP8 (LP, FINGER_F8) codes, product on the tensor cores; k steps
+    constexpr bool WB = MODE == MODE_F16_K2 || MODE == MODE_F16_K4 || W8;
+    constexpr int WKS = MODE == MODE_F16_K2 || MODE == MODE_LP_K2 || MODE == MODE_F8_K2 ? 2 : 4;
+    // bytes of half a code block (the slots 16 NPL .. of a centre are the other half)
+    constexpr int HALF_BYTES = NPL * WKS * 512 / (W8 ? 2 : 1);
     constexpr int WNT = 2 * NPL;                            // tiles per node
     // ids in T: FP16-code mode ids carry the tag TAG (the node has more than
     // 16 NPL neighbours, so its code block's second half is needed) below EXP
@@ -871,7 +874,7 @@ __global__ void __launch_bounds__(128, OCC) k_search(DevIndex ix, SearchArgs a) 
                         scw[s] = j < ix.deg0 ? __ldg(ix.edge_s + (size_t)c * ix.deg0 + j)
                                              : make_float2(0.f, 0.f);
                     }
-                    wb_load<WKS, WNT, LP>(ix, c, 0, cfull, hx, lane);
+                    wb_load<WKS, WNT, W8>(ix, c, 0, cfull, hx, lane);
                     c_half += cfull ? 2 : 1;
                     // per-centre prep (Sec. 3.2 identity for q^T c, Supplementary G),
                     // then the product: the codes arrive with the adjacency row
@@ -892,15 +895,15 @@ __global__ void __launch_bounds__(128, OCC) k_search(DevIndex ix, SearchArgs a) 
                     wb_bfrag_store(bsm, u0 * inv, u1 * inv, WKS, lane);
                     __syncwarp();
                     float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-                    wb_mma<WKS, WNT, LP>(hx, bsm, 0, v, lane);
-                    if constexpr (!LP && WNT * WKS > 8) {   // second round: tiles 2, 3
+                    wb_mma<WKS, WNT, W8>(hx, bsm, 0, v, lane);
+                    if constexpr (!W8 && WNT * WKS > 8) {   // second round: tiles 2, 3
                         if (cfull) {
                             wb_load<WKS, WNT>(ix, c, 2, true, hx, lane);
                             wb_mma<WKS, WNT>(hx, bsm, 2, v, lane);
                         }
                     }
                     wb_route<NPL>(v, th, lane);
-                    if constexpr (LP) {   // the FP8 codes hold 256 u
+                    if constexpr (W8) {   // the FP8 codes hold 256 u
 #pragma unroll
                         for (int s = 0; s < NPL; ++s) th[s] *= ix.code_inv;
                     }
@@ -1422,7 +1425,7 @@ __global__ void __launch_bounds__(128, OCC) k_search(DevIndex ix, SearchArgs a) 
             atomicAdd(g + 5, (unsigned long long)c_adm);
             atomicAdd(g + 6, (unsigned long long)c_up);
             atomicAdd(g + 7, (unsigned long long)c_gath);
-            if (WB) atomicAdd(g + 8, (unsigned long long)c_half);
+            if (WB) atomicAdd(g + 8, (unsigned long long)c_half * HALF_BYTES);
             if (a.cnt_q) {
                 int32_t* cq = a.cnt_q + (size_t)qi * 8;
                 cq[0] = c_exp;
@@ -1441,11 +1444,11 @@ __global__ void __launch_bounds__(128, OCC) k_search(DevIndex ix, SearchArgs a) 
 
 // instantiate and dispatch one mode over the (G, VPL, NPL) variants and the
 // resident-block target: 5 blocks of 4 warps (96 registers) everywhere, 6 (80
-// registers) for the plain, FINGER, LP and FP16-code modes, 8 (64 registers)
+// registers) for the plain, FINGER, LP and FP16/FP8-code modes, 8 (64 registers)
 // for the plain mode.  The FINGER modes keep their gathers in flight in
 // registers and are fastest at 6 (the FP16-code mode measured slower at 7,
 // where it spills); plain search at 8.
-#define LP_MODE(m) ((m) == MODE_LP_K2 || (m) == MODE_LP_K4)
+#define LP_MODE(m) ((m) == MODE_LP_K2 || (m) == MODE_LP_K4 || (m) == MODE_F8_K2 || (m) == MODE_F8_K4)
 
 template <int MODE, int OCC>
 cudaError_t launch_occ(const DevIndex& ix, const SearchArgs& a, const SearchPlan& p,
@@ -1490,10 +1493,12 @@ cudaError_t occupancy_occ(const SearchPlan& p, int* blocks) {
     return cudaErrorInvalidValue;
 }
 
+#define F8_MODE(m) ((m) == MODE_F8_K2 || (m) == MODE_F8_K4)
+
 template <int MODE>
 cudaError_t launch_mode(const DevIndex& ix, const SearchArgs& a, const SearchPlan& p,
                         cudaStream_t s) {
-    if constexpr (MODE == FINGER_MODE_PLAIN)
+    if constexpr (MODE == FINGER_MODE_PLAIN || F8_MODE(MODE))
         if (p.occ == 8) return launch_occ<MODE, 8>(ix, a, p, s);
     if constexpr (MODE == FINGER_MODE_PLAIN || MODE == FINGER_MODE_FINGER ||
                   LP_MODE(MODE) || MODE == MODE_F16_K2 || MODE == MODE_F16_K4)
@@ -1506,7 +1511,7 @@ cudaError_t launch_mode(const DevIndex& ix, const SearchArgs& a, const SearchPla
 // mode does not have
 template <int MODE>
 cudaError_t occupancy_mode(const SearchPlan& p, int* blocks) {
-    if constexpr (MODE == FINGER_MODE_PLAIN)
+    if constexpr (MODE == FINGER_MODE_PLAIN || F8_MODE(MODE))
         if (p.occ == 8) return occupancy_occ<MODE, 8>(p, blocks);
     if constexpr (MODE == FINGER_MODE_PLAIN || MODE == FINGER_MODE_FINGER ||
                   LP_MODE(MODE) || MODE == MODE_F16_K2 || MODE == MODE_F16_K4)

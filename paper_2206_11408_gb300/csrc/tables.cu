@@ -720,34 +720,56 @@ cudaError_t build_tagged_adj(finger_index* ix) {
     return e;
 }
 
-// BF16 rows and FP8-e4m3 residual codes from the FP32 tables (mode LP): codes
+// FP8-e4m3 residual codes from the FP32 tables (modes LP and FINGER_F8): codes
 // of code_scale * u in the tensor cores' fragment order, per node 2 tiles of 16
-// slots (4 when deg0 > 32) x 1 (r <= 32) or 2 k pairs x 512 bytes
-cudaError_t lp_rebuild(finger_index* ix) {
+// slots (4 when deg0 > 32) x 1 (r <= 32) or 2 k pairs x 512 bytes, plus the
+// tagged adjacency
+cudaError_t fp8_rebuild(finger_index* ix) {
     using namespace fg;
-    cudaFree(ix->Xh);
     cudaFree(ix->edge_q);
-    ix->Xh = nullptr;
     ix->edge_q = nullptr;
     const int64_t n = ix->n;
+    if (n >= (int64_t(1) << 30)) return cudaErrorInvalidValue;
     const int hks = ix->r > 32 ? 4 : 2;
     const int tiles = ix->deg0 > 32 ? 4 : 2;
     const int64_t units = n * tiles * (hks / 2) * 32;
-    cudaError_t e = cudaMalloc(&ix->Xh, sizeof(__nv_bfloat16) * (size_t)n * ix->m8 * 8 + 16);
-    if (e != cudaSuccess) return e;
-    e = cudaMalloc(&ix->edge_q, sizeof(uint4) * (size_t)units + 16);
-    if (e != cudaSuccess) return e;
-    e = launch_to_bf16(ix->X, n, ix->m_pad, ix->m8, ix->Xh, 0);
-    if (e != cudaSuccess) return e;
+    cudaError_t e = cudaMalloc(&ix->edge_q, sizeof(uint4) * (size_t)units + 16);
+    if (e != cudaSuccess) {
+        ix->edge_q = nullptr;
+        return e;
+    }
     k_lp_codes<<<(unsigned)((units + 255) / 256), 256>>>(ix->edge_u, n, ix->deg0, ix->r_pad, tiles,
                                                          hks / 2, ix->code_scale,
                                                          reinterpret_cast<uint4*>(ix->edge_q));
     e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        cudaFree(ix->edge_q);
+        ix->edge_q = nullptr;
+        return e;
+    }
     ix->hks = hks;
-    e = cudaDeviceSynchronize();
-    if (e != cudaSuccess) return e;
     return build_tagged_adj(ix);
+}
+
+// BF16 rows (mode LP) and the FP8 codes
+cudaError_t lp_rebuild(finger_index* ix) {
+    using namespace fg;
+    cudaFree(ix->Xh);
+    ix->Xh = nullptr;
+    const int64_t n = ix->n;
+    cudaError_t e = cudaMalloc(&ix->Xh, sizeof(__nv_bfloat16) * (size_t)n * ix->m8 * 8 + 16);
+    if (e != cudaSuccess) {
+        ix->Xh = nullptr;
+        return e;
+    }
+    e = launch_to_bf16(ix->X, n, ix->m_pad, ix->m8, ix->Xh, 0);
+    if (e == cudaSuccess) e = fp8_rebuild(ix);
+    if (e != cudaSuccess) {
+        cudaFree(ix->Xh);
+        ix->Xh = nullptr;
+    }
+    return e;
 }
 
 // FP16 unit residual codes from the FP32 tables (mode FINGER_F16), in the
@@ -897,10 +919,12 @@ finger_status build_tables(finger_index* ix, const finger_build_params* p, cudaS
     if (!ix->adj0) return FINGER_ERR_NOT_BUILT;
     const int r = p->r;
     if (r < 1 || r > MAX_R || r > ix->m) return FINGER_ERR_INVALID_ARG;
-    if (p->flags & ~(FINGER_BUILD_NO_MATCHING | FINGER_BUILD_NO_EPS | FINGER_BUILD_HALF_CODES))
+    if (p->flags & ~(FINGER_BUILD_NO_MATCHING | FINGER_BUILD_NO_EPS | FINGER_BUILD_HALF_CODES |
+                     FINGER_BUILD_FP8_CODES))
         return FINGER_ERR_INVALID_ARG;
-    if ((p->flags & FINGER_BUILD_HALF_CODES || p->build_lp) && ix->n >= (int64_t(1) << 30))
-        return FINGER_ERR_UNSUPPORTED;   // the FP16-code and LP modes tag ids in bit 30
+    if ((p->flags & (FINGER_BUILD_HALF_CODES | FINGER_BUILD_FP8_CODES) || p->build_lp) &&
+        ix->n >= (int64_t(1) << 30))
+        return FINGER_ERR_UNSUPPORTED;   // the code modes tag ids in bit 30
     const int spn = p->samples_per_node > 0 ? p->samples_per_node : 1;
     const int64_t n = ix->n;
     const int m = ix->m, m_pad = ix->m_pad, m4 = ix->m4, deg0 = ix->deg0;
@@ -1005,6 +1029,10 @@ done:
         return FINGER_ERR_CUDA;
     }
     if ((p->flags & FINGER_BUILD_HALF_CODES) && half_rebuild(ix) != cudaSuccess) {
+        cudaGetLastError();
+        return FINGER_ERR_CUDA;
+    }
+    if ((p->flags & FINGER_BUILD_FP8_CODES) && !ix->edge_q && fp8_rebuild(ix) != cudaSuccess) {
         cudaGetLastError();
         return FINGER_ERR_CUDA;
     }

@@ -109,19 +109,60 @@ def test_uneven_batch_matches_single_searches(glove_like):
     ix.close()
 
 
-def test_autotune_then_batch(glove_like):
+@pytest.mark.parametrize("mode", [fg.MODE_PLAIN, fg.MODE_FINGER])
+def test_autotune_then_batch(glove_like, mode):
     X, Q, g, fp, gt = glove_like
     ix = _index(X, g, fp, 32)
-    ix.set_mode(fg.MODE_FINGER, 5)
+    ix.set_mode(mode, 5)
     q = torch.from_numpy(Q).cuda()
+    assert ix.tuned(64) is None
     ms = ix.autotune(q, 10, 64)
     assert ms > 0
+    # the pick of the ef bucket 64 (ef 33..64); other buckets stay untuned
+    pick = ix.tuned(40)
+    assert pick is not None and pick == ix.tuned(64)
+    assert pick["warps_per_block"] in (2, 4, 8)
+    assert pick["resident_warps"] % pick["warps_per_block"] == 0
+    assert 2 <= pick["resident_warps"] <= 64
+    assert pick["hash_slots"] >= 256 and pick["best_ms"] == pytest.approx(ms)
+    assert ix.tuned(65) is None and ix.tuned(32) is None
     K = torch.full((Q.shape[0],), 10, dtype=torch.int32, device="cuda")
     ef = torch.full((Q.shape[0],), 64, dtype=torch.int32, device="cuda")
     ids, d, off = ix.search_batch(q, K, ef)
     si, sd = ix.search(q, 10, 64)
     torch.cuda.synchronize()
     assert (ids.cpu().numpy().reshape(-1, 10) == si.cpu().numpy()).all()
+    ix.close()
+
+
+def test_fp8_codes_without_lp_rows(glove_like, tmp_path):
+    """FINGER_BUILD_FP8_CODES alone: mode FINGER_F8 runs, mode LP (which also
+    needs the BF16 rows) reports its tables missing, and a saved index rebuilds
+    the FP8 codes on load with identical results."""
+    X, Q, g, fp, gt = glove_like
+    ix = fg.Index(X)
+    ix.set_graph(g.adj0, g.level, g.up_off, g.up_adj, g.entry, g.maxlevel, g.M)
+    ix.build_tables(32, 4003, basis=fp.P, stats=fp.stats(), fp8_codes=True)
+    info = ix.info()
+    assert info["has_fp8_codes"] and not info["has_lp"] and not info["has_half_codes"]
+    q = torch.from_numpy(Q).cuda()
+    ix.set_mode(fg.MODE_FINGER_LP, 5)
+    with pytest.raises(fg.FingerError):
+        ix.search(q, 10, 40)
+    ix.set_mode(fg.MODE_FINGER_F8, 5)
+    a_ids, a_d = ix.search(q, 10, 40)
+    torch.cuda.synchronize()
+    ix.sync()
+    assert ix.stats()["code_bytes"] > 0
+    path = str(tmp_path / "f8.finger")
+    ix.save(path)
+    jx = fg.Index.load(path)
+    assert jx.info()["has_fp8_codes"] and not jx.info()["has_lp"]
+    jx.set_mode(fg.MODE_FINGER_F8, 5)
+    b_ids, b_d = jx.search(q, 10, 40)
+    torch.cuda.synchronize()
+    assert torch.equal(a_ids, b_ids) and torch.equal(a_d, b_d)
+    jx.close()
     ix.close()
 
 

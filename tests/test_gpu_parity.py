@@ -35,7 +35,7 @@ def cfg1():
     gt, gd = oracle.bruteforce(X, Q, 10)
     ix = fg.Index(X)
     ix.set_graph(g.adj0, g.level, g.up_off, g.up_adj, g.entry, g.maxlevel, g.M)
-    ix.build_tables(16, 4001, basis=fp.P, stats=fp.stats(), half_codes=True)
+    ix.build_tables(16, 4001, basis=fp.P, stats=fp.stats(), half_codes=True, fp8_codes=True)
     q = torch.from_numpy(Q).cuda()
     yield dict(X=X, Q=Q, g=g, fp=fp, pairs=pairs, gt=gt, gd=gd, ix=ix, q=q)
     ix.close()
@@ -50,8 +50,15 @@ def _f16(fp):
     return dataclasses.replace(fp, codes=16)
 
 
+def _f8(fp):
+    """The oracle's FINGER parameters with the per-edge codes stored as FP8 E4M3
+    codes of 256 u."""
+    return dataclasses.replace(fp, codes=8)
+
+
 def _modes(fp):
-    return ((fg.MODE_PLAIN, None), (fg.MODE_FINGER, fp), (fg.MODE_FINGER_F16, _f16(fp)))
+    return ((fg.MODE_PLAIN, None), (fg.MODE_FINGER, fp), (fg.MODE_FINGER_F16, _f16(fp)),
+            (fg.MODE_FINGER_F8, _f8(fp)))
 
 
 def test_bruteforce_knn_matches_oracle(cfg1):
@@ -87,9 +94,20 @@ def test_finger_f16_search_parity(cfg1, ef):
     assert gc[:, 3].sum() > 0
 
 
+@pytest.mark.parametrize("ef", [10, 20, 50, 100])
+def test_finger_f8_search_parity(cfg1, ef):
+    """FINGER with FP32 rows and the codes stored as FP8 E4M3 of 256 u against
+    the oracle's Algorithm 4 on the same FP8 codes."""
+    gi, gd, gc = _gpu_search(cfg1["ix"], cfg1["q"], 10, ef, fg.MODE_FINGER_F8)
+    oi, od, oc = oracle.search(cfg1["g"], cfg1["X"], cfg1["Q"], 10, ef, _f8(cfg1["fp"]))
+    _compare(gi, gd, gc, oi, od, oc, cfg1["gt"], 10, f"finger-f8 ef={ef}")
+    assert gc[:, 3].sum() > 0
+
+
 def test_alg4_hand_trace_on_gpu():
     """The hand-traced Algorithm 4 instance (tests/golden/alg4_hand_trace.json:
-    one estimate exactly equal to ub) through both FINGER modes of the kernel."""
+    one estimate exactly equal to ub) through the FINGER modes of the kernel
+    (r = 1: the unit codes are +-1, exact in FP16 and, as 256, in FP8)."""
     t = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "alg4_hand_trace.json")))
     names = sorted(t["ids"], key=t["ids"].get)
     X = np.array([t["points"][k] for k in names], np.float32)
@@ -102,9 +120,9 @@ def test_alg4_hand_trace_on_gpu():
     ix = fg.Index(X)
     ix.set_graph(adj, np.zeros(len(names), np.int32), np.full(len(names), -1, np.int64),
                  np.zeros((0, 1), np.int32), t["ids"][t["entry"]], 0, 1)
-    ix.build_tables(1, 1, basis=np.array(t["P"], np.float32), stats=stats, half_codes=True)
+    ix.build_tables(1, 1, basis=np.array(t["P"], np.float32), stats=stats, half_codes=True, fp8_codes=True)
     q = torch.tensor([t["query"]], dtype=torch.float32, device="cuda")
-    for mode in (fg.MODE_FINGER, fg.MODE_FINGER_F16):
+    for mode in (fg.MODE_FINGER, fg.MODE_FINGER_F16, fg.MODE_FINGER_F8):
         for key, warmup in (("warmup1_strict", 1), ("warmup2_strict", 2)):
             exp = t["expected"][key]
             ids, d, c = _gpu_search(ix, q, t["K"], t["ef"], mode, warmup)
@@ -215,7 +233,7 @@ def test_ragged_batch_and_odd_dimension():
     fp, _ = oracle.build_tables(X, g, 10, 5)
     ix = fg.Index(X)
     ix.set_graph(g.adj0, g.level, g.up_off, g.up_adj, g.entry, g.maxlevel, g.M)
-    ix.build_tables(10, 5, basis=fp.P, stats=fp.stats(), half_codes=True)
+    ix.build_tables(10, 5, basis=fp.P, stats=fp.stats(), half_codes=True, fp8_codes=True)
     q = torch.from_numpy(Q).cuda()
     for mode, f in _modes(fp):
         gi, gd, gc = _gpu_search(ix, q, 7, 33, mode)
@@ -233,7 +251,7 @@ def test_two_neighbour_slots_per_lane():
     fp, _ = oracle.build_tables(X, g, 16, 12)
     ix = fg.Index(X)
     ix.set_graph(g.adj0, g.level, g.up_off, g.up_adj, g.entry, g.maxlevel, g.M)
-    ix.build_tables(16, 12, basis=fp.P, stats=fp.stats(), half_codes=True)
+    ix.build_tables(16, 12, basis=fp.P, stats=fp.stats(), half_codes=True, fp8_codes=True)
     q = torch.from_numpy(Q).cuda()
     gt, _ = oracle.bruteforce(X, Q, 10)
     for mode, f in _modes(fp):
@@ -253,7 +271,7 @@ def test_wide_rows_k1_and_ef_equal_k():
     fp, _ = oracle.build_tables(X, g, 32, 22)
     ix = fg.Index(X)
     ix.set_graph(g.adj0, g.level, g.up_off, g.up_adj, g.entry, g.maxlevel, g.M)
-    ix.build_tables(32, 22, basis=fp.P, stats=fp.stats(), half_codes=True)
+    ix.build_tables(32, 22, basis=fp.P, stats=fp.stats(), half_codes=True, fp8_codes=True)
     q = torch.from_numpy(Q).cuda()
     for K, ef in ((1, 1), (1, 16), (10, 10), (10, 48)):
         gt, _ = oracle.bruteforce(X, Q, K)
@@ -274,7 +292,7 @@ def test_wide_codes_two_row_groups():
     fp, _ = oracle.build_tables(X, g, 64, 42)
     ix = fg.Index(X)
     ix.set_graph(g.adj0, g.level, g.up_off, g.up_adj, g.entry, g.maxlevel, g.M)
-    ix.build_tables(64, 42, basis=fp.P, stats=fp.stats(), half_codes=True)
+    ix.build_tables(64, 42, basis=fp.P, stats=fp.stats(), half_codes=True, fp8_codes=True)
     assert ix.info()["deg0"] == 64
     q = torch.from_numpy(Q).cuda()
     gt, _ = oracle.bruteforce(X, Q, 10)

@@ -7,7 +7,7 @@ ties), 500 fresh queries, HNSW M = 16 (layer-0 degree 32), efConstruction
 benchmark times at full size: exact rows on 16 lanes x 2 chunks, edge rows on
 16 lanes with the transpose-reduce of the row sums.
 
-1. FINGER (Algorithm 4; FP32 codes and binary16 codes) and plain search
+1. FINGER (Algorithm 4; FP32, binary16 and FP8 codes) and plain search
    (Algorithm 1) at ef 40 and 140 against the oracle, with the oracle's basis
    and matching statistics.
 2. The product path: FINGER tables built on the device from the graph alone
@@ -45,19 +45,21 @@ def sift_like():
     gt, _ = oracle.bruteforce(X, Q, 100)
     ix = fg.Index(X)
     ix.set_graph(g.adj0, g.level, g.up_off, g.up_adj, g.entry, g.maxlevel, g.M)
-    ix.build_tables(R, 4002, basis=fp.P, stats=fp.stats(), half_codes=True)
+    ix.build_tables(R, 4002, basis=fp.P, stats=fp.stats(), half_codes=True, fp8_codes=True)
     q = torch.from_numpy(Q).cuda()
     yield dict(X=X, Q=Q, g=g, fp=fp, gt=gt, ix=ix, q=q)
     ix.close()
 
 
 @pytest.mark.parametrize("ef", [40, 140])
-@pytest.mark.parametrize("mode", [fg.MODE_PLAIN, fg.MODE_FINGER, fg.MODE_FINGER_F16])
+@pytest.mark.parametrize("mode", [fg.MODE_PLAIN, fg.MODE_FINGER, fg.MODE_FINGER_F16,
+                                  fg.MODE_FINGER_F8])
 def test_benchmark_instance_parity(sift_like, mode, ef):
     s = sift_like
     gi, gd, gc = parity_util.gpu_search(s["ix"], s["q"], 10, ef, mode)
     fp = {fg.MODE_PLAIN: None, fg.MODE_FINGER: s["fp"],
-          fg.MODE_FINGER_F16: dataclasses.replace(s["fp"], codes=16)}[mode]
+          fg.MODE_FINGER_F16: dataclasses.replace(s["fp"], codes=16),
+          fg.MODE_FINGER_F8: dataclasses.replace(s["fp"], codes=8)}[mode]
     oi, od, oc = oracle.search(s["g"], s["X"], s["Q"], 10, ef, fp)
     parity_util.compare(gi, gd, gc, oi, od, oc, s["gt"][:, :10], 10,
                         f"mode {mode} m=128 r=64 ef={ef}")
@@ -88,7 +90,7 @@ def test_device_built_tables_product_path(sift_like):
     ix.close()
 
 
-@pytest.mark.parametrize("mode", [fg.MODE_PLAIN, fg.MODE_FINGER])
+@pytest.mark.parametrize("mode", [fg.MODE_PLAIN, fg.MODE_FINGER, fg.MODE_FINGER_F8])
 def test_uneven_batch_matches_oracle(sift_like, mode):
     s = sift_like
     ix = s["ix"]
@@ -102,7 +104,8 @@ def test_uneven_batch_matches_oracle(sift_like, mode):
     torch.cuda.synchronize()
     ix.sync()
     ids, d, off = ids.cpu().numpy(), d.cpu().numpy(), off.cpu().numpy()
-    fp = s["fp"] if mode == fg.MODE_FINGER else None
+    fp = {fg.MODE_PLAIN: None, fg.MODE_FINGER: s["fp"],
+          fg.MODE_FINGER_F8: dataclasses.replace(s["fp"], codes=8)}[mode]
     same, hits_g, hits_o, tot, worst = 0, 0, 0, 0, 0.0
     for i in range(nq):
         k = int(K[i])

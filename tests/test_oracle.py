@@ -108,6 +108,41 @@ def test_estimate_half_codes_hand_example():
     assert oracle.estimate(q, c, d, fp) == 32.998046875
 
 
+def test_fp8_codes_round_to_nearest_even_from_fp64():
+    """The FP8 E4M3 rounding of the stored codes (4 exponent bits, bias 7, 3
+    fraction bits, no infinities, largest finite 448): ties to even, subnormal
+    spacing 2^-9, saturation at +-448 as a satfinite conversion does."""
+    cases = {1.0: 1.0, 1.0625: 1.0,                 # tie between 1 and 1.125 -> even
+             1.1875: 1.25,                          # tie between 1.125 and 1.25 -> even
+             1.07: 1.125, 153.6: 160.0, 204.8: 208.0,   # spacing 16 in [128, 256)
+             2.0 ** -6: 2.0 ** -6,                  # smallest normal
+             2.0 ** -10: 0.0, 3 * 2.0 ** -10: 2.0 ** -8,  # subnormal ties -> even
+             5 * 2.0 ** -11: 2.0 ** -9,
+             448.0: 448.0, 464.0: 448.0, 500.0: 448.0, 1e6: 448.0}
+    for x, want in cases.items():
+        assert oracle.e4m3_round(x) == want and oracle.e4m3_round(-x) == -want, x
+    torch = pytest.importorskip("torch")
+    if not hasattr(torch, "float8_e4m3fn"):
+        pytest.skip("no FP8 dtype in this torch")
+    rng = np.random.default_rng(7)
+    x = rng.uniform(-1, 1, 20000) * 2.0 ** rng.uniform(-12, 8.7, 20000)   # |x| < 416
+    ref = torch.from_numpy(x).to(torch.float8_e4m3fn).to(torch.float64).numpy()
+    assert all(oracle.e4m3_round(v) == w for v, w in zip(x, ref))
+
+
+def test_estimate_fp8_codes_hand_example():
+    """Algorithm 3 with the edge's unit residual projection stored as FP8 E4M3
+    codes of 256 u.  Same triple as the binary16 example: u_d = (0.6, 0.8), so
+    the codes are e4m3(153.6) = 160 and e4m3(204.8) = 208, u_d is read back as
+    (0.625, 0.8125), t_hat = 0.625 against u_q = (1, 0), and the estimate
+    45 - 20 t is 32.5 instead of 33."""
+    P = np.array([[1.0, 0, 0], [0, 1.0, 0]])
+    q, c, d = np.array([2.0, 0, 1]), np.array([0, 0, 1.0]), np.array([3.0, 4, 5])
+    fp = _stats(P=P)
+    fp.codes = 8
+    assert oracle.estimate(q, c, d, fp) == 32.5
+
+
 def test_estimate_full_rank_is_exact_distance():
     """Eq. (2): with an orthogonal P (r = m) and identity matching the estimate
     is ||q - d||^2 exactly (the cross term q_proj^T q_res vanishes)."""
