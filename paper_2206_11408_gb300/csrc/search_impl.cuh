@@ -212,6 +212,77 @@ __device__ __forceinline__ int find_next(const uint32_t* Ti, int sz, int from, i
     return sz;
 }
 
+// Merge the sorted list A (ak / ai, na <= 32 NPL entries) into the sorted
+// T[0..tk): T[0..tk + na) afterwards (tk + na <= ef).  Each key of A finds its
+// rank in T by binary search; the entries of T above the smallest of those
+// ranks move up by the number of keys of A below them (the ranks at or below
+// their position), 32 at a time from the top; then the keys of A are written
+// at rank + index.  The scan cursor moves
+// back to the first position that changed.
+template <int NPL>
+__device__ __forceinline__ void t_merge(float* Tk, uint32_t* Ti, int tk, const float* ak,
+                                        const uint32_t* ai, int na, int ef, uint32_t idm,
+                                        int& cursor, int lane) {
+    int apt[NPL];         // rank of each key of A among T[0..tk)
+    float akd[NPL];
+    uint32_t aki[NPL];
+#pragma unroll
+    for (int t = 0; t < NPL; ++t) {
+        const int k = lane + 32 * t;
+        apt[t] = 0;
+        akd[t] = 0.f;
+        aki[t] = 0u;
+        if (k < na) {
+            akd[t] = ak[k];
+            aki[t] = ai[k];
+            int lo = 0, hi = tk;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (key_lt(Tk[mid], Ti[mid] & idm, akd[t], aki[t] & idm)) lo = mid + 1;
+                else hi = mid;
+            }
+            apt[t] = lo;
+        }
+    }
+    const int pmin = __shfl_sync(FULLMASK, apt[0], 0);   // A is sorted
+    for (int top = tk - 1; top >= pmin; top -= 32) {
+        const int i = top - lane;
+        const bool act = i >= pmin;
+        float kd = 0.f;
+        uint32_t ki = 0;
+        if (act) {
+            kd = Tk[i];
+            ki = Ti[i];
+        }
+        // the keys of A below T[i] are those whose rank in T is at most i
+        int sh = 0;
+        if (na == 1) {
+            sh = act ? 1 : 0;
+        } else {
+            for (int k = 0; k < na; ++k) {
+                const int r = __shfl_sync(FULLMASK, k < 32 ? apt[0] : apt[NPL - 1], k & 31);
+                sh += act && r <= i;
+            }
+        }
+        __syncwarp();
+        if (act && sh) {
+            Tk[CK(i + sh, ef, 1014)] = kd;
+            Ti[i + sh] = ki;
+        }
+        __syncwarp();
+    }
+#pragma unroll
+    for (int t = 0; t < NPL; ++t) {
+        const int k = lane + 32 * t;
+        if (k < na) {
+            Tk[CK(apt[t] + k, ef, 1015)] = akd[t];
+            Ti[apt[t] + k] = aki[t];
+        }
+    }
+    __syncwarp();
+    if (pmin < cursor) cursor = pmin;
+}
+
 // insert key (d, id) into the sorted list T (size sz <= ef), dropping the
 // worst entry when full.  Caller has checked admission.
 __device__ __forceinline__ void t_insert(float* Tk, uint32_t* Ti, int& sz, int ef, float d,
@@ -1132,6 +1203,7 @@ __global__ void __launch_bounds__(128, OCC) k_search(DevIndex ix, SearchArgs a) 
             }
             int nl = 0;
             bool needr[NPL];
+            float estv[NPL];
 #pragma unroll
             for (int s = 0; s < NPL; ++s) {
                 float est = -INFINITY;
@@ -1172,6 +1244,7 @@ __global__ void __launch_bounds__(128, OCC) k_search(DevIndex ix, SearchArgs a) 
                 needr[s] = need;
                 if (need) prefetch_row<LP>(ix, nb[s]);
                 es[s * 32 + lane] = est;
+                estv[s] = est;
                 const unsigned bm = __ballot_sync(FULLMASK, need);
                 if (need) lst[CK(nl + __popc(bm & ltmask), 32 * NPL, 1017)] = s * 32 + lane;
                 nl += __popc(bm);
@@ -1207,86 +1280,227 @@ __global__ void __launch_bounds__(128, OCC) k_search(DevIndex ix, SearchArgs a) 
                 const float u0d = Tk[ef - 1];
                 const uint32_t u0i = Ti[ef - 1] & IDM;
                 unsigned cb[NPL], cskip[NPL];
+                float xd[NPL];     // exact distance of each slot
+                int ncand = 0;
 #pragma unroll
                 for (int s = 0; s < NPL; ++s) {
                     const int o = s * 32 + lane;
-                    const bool cand = needr[s] && key_lt(xb[o], nb[s], u0d, u0i);
+                    xd[s] = xb[o];
+                    const bool cand = needr[s] && key_lt(xd[s], nb[s], u0d, u0i);
                     cb[s] = __ballot_sync(FULLMASK, cand);
                     cskip[s] = 0u;
+                    ncand += __popc(cb[s]);
                 }
-                // the serial replay runs on lane 0 only; results go through smem
-                if (lane == 0) {
+                int tk, na, nadm;
+                float myub[NPL];   // the running ub (distance) when the scan reaches each slot
+                if (ncand == 0) {
+                    tk = ef;
+                    na = 0;
+                    nadm = 0;
+#pragma unroll
+                    for (int t = 0; t < NPL; ++t) myub[t] = u0d;
+                } else if (ncand == 1) {
+                    // The first candidate in slot order is always admitted (its
+                    // estimate and key are below the starting ub); it pushes out
+                    // T's last entry, and ub becomes the larger of it and T[ef - 2].
+                    int s1 = 0;
+#pragma unroll
+                    for (int s = NPL - 1; s >= 0; --s)
+                        if (cb[s]) s1 = s;
+                    float xs = xd[0];
+                    uint32_t ns = nbt[0];
+                    unsigned bs = cb[0];
+#pragma unroll
+                    for (int s = 1; s < NPL; ++s)
+                        if (s == s1) {
+                            xs = xd[s];
+                            ns = nbt[s];
+                            bs = cb[s];
+                        }
+                    const int jj = __ffs(bs) - 1;
+                    const int o1 = s1 * 32 + jj;
+                    const float cd = __shfl_sync(FULLMASK, xs, jj);
+                    const uint32_t craw2 = __shfl_sync(FULLMASK, ns, jj);   // as stored in T
+                    float ubd = cd;
+                    uint32_t ubi = craw2 & IDM;
+                    if (ef >= 2) {
+                        const float td = Tk[ef - 2];
+                        const uint32_t ti = Ti[ef - 2] & IDM;
+                        if (key_lt(ubd, ubi, td, ti)) {
+                            ubd = td;
+                            ubi = ti;
+                        }
+                    }
+#pragma unroll
+                    for (int t = 0; t < NPL; ++t) myub[t] = t * 32 + lane <= o1 ? u0d : ubd;
+                    tk = ef - 1;
+                    na = 1;
+                    nadm = 1;
+                    if (lane == 0) {
+                        ak[0] = cd;
+                        ai[0] = craw2;
+                    }
+                    __syncwarp();
+                } else if (ncand < 32) {
+                    // Warp-parallel replay.  After j admissions the top ef is the
+                    // ef smallest keys of T and the admitted set A, so ub is the
+                    // (j+1)-th largest key of T's tail and A: lane p holds the
+                    // p-th largest of them (the pool, 32 deep, enough for j < 32),
+                    // lane j the j-th admission (the log).  Candidates are taken
+                    // in slot order as the sequential scan meets them.
+                    float pd = lane < ef ? Tk[ef - 1 - lane] : -1.f;   // -1: below any distance
+                    uint32_t pi = lane < ef ? Ti[ef - 1 - lane] & IDM : 0u;
+                    float ld = 0.f;
+                    uint32_t li = 0u;
                     float ubd = u0d;
                     uint32_t ubi = u0i;
-                    int tk = ef, na = 0, nadm = 0;
+                    int j = 0, prev = -1;
 #pragma unroll
                     for (int s = 0; s < NPL; ++s) {
                         unsigned bits = cb[s];
                         unsigned skm = 0u;
                         while (bits) {
-                            const int j = __ffs(bits) - 1;
+                            const int jj = __ffs(bits) - 1;
                             bits &= bits - 1;
-                            const int o = s * 32 + j;
-                            if (use_est && es[o] > ubd) {
-                                skm |= 1u << j;
+                            const int o = s * 32 + jj;
+#pragma unroll
+                            for (int t = 0; t < NPL; ++t) {
+                                const int so = t * 32 + lane;
+                                if (so > prev && so <= o) myub[t] = ubd;
+                            }
+                            prev = o;
+                            const float ce = __shfl_sync(FULLMASK, estv[s], jj);
+                            const float cd = __shfl_sync(FULLMASK, xd[s], jj);
+                            const uint32_t craw2 = __shfl_sync(FULLMASK, nbt[s], jj);   // as stored in T
+                            const uint32_t cid = craw2 & IDM;
+                            if (use_est && ce > ubd) {
+                                skm |= 1u << jj;
                                 continue;
                             }
-                            const float d = xb[CK(o, 32 * NPL, 1008)];
-                            const uint32_t idt = nbs[o];   // as stored in T
-                            const uint32_t id = idt & IDM;
-                            if (!key_lt(d, id, ubd, ubi)) continue;
-                            // the current worst of the top ef leaves it
-                            if (tk == 0 ||
-                                (na > 0 && key_lt(Tk[CK(tk - 1, ef, 1009)], Ti[tk - 1] & IDM,
-                                                  ak[CK(na - 1, 32 * NPL, 1010)], ai[na - 1] & IDM)))
-                                na--;
-                            else
-                                tk--;
-                            // insert (d, id) into the sorted admitted list
-                            int p = na;
-                            while (p > 0 && key_lt(d, id, ak[p - 1], ai[p - 1] & IDM)) {
-                                ak[CK(p, 32 * NPL, 1011)] = ak[p - 1];
-                                ai[p] = ai[p - 1];
-                                --p;
+                            if (!key_lt(cd, cid, ubd, ubi)) continue;
+                            // admit: log it, insert it into the descending pool
+                            if (lane == j) {
+                                ld = cd;
+                                li = craw2;
                             }
-                            ak[CK(p, 32 * NPL, 1012)] = d;
-                            ai[p] = idt;
-                            na++;
-                            // new ub: the larger of T[tk-1] and max(A)
-                            ubd = ak[na - 1];
-                            ubi = ai[na - 1] & IDM;
-                            if (tk > 0 && key_lt(ubd, ubi, Tk[tk - 1], Ti[tk - 1] & IDM)) {
-                                ubd = Tk[tk - 1];
-                                ubi = Ti[tk - 1] & IDM;
+                            const int pos = __popc(__ballot_sync(FULLMASK, key_lt(cd, cid, pd, pi)));
+                            const float sd = __shfl_up_sync(FULLMASK, pd, 1);
+                            const uint32_t si = __shfl_up_sync(FULLMASK, pi, 1);
+                            if (lane > pos) {
+                                pd = sd;
+                                pi = si;
+                            } else if (lane == pos) {
+                                pd = cd;
+                                pi = cid;
                             }
-                            apos[CK(nadm, 32 * NPL, 1013)] = o;
-                            aub[nadm] = ubd;
-                            nadm++;
+                            ++j;
+                            ubd = __shfl_sync(FULLMASK, pd, j);
+                            ubi = __shfl_sync(FULLMASK, pi, j);
                         }
-                        meta[3 + s] = (int)skm;
+                        cskip[s] = skm;
                     }
-                    meta[0] = tk;
-                    meta[1] = na;
-                    meta[2] = nadm;
-                }
-                __syncwarp();
-                const int tk = meta[0], na = meta[1], nadm = meta[2];
 #pragma unroll
-                for (int s = 0; s < NPL; ++s) cskip[s] = (unsigned)meta[3 + s];
+                    for (int t = 0; t < NPL; ++t)
+                        if (t * 32 + lane > prev) myub[t] = ubd;
+                    nadm = j;
+                    // the j largest keys left the top ef; an admitted key stays iff
+                    // it is below the smallest of them, pool[j - 1]
+                    const float thd = __shfl_sync(FULLMASK, pd, j > 0 ? j - 1 : 0);
+                    const uint32_t thi = __shfl_sync(FULLMASK, pi, j > 0 ? j - 1 : 0);
+                    const bool kept = lane < j && key_lt(ld, li & IDM, thd, thi);
+                    const unsigned bk = __ballot_sync(FULLMASK, kept);
+                    na = __popc(bk);
+                    tk = ef - na;
+                    // the kept admissions, ascending, into ak / ai for the merge
+                    int rk = 0;
+                    for (int t = 0; t < j; ++t) {
+                        const float od = __shfl_sync(FULLMASK, ld, t);
+                        const uint32_t oi = __shfl_sync(FULLMASK, li, t);
+                        rk += ((bk >> t) & 1u) && key_lt(od, oi & IDM, ld, li & IDM);
+                    }
+                    if (kept) {
+                        ak[rk] = ld;
+                        ai[rk] = li;
+                    }
+                    __syncwarp();
+                } else {
+                    // 32 or more candidates: the serial replay on lane 0, results
+                    // through shared memory
+                    if (lane == 0) {
+                        float ubd = u0d;
+                        uint32_t ubi = u0i;
+                        int tk = ef, na = 0, nadm = 0;
+#pragma unroll
+                        for (int s = 0; s < NPL; ++s) {
+                            unsigned bits = cb[s];
+                            unsigned skm = 0u;
+                            while (bits) {
+                                const int j = __ffs(bits) - 1;
+                                bits &= bits - 1;
+                                const int o = s * 32 + j;
+                                if (use_est && es[o] > ubd) {
+                                    skm |= 1u << j;
+                                    continue;
+                                }
+                                const float d = xb[CK(o, 32 * NPL, 1008)];
+                                const uint32_t idt = nbs[o];   // as stored in T
+                                const uint32_t id = idt & IDM;
+                                if (!key_lt(d, id, ubd, ubi)) continue;
+                                // the current worst of the top ef leaves it
+                                if (tk == 0 ||
+                                    (na > 0 && key_lt(Tk[CK(tk - 1, ef, 1009)], Ti[tk - 1] & IDM,
+                                                      ak[CK(na - 1, 32 * NPL, 1010)], ai[na - 1] & IDM)))
+                                    na--;
+                                else
+                                    tk--;
+                                // insert (d, id) into the sorted admitted list
+                                int p = na;
+                                while (p > 0 && key_lt(d, id, ak[p - 1], ai[p - 1] & IDM)) {
+                                    ak[CK(p, 32 * NPL, 1011)] = ak[p - 1];
+                                    ai[p] = ai[p - 1];
+                                    --p;
+                                }
+                                ak[CK(p, 32 * NPL, 1012)] = d;
+                                ai[p] = idt;
+                                na++;
+                                // new ub: the larger of T[tk-1] and max(A)
+                                ubd = ak[na - 1];
+                                ubi = ai[na - 1] & IDM;
+                                if (tk > 0 && key_lt(ubd, ubi, Tk[tk - 1], Ti[tk - 1] & IDM)) {
+                                    ubd = Tk[tk - 1];
+                                    ubi = Ti[tk - 1] & IDM;
+                                }
+                                apos[CK(nadm, 32 * NPL, 1013)] = o;
+                                aub[nadm] = ubd;
+                                nadm++;
+                            }
+                            meta[3 + s] = (int)skm;
+                        }
+                        meta[0] = tk;
+                        meta[1] = na;
+                        meta[2] = nadm;
+                    }
+                    __syncwarp();
+                    tk = meta[0];
+                    na = meta[1];
+                    nadm = meta[2];
+#pragma unroll
+                    for (int s = 0; s < NPL; ++s) {
+                        cskip[s] = (unsigned)meta[3 + s];
+                        const int o = s * 32 + lane;
+                        float ubt = u0d;
+                        for (int k = 0; k < nadm; ++k)
+                            if (apos[k] < o) ubt = aub[k];
+                        myub[s] = ubt;
+                    }
+                }
                 // counters of every new neighbour under the sequential semantics
 #pragma unroll
                 for (int s = 0; s < NPL; ++s) {
-                    const int o = s * 32 + lane;
                     bool skipped = false;
                     if (isnew[s]) {
-                        if ((cb[s] >> lane) & 1u) {
-                            skipped = (cskip[s] >> lane) & 1u;
-                        } else if (use_est) {
-                            float ubt = u0d;
-                            for (int k = 0; k < nadm; ++k)
-                                if (apos[k] < o) ubt = aub[k];
-                            skipped = es[o] > ubt;
-                        }
+                        if ((cb[s] >> lane) & 1u) skipped = (cskip[s] >> lane) & 1u;
+                        else if (use_est) skipped = estv[s] > myub[s];
                     }
                     const int nnew = __popc(__ballot_sync(FULLMASK, isnew[s]));
                     const int nsk = __popc(__ballot_sync(FULLMASK, skipped));
@@ -1297,63 +1511,50 @@ __global__ void __launch_bounds__(128, OCC) k_search(DevIndex ix, SearchArgs a) 
                 }
                 c_adm += nadm;
                 // merge A (sorted, na entries) into T[0..tk) -> T[0..ef)
-                if (na > 0) {
-                    int apt[NPL];         // rank of each admitted key among T[0..tk)
-                    float akd[NPL];
-                    uint32_t aki[NPL];
+                if (na > 0) t_merge<NPL>(Tk, Ti, tk, ak, ai, na, ef, IDM, cursor, lane);
+            } else {
+                unsigned bnew[NPL];
+                int nnew = 0;
 #pragma unroll
-                    for (int t = 0; t < NPL; ++t) {
-                        const int k = lane + 32 * t;
-                        apt[t] = 0;
-                        akd[t] = 0.f;
-                        aki[t] = 0u;
-                        if (k < na) {
-                            akd[t] = ak[k];
-                            aki[t] = ai[k];
-                            int lo = 0, hi = tk;
-                            while (lo < hi) {
-                                const int mid = (lo + hi) >> 1;
-                                if (key_lt(Tk[mid], Ti[mid] & IDM, akd[t], aki[t] & IDM)) lo = mid + 1;
-                                else hi = mid;
+                for (int s = 0; s < NPL; ++s) {
+                    bnew[s] = __ballot_sync(FULLMASK, isnew[s]);
+                    nnew += __popc(bnew[s]);
+                }
+                if (sz + nnew <= ef) {
+                    // T stays below ef until the last of them: every new neighbour
+                    // is admitted with no gate.  Rank them by key into ak / ai and
+                    // merge once.
+#pragma unroll
+                    for (int s = 0; s < NPL; ++s) {
+                        const float md = xb[s * 32 + lane];
+                        const uint32_t mi = nb[s];
+                        int rk = 0;
+#pragma unroll
+                        for (int s2 = 0; s2 < NPL; ++s2) {
+                            unsigned bits = bnew[s2];
+                            while (bits) {
+                                const int j = __ffs(bits) - 1;
+                                bits &= bits - 1;
+                                const int o = s2 * 32 + j;
+                                rk += key_lt(xb[o], nbs[o] & IDM, md, mi);
                             }
-                            apt[t] = lo;
                         }
-                    }
-                    const int pmin = __shfl_sync(FULLMASK, apt[0], 0);   // A is sorted
-                    for (int top = tk - 1; top >= pmin; top -= 32) {
-                        const int i = top - lane;
-                        const bool act = i >= pmin;
-                        float kd = 0.f;
-                        uint32_t ki = 0;
-                        int sh = 0;
-                        if (act) {
-                            kd = Tk[i];
-                            ki = Ti[i];
-                            for (int k = 0; k < na; ++k) sh += key_lt(ak[k], ai[k] & IDM, kd, ki & IDM);
-                        }
-                        __syncwarp();
-                        if (act && sh) {
-                            Tk[CK(i + sh, ef, 1014)] = kd;
-                            Ti[i + sh] = ki;
-                        }
-                        __syncwarp();
-                    }
-#pragma unroll
-                    for (int t = 0; t < NPL; ++t) {
-                        const int k = lane + 32 * t;
-                        if (k < na) {
-                            Tk[CK(apt[t] + k, ef, 1015)] = akd[t];
-                            Ti[apt[t] + k] = aki[t];
+                        if (isnew[s]) {
+                            ak[rk] = md;
+                            ai[rk] = nbt[s];   // as stored in T
                         }
                     }
                     __syncwarp();
-                    if (pmin < cursor) cursor = pmin;
-                }
-            } else {
-                // T not full at the start of this expansion: plain sequential replay
+                    c_exa += nnew;
+                    c_exact += nnew;
+                    c_adm += nnew;
+                    if (nnew > 0) t_merge<NPL>(Tk, Ti, sz, ak, ai, nnew, ef, IDM, cursor, lane);
+                    sz += nnew;
+                } else {
+                // T fills during this expansion: the sequential scan
 #pragma unroll
                 for (int s = 0; s < NPL; ++s) {
-                    unsigned bits = __ballot_sync(FULLMASK, isnew[s]);
+                    unsigned bits = bnew[s];
                     c_exa += __popc(bits);
                     while (bits) {
                         const int j = __ffs(bits) - 1;
@@ -1376,6 +1577,7 @@ __global__ void __launch_bounds__(128, OCC) k_search(DevIndex ix, SearchArgs a) 
                             c_adm++;
                         }
                     }
+                }
                 }
             }
             __syncwarp();
