@@ -7,7 +7,7 @@ shape of SIFT-1M); HNSW-style graph with M = 16 (layer-0 degree 32) built on the
 GPU from exact 200-nearest-neighbour candidates; FINGER rank r = 64; 10,000
 fresh queries from the same mixture; K = 10.
 
-Setup (untimed): data, graph, FINGER tables (FP32, and the FP16 codes),
+Setup (untimed): data, graph, FINGER tables (FP32, the FP16 and FP8 codes),
 exact ground truth by GPU brute force, then for every method an ef sweep and a
 step-2 refinement to find the smallest ef whose recall@10 reaches 0.95.  A
 step is one finger_search over the 10,000-query batch at that ef (one
@@ -15,7 +15,7 @@ persistent kernel launch).  `value` is queries/s of FINGER with FP16 codes
 (the fastest FINGER form: the per-edge codes in FP16, estimates as one
 tensor-core matrix-vector product, FP32 vectors and distances); `plain_qps`
 the same for plain greedy search at its own ef, `finger_f32_qps` FINGER on
-the FP32 tables.  The index (~14 GB) is far larger than L2, so no flush is
+the FP32 tables, `finger_f8_qps` FINGER with FP8-e4m3 codes.  The index (~14 GB) is far larger than L2, so no flush is
 needed between steps.
 
 Multi-GPU (torchrun): every rank holds a replica of the index and searches its
@@ -479,7 +479,7 @@ def leg_lp(args):
     gt_ids, _ = ix.knn(q, c.K)
     gt = gt_ids.cpu().numpy()
     modes = {"plain": fg.MODE_PLAIN, "finger": fg.MODE_FINGER, "finger_f16": fg.MODE_FINGER_F16,
-             "finger_lp": fg.MODE_FINGER_LP}
+             "finger_f8": fg.MODE_FINGER_F8, "finger_lp": fg.MODE_FINGER_LP}
     curves, choice = _sweep(ix, q, gt, c.K, modes, c.ef_grid, nq)
     res = {}
     ck = None
@@ -503,9 +503,10 @@ def leg_lp(args):
              "roofline": roof, "counters_per_query": cpq,
              "qps_at_recall_interp": {k: qps_at(v) for k, v in curves.items()},
              "finger_qps": res["finger"][0], "plain_qps": res["plain"][0],
-             "finger_f16_qps": res["finger_f16"][0],
+             "finger_f16_qps": res["finger_f16"][0], "finger_f8_qps": res["finger_f8"][0],
              "lp_over_plain": res["finger_lp"][0] / res["plain"][0],
              "f16_over_plain": res["finger_f16"][0] / res["plain"][0],
+             "f8_over_plain": res["finger_f8"][0] / res["plain"][0],
              "ef": {k: v[0] for k, v in choice.items()},
              "recall": {k: v[1] for k, v in choice.items()},
              "distance_error_vs_fp64": {"returned_fp32": {"max": float(rel32.max()),
@@ -644,7 +645,7 @@ def leg_batch(args):
                 ix.autotune(q[:2048], 10, min(bkt, 1000))
                 pk = ix.tuned(min(bkt, 1000))
                 picks[str(bkt)] = [pk["warps_per_block"], pk["hash_slots"], pk["resident_warps"],
-                                   round(pk["best_ms"], 3)]
+                                   pk["rows_per_warp"], round(pk["best_ms"], 3)]
         for start, size, Kt, eft, mx, _, off, tot in batches:   # warm-up pass: captures graphs
             ix.search_batch(q[start:start + size], Kt, eft, max_ef=mx, offsets=off, total=tot)
         torch.cuda.synchronize()
@@ -685,7 +686,8 @@ def leg_batch(args):
              "recall": {k: v[1] for k, v in choice.items()},
              "roofline": roof, "counters_per_query": cpq,
              "qps_at_recall_interp": {k: qps_at(v) for k, v in curves.items()},
-             # per ef bucket: [warps per block, hash slots, resident warps per SM, best ms]
+             # per ef bucket: [warps per block, hash slots, resident warps per SM,
+             # exact rows in flight per warp, best ms]
              "stream": {"queries": nq, "batches": len(plan), "plain": out["plain"],
                         "finger": out["finger"],
                         "finger_over_plain": out["finger"]["qps"] / out["plain"]["qps"]},
@@ -940,6 +942,7 @@ def extensions(args):
             torch.cuda.empty_cache()
         keep = {k: line.get(k) for k in (
             "value", "plain_qps", "finger_qps", "finger_f16_qps", "finger_f32_qps",
+            "finger_f8_qps", "f8_over_plain",
             "lp_over_plain", "f16_over_plain", "mlp_over_plain", "mlp_over_finger",
             "mlp_all_over_finger", "mlp_gate",
             "finger_over_plain", "finger_f32_over_plain", "ef", "recall",
@@ -1007,12 +1010,13 @@ def main():
     torch.cuda.synchronize()
     t_graph = time.perf_counter() - t0
     t0 = time.perf_counter()
-    ix.build_tables(c.r, 4000 + args.cfg, half_codes=True)
+    ix.build_tables(c.r, 4000 + args.cfg, half_codes=True, fp8_codes=True)
     torch.cuda.synchronize()
     t_tables = time.perf_counter() - t0
     info = ix.info()
     q = torch.from_numpy(Q).cuda()
-    MODES = {"plain": fg.MODE_PLAIN, "finger": fg.MODE_FINGER_F16, "finger_f32": fg.MODE_FINGER}
+    MODES = {"plain": fg.MODE_PLAIN, "finger": fg.MODE_FINGER_F16, "finger_f32": fg.MODE_FINGER,
+             "finger_f8": fg.MODE_FINGER_F8}
     if args.profile_ef:
         ix.set_mode(fg.MODE_FINGER_F16, 5)
         ids, d = ix.search(q, K, args.profile_ef)
@@ -1182,6 +1186,7 @@ def main():
             "config": {"workload": workload, "n": n, "m": c.m, "nq_per_gpu": nq, "K": K,
                        "M": c.M, "deg0": info["deg0"], "r": c.r, "ef_finger": efs["finger"],
                        "ef_plain": efs["plain"], "ef_finger_f32": efs["finger_f32"],
+                       "ef_finger_f8": efs["finger_f8"],
                        "finger": "FP16 unit residual codes (tensor-core matrix-vector "
                                  "estimate, FP32 accumulation), FP32 vectors and distances",
                        "graph": f"GPU {'single-layer' if args.flat else 'HNSW'}, insertion "
@@ -1195,6 +1200,8 @@ def main():
             "finger_over_plain": value / plain_qps,
             "finger_f32_qps": res["finger_f32"]["qps"],
             "finger_f32_over_plain": res["finger_f32"]["qps"] / plain_qps,
+            "recall_finger_f8": recs["finger_f8"], "finger_f8_qps": res["finger_f8"]["qps"],
+            "finger_f8_over_plain": res["finger_f8"]["qps"] / plain_qps,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_kind": peak_kind,

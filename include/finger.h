@@ -279,9 +279,11 @@ finger_status finger_search_batch(finger_index* ix, const float* queries, int64_
 
 /* Autotuner: times the candidate launch shapes (warps per block x visited-hash
  * size x the kernel's register variant: the one with the most resident warps
- * that shared memory admits and each one with fewer that the mode has) on a
- * sample batch (device queries, nq x m, uniform K and ef; scratch outputs of
- * nq x K) in the current mode, and keeps the fastest for that mode and the
+ * that shared memory admits and each one with fewer that the mode has x the
+ * exact-row shape: the default lanes per row, or rows on all 32 lanes, with
+ * fewer rows in flight per warp) on a sample batch (device queries, nq x m,
+ * uniform K and ef; scratch outputs of nq x K) in the current mode, and keeps
+ * the fastest for that mode and the
  * power-of-two ef bucket of `ef` (16, 32, ..., 1024).  finger_search,
  * finger_search_host and finger_search_batch then launch with it at any ef of
  * that bucket where it fits (a batch plans for the bucket's largest ef), else
@@ -291,12 +293,15 @@ finger_status finger_autotune(finger_index* ix, const float* queries, int64_t nq
                               int64_t* scratch_ids, float* scratch_dists, float* best_ms,
                               void* stream);
 
-/* The autotuner's pick for the ef bucket of `ef` (any pointer may be NULL):
- * warps per block, visited-hash slots, resident warps per SM and the best
- * sample-batch time in milliseconds.  FINGER_ERR_NOT_BUILT when that bucket
- * was not tuned (it then uses the default plan). */
+/* The autotuner's pick for the current mode and the ef bucket of `ef` (any
+ * pointer may be NULL): warps per block, visited-hash slots, resident warps
+ * per SM, exact rows in flight per warp (the staging depth of the row
+ * gathers) and the best sample-batch time in milliseconds.
+ * FINGER_ERR_NOT_BUILT when that bucket was not tuned in this mode (it then
+ * uses the default plan). */
 finger_status finger_get_tuned(const finger_index* ix, int ef, int* warps_per_block,
-                               int* hash_slots, int* resident_warps, float* best_ms);
+                               int* hash_slots, int* resident_warps, int* rows_per_warp,
+                               float* best_ms);
 
 /* Cap on the layer-0 expansions (and upper-layer steps) of one query; a query
  * that reaches it stops, keeps its results so far and latches

@@ -111,7 +111,7 @@ SIGNATURES = {
     "finger_set_predictor": (_I, [_P, _P, _I64, _F]),
     "finger_get_predictor": (_I, [_P, _P, _P]),
     "finger_set_predictor_gate": (_I, [_P, _F]),
-    "finger_get_tuned": (_I, [_P, _I, _P, _P, _P, _P]),
+    "finger_get_tuned": (_I, [_P, _I, _P, _P, _P, _P, _P]),
     "finger_mlp_loss_grad": (_I, [_P, _I, _P, _P, _P, _I64, _P, _P, _P]),
     "finger_mlp_predict": (_I, [_P, _P, _I64, _P, _P]),
     "finger_merge_topk": (_I, [_P, _P, _I, _I64, _I, _P, _P, _P, _P]),
@@ -423,13 +423,15 @@ class Index:
 
     def tuned(self, ef: int) -> dict | None:
         """finger_get_tuned: the autotuner's pick for ef's bucket, or None."""
-        w, h, o, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_float()
+        w, h, o, rw = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        ms = ctypes.c_float()
         st = self._lib.finger_get_tuned(self._h, ef, ctypes.byref(w), ctypes.byref(h),
-                                        ctypes.byref(o), ctypes.byref(ms))
+                                        ctypes.byref(o), ctypes.byref(rw), ctypes.byref(ms))
         if st == 6:      # FINGER_ERR_NOT_BUILT: not tuned
             return None
         _check(st, "finger_get_tuned")
         return {"warps_per_block": w.value, "hash_slots": h.value, "resident_warps": o.value,
+                "rows_per_warp": rw.value,
                 "best_ms": ms.value}
     def knn(self, queries, K: int, stream=None):
         """Exact K nearest neighbours by brute force on the GPU."""

@@ -21,7 +21,7 @@
 using namespace fg;
 
 finger_status fg_make_plan(finger_index* ix, int mode, int ef_max, int64_t nq, SearchPlan* p,
-                           int wpb, int H, int occ = 0);
+                           int wpb, int H, int occ = 0, int shape = 0);
 finger_status fg_run_search(finger_index* ix, const SearchPlan& p, SearchArgs& a, cudaStream_t s);
 SearchArgs fg_base_args(finger_index* ix, const SearchPlan& p);
 finger_status fg_check_mode_ready(const finger_index* ix, int mode);
@@ -99,7 +99,7 @@ finger_status finger_search_batch(finger_index* ix, const float* queries, int64_
     auto tit = ix->tuned.find(bucket);
     if (tit != ix->tuned.end() && tit->second.mode == ix->mode) {
         p = tit->second;
-        st = fg_make_plan(ix, ix->mode, bucket, nqb, &p, p.wpb, p.H, p.occ);
+        st = fg_make_plan(ix, ix->mode, bucket, nqb, &p, p.wpb, p.H, p.occ, p.shape);
         if (st != FINGER_OK) {   // (not expected: the tuner ran this shape)
             cudaGetLastError();
             st = fg_make_plan(ix, ix->mode, bucket, nqb, &p, 4, 0);
@@ -198,8 +198,10 @@ finger_status finger_search_batch(finger_index* ix, const float* queries, int64_
 // around the default H x the kernel's register variants (the one with the
 // most resident warps that shared memory admits, and each one the mode has
 // with fewer: 64 / 80 / 96 registers, compiled for 32 / 24 / 20 resident
-// warps).  Returns the best time in *best_ms (may be NULL); finger_get_tuned
-// reads the pick back.
+// warps) x the exact-row shape (the default groups of lanes per row, and rows
+// on all 32 lanes: fewer rows in flight per warp, the staging depth).
+// Returns the best time in *best_ms (may be NULL); finger_get_tuned reads
+// the pick back.
 finger_status finger_autotune(finger_index* ix, const float* queries, int64_t nq, int K, int ef,
                               int64_t* scratch_ids, float* scratch_dists, float* best_ms,
                               void* stream) {
@@ -230,9 +232,10 @@ finger_status finger_autotune(finger_index* ix, const float* queries, int64_t nq
     const int Os[4] = {0, 8, 6, 5};   // 0: the largest variant that fits
     for (int wi = 0; wi < 3; ++wi)
         for (int hi = 0; hi < 3; ++hi)
-            for (int oi = 0; oi < 4; ++oi) {
+            for (int oi = 0; oi < 4; ++oi)
+                for (int sh = 0; sh < 2; ++sh) {
             SearchPlan p;
-            if (fg_make_plan(ix, ix->mode, ef, nq, &p, Ws[wi], Hs[hi], Os[oi]) != FINGER_OK) {
+            if (fg_make_plan(ix, ix->mode, ef, nq, &p, Ws[wi], Hs[hi], Os[oi], sh) != FINGER_OK) {
                 cudaGetLastError();
                 continue;
             }
@@ -265,7 +268,7 @@ finger_status finger_autotune(finger_index* ix, const float* queries, int64_t nq
                 best = tbest;
                 bestp = p;
             }
-            }
+                }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     ix->tuned[bucket] = bestp;
@@ -277,7 +280,8 @@ finger_status finger_autotune(finger_index* ix, const float* queries, int64_t nq
 }
 
 finger_status finger_get_tuned(const finger_index* ix, int ef, int* warps_per_block,
-                               int* hash_slots, int* resident_warps, float* best_ms) {
+                               int* hash_slots, int* resident_warps, int* rows_per_warp,
+                               float* best_ms) {
     if (!ix || ef < 1 || ef > MAX_EF) return FINGER_ERR_INVALID_ARG;
     const int bucket = std::min(bucket_of(ef), MAX_EF);
     auto it = ix->tuned.find(bucket);
@@ -285,6 +289,7 @@ finger_status finger_get_tuned(const finger_index* ix, int ef, int* warps_per_bl
     if (warps_per_block) *warps_per_block = it->second.wpb;
     if (hash_slots) *hash_slots = it->second.H;
     if (resident_warps) *resident_warps = it->second.bps * it->second.wpb;
+    if (rows_per_warp) *rows_per_warp = rows_in_flight(it->second.G, it->second.VPL);
     if (best_ms) {
         auto mt = ix->tuned_ms.find(bucket);
         *best_ms = mt == ix->tuned_ms.end() ? 0.f : mt->second;

@@ -197,11 +197,22 @@ struct DeviceGuard {
 // default launch plan for a mode and a bound on ef; occ_force > 0 takes that
 // resident-block variant (the autotuner's choice) instead of the largest one
 // shared memory admits
+// shape 0: the row shape choose_groups picks; shape 1: rows on all 32 lanes
+// (fewer rows in flight, more chunks per load round), when that differs
 finger_status make_plan(finger_index* ix, int mode, int ef_max, int64_t nq, SearchPlan* p,
-                        int wpb = 4, int H = 0, int occ_force = 0) {
+                        int wpb = 4, int H = 0, int occ_force = 0, int shape = 0) {
     const DevIndex d = make_dev(ix);
     p->mode = mode;
-    choose_groups(mode == FINGER_MODE_FINGER_LP ? ix->m8 : ix->m4, &p->G, &p->VPL);
+    const int nchunks = mode == FINGER_MODE_FINGER_LP ? ix->m8 : ix->m4;
+    choose_groups(nchunks, &p->G, &p->VPL);
+    if (shape == 1) {
+        if (p->G == 32) return FINGER_ERR_UNSUPPORTED;   // already the widest
+        const int v = (nchunks + 31) / 32;
+        p->G = 32;
+        p->VPL = v <= 1 ? 1 : v <= 2 ? 2 : v <= 4 ? 4 : 8;
+    } else if (shape != 0) {
+        return FINGER_ERR_INVALID_ARG;
+    }
     p->NPL = ix->deg0 > 32 ? 2 : 1;
     p->ef_cap = (ef_max + 3) & ~3;
     if (H <= 0) H = pow2ceil(std::min(std::max(16 * ef_max, 512), 2048));
@@ -252,6 +263,7 @@ finger_status make_plan(finger_index* ix, int mode, int ef_max, int64_t nq, Sear
         return FINGER_ERR_UNSUPPORTED;
     }
     p->bps = bps;
+    p->shape = shape;
     int64_t blocks = (int64_t)ix->num_sms * bps;
     blocks = std::min<int64_t>(blocks, (nq + wpb - 1) / wpb);
     p->blocks = (int)std::max<int64_t>(blocks, 1);
@@ -268,7 +280,7 @@ finger_status make_search_plan(finger_index* ix, int ef, int64_t nq, SearchPlan*
     auto it = ix->tuned.find(bucket);
     if (it != ix->tuned.end() && it->second.mode == ix->mode) {
         SearchPlan t = it->second;
-        if (make_plan(ix, ix->mode, ef, nq, &t, t.wpb, t.H, t.occ) == FINGER_OK) {
+        if (make_plan(ix, ix->mode, ef, nq, &t, t.wpb, t.H, t.occ, t.shape) == FINGER_OK) {
             *p = t;
             return FINGER_OK;
         }
@@ -368,8 +380,8 @@ uint64_t wsum64(const void* p, size_t bytes) {
 
 // entry points shared with batch.cu
 finger_status fg_make_plan(finger_index* ix, int mode, int ef_max, int64_t nq, SearchPlan* p,
-                           int wpb, int H, int occ) {
-    return make_plan(ix, mode, ef_max, nq, p, wpb, H, occ);
+                           int wpb, int H, int occ, int shape) {
+    return make_plan(ix, mode, ef_max, nq, p, wpb, H, occ, shape);
 }
 finger_status fg_run_search(finger_index* ix, const SearchPlan& p, SearchArgs& a, cudaStream_t s) {
     return run_search(ix, p, a, s);

@@ -114,6 +114,13 @@ constexpr int MODE_LP_K4 = 9;
 constexpr int MODE_F8_K2 = 10;
 constexpr int MODE_F8_K4 = 11;
 
+// exact rows in flight per group of G lanes (VPL 16-byte chunks per lane)
+__host__ __device__ constexpr int rows_per_group(int VPL) { return VPL >= 8 ? 1 : VPL >= 4 ? 2 : 4; }
+// and per warp
+__host__ __device__ constexpr int rows_in_flight(int G, int VPL) {
+    return (32 / G) * rows_per_group(VPL);
+}
+
 struct SearchPlan {
     int mode;
     int G, VPL, NPL;
@@ -123,6 +130,7 @@ struct SearchPlan {
     int h16;            // visited hash in 16-bit slots
     int occ;            // resident blocks of 4 warps per SM the kernel variant is compiled for
     int bps;            // resident blocks per SM of this plan (its register and shared-memory limit)
+    int shape;          // row shape: 0 the default (G, VPL), 1 rows on all 32 lanes
     int smem_per_warp;
     int blk_smem;       // per-block shared memory before the warp regions
 };

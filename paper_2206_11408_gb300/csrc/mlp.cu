@@ -30,7 +30,7 @@
 using namespace fg;
 
 finger_status fg_make_plan(finger_index* ix, int mode, int ef_max, int64_t nq, SearchPlan* p,
-                           int wpb, int H, int occ = 0);
+                           int wpb, int H, int occ = 0, int shape = 0);
 finger_status fg_run_search(finger_index* ix, const SearchPlan& p, SearchArgs& a, cudaStream_t s);
 SearchArgs fg_base_args(finger_index* ix, const SearchPlan& p);
 void fg_drop_captures(const finger_index* ix);

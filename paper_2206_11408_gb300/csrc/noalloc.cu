@@ -48,7 +48,7 @@
 using namespace fg;
 
 finger_status fg_make_plan(finger_index* ix, int mode, int ef_max, int64_t nq, SearchPlan* p,
-                           int wpb, int H, int occ = 0);
+                           int wpb, int H, int occ = 0, int shape = 0);
 SearchArgs fg_base_args(finger_index* ix, const SearchPlan& p);
 finger_status fg_check_mode_ready(const finger_index* ix, int mode);
 

@@ -148,7 +148,7 @@ __device__ __forceinline__ void exact_list(const QRegs<LP, VPL>& qr, const float
     if constexpr (QS) load_qregs<LP, G, VPL>(qt, qs, LP ? ix.m8 : ix.m4, lane % G);
     const QRegs<LP, VPL>& q = QS ? qt : qr;
     constexpr int RPW = 32 / G;
-    constexpr int U = VPL >= 8 ? 1 : VPL >= 4 ? 2 : 4;   // rows per group in flight
+    constexpr int U = rows_per_group(VPL);   // rows per group in flight
     const int grp = lane / G, kin = lane % G;
     for (int base = 0; base < nlist; base += U * RPW) {
         int o[U];
@@ -1203,7 +1203,6 @@ __global__ void __launch_bounds__(128, OCC) k_search(DevIndex ix, SearchArgs a) 
             }
             int nl = 0;
             bool needr[NPL];
-            float estv[NPL];
 #pragma unroll
             for (int s = 0; s < NPL; ++s) {
                 float est = -INFINITY;
@@ -1244,7 +1243,6 @@ __global__ void __launch_bounds__(128, OCC) k_search(DevIndex ix, SearchArgs a) 
                 needr[s] = need;
                 if (need) prefetch_row<LP>(ix, nb[s]);
                 es[s * 32 + lane] = est;
-                estv[s] = est;
                 const unsigned bm = __ballot_sync(FULLMASK, need);
                 if (need) lst[CK(nl + __popc(bm & ltmask), 32 * NPL, 1017)] = s * 32 + lane;
                 nl += __popc(bm);
@@ -1281,11 +1279,13 @@ __global__ void __launch_bounds__(128, OCC) k_search(DevIndex ix, SearchArgs a) 
                 const uint32_t u0i = Ti[ef - 1] & IDM;
                 unsigned cb[NPL], cskip[NPL];
                 float xd[NPL];     // exact distance of each slot
+                float estv[NPL];   // estimate of each slot (read back: no register across the gathers)
                 int ncand = 0;
 #pragma unroll
                 for (int s = 0; s < NPL; ++s) {
                     const int o = s * 32 + lane;
                     xd[s] = xb[o];
+                    estv[s] = es[o];
                     const bool cand = needr[s] && key_lt(xd[s], nb[s], u0d, u0i);
                     cb[s] = __ballot_sync(FULLMASK, cand);
                     cskip[s] = 0u;

@@ -123,6 +123,7 @@ def test_autotune_then_batch(glove_like, mode):
     assert pick is not None and pick == ix.tuned(64)
     assert pick["warps_per_block"] in (2, 4, 8)
     assert pick["resident_warps"] % pick["warps_per_block"] == 0
+    assert pick["rows_per_warp"] in (4, 8)      # m = 100: 16 lanes x 2 chunks, or 32 x 1
     assert 2 <= pick["resident_warps"] <= 64
     assert pick["hash_slots"] >= 256 and pick["best_ms"] == pytest.approx(ms)
     assert ix.tuned(65) is None and ix.tuned(32) is None
