@@ -283,43 +283,6 @@ __device__ __forceinline__ void t_merge(float* Tk, uint32_t* Ti, int tk, const f
     if (pmin < cursor) cursor = pmin;
 }
 
-// insert key (d, id) into the sorted list T (size sz <= ef), dropping the
-// worst entry when full.  Caller has checked admission.
-__device__ __forceinline__ void t_insert(float* Tk, uint32_t* Ti, int& sz, int ef, float d,
-                                         uint32_t id, int& cursor, int lane,
-                                         uint32_t idm = ~EXP) {
-    int p = 0;
-    for (int b = 0; b < sz; b += 32) {
-        const int i = b + lane;
-        const bool lt = i < sz && key_lt(Tk[i], Ti[i] & idm, d, id & idm);
-        p += __popc(__ballot_sync(FULLMASK, lt));
-    }
-    const int last = sz < ef ? sz : ef - 1;
-    for (int top = last - 1; top >= p; top -= 32) {
-        const int i = top - lane;
-        const bool act = i >= p;
-        float kd = 0.f;
-        uint32_t ki = 0;
-        if (act) {
-            kd = Tk[i];
-            ki = Ti[i];
-        }
-        __syncwarp();
-        if (act) {
-            Tk[i + 1] = kd;
-            Ti[i + 1] = ki;
-        }
-        __syncwarp();
-    }
-    if (lane == 0) {
-        Tk[p] = d;
-        Ti[p] = id;
-    }
-    __syncwarp();
-    if (sz < ef) sz++;
-    if (p < cursor) cursor = p;
-}
-
 enum { V_SEEN = 0, V_NEW = 1, V_NEW_SPILL = 2, V_PENDING = 3 };
 
 // The visited hash in shared memory is bucketed: H slots form H/4 buckets of
@@ -1270,7 +1233,62 @@ __global__ void __launch_bounds__(128, OCC) k_search(DevIndex ix, SearchArgs a) 
                 }
             }
 
-            if (full0) {
+            // New neighbours met while T is below ef are admitted with no gate:
+            // the first ef - |T| of them in slot order are rank-sorted into
+            // ak / ai and merged at once.  The rest, met once T is full (all of
+            // them when it was full at the start), go through the gate replay.
+            bool gate[NPL];
+            bool replay = full0;
+#pragma unroll
+            for (int s = 0; s < NPL; ++s) gate[s] = isnew[s];
+            if (!full0) {
+                unsigned bnew[NPL], bfill[NPL];
+                int nnew = 0;
+#pragma unroll
+                for (int s = 0; s < NPL; ++s) {
+                    bnew[s] = __ballot_sync(FULLMASK, isnew[s]);
+                    nnew += __popc(bnew[s]);
+                }
+                const int f = min(nnew, ef - sz);
+                bool fill[NPL];
+                int before = 0;
+#pragma unroll
+                for (int s = 0; s < NPL; ++s) {
+                    const int idx = before + __popc(bnew[s] & ltmask);
+                    fill[s] = isnew[s] && idx < f;
+                    gate[s] = isnew[s] && idx >= f;
+                    bfill[s] = __ballot_sync(FULLMASK, fill[s]);
+                    before += __popc(bnew[s]);
+                }
+#pragma unroll
+                for (int s = 0; s < NPL; ++s) {
+                    const float md = xb[s * 32 + lane];
+                    const uint32_t mi = nb[s];
+                    int rk = 0;
+#pragma unroll
+                    for (int s2 = 0; s2 < NPL; ++s2) {
+                        unsigned bits = bfill[s2];
+                        while (bits) {
+                            const int j = __ffs(bits) - 1;
+                            bits &= bits - 1;
+                            const int o = s2 * 32 + j;
+                            rk += key_lt(xb[o], nbs[o] & IDM, md, mi);
+                        }
+                    }
+                    if (fill[s]) {
+                        ak[rk] = md;
+                        ai[rk] = nbt[s];   // as stored in T
+                    }
+                }
+                __syncwarp();
+                c_exa += f;
+                c_exact += f;
+                c_adm += f;
+                if (f > 0) t_merge<NPL>(Tk, Ti, sz, ak, ai, f, ef, IDM, cursor, lane);
+                sz += f;
+                replay = nnew > f;   // T is full now and new neighbours remain
+            }
+            if (replay) {
                 // T is full and stays full.  Only neighbours evaluated exactly and
                 // below the starting ub can be admitted; replay the sequential gate
                 // over them with a running model of ub (top-ef of T and the admitted
@@ -1286,7 +1304,7 @@ __global__ void __launch_bounds__(128, OCC) k_search(DevIndex ix, SearchArgs a) 
                     const int o = s * 32 + lane;
                     xd[s] = xb[o];
                     estv[s] = es[o];
-                    const bool cand = needr[s] && key_lt(xd[s], nb[s], u0d, u0i);
+                    const bool cand = gate[s] && needr[s] && key_lt(xd[s], nb[s], u0d, u0i);
                     cb[s] = __ballot_sync(FULLMASK, cand);
                     cskip[s] = 0u;
                     ncand += __popc(cb[s]);
@@ -1498,11 +1516,11 @@ __global__ void __launch_bounds__(128, OCC) k_search(DevIndex ix, SearchArgs a) 
 #pragma unroll
                 for (int s = 0; s < NPL; ++s) {
                     bool skipped = false;
-                    if (isnew[s]) {
+                    if (gate[s]) {
                         if ((cb[s] >> lane) & 1u) skipped = (cskip[s] >> lane) & 1u;
                         else if (use_est) skipped = estv[s] > myub[s];
                     }
-                    const int nnew = __popc(__ballot_sync(FULLMASK, isnew[s]));
+                    const int nnew = __popc(__ballot_sync(FULLMASK, gate[s]));
                     const int nsk = __popc(__ballot_sync(FULLMASK, skipped));
                     c_exa += nnew;
                     if (use_est) c_est += nnew;
@@ -1512,73 +1530,6 @@ __global__ void __launch_bounds__(128, OCC) k_search(DevIndex ix, SearchArgs a) 
                 c_adm += nadm;
                 // merge A (sorted, na entries) into T[0..tk) -> T[0..ef)
                 if (na > 0) t_merge<NPL>(Tk, Ti, tk, ak, ai, na, ef, IDM, cursor, lane);
-            } else {
-                unsigned bnew[NPL];
-                int nnew = 0;
-#pragma unroll
-                for (int s = 0; s < NPL; ++s) {
-                    bnew[s] = __ballot_sync(FULLMASK, isnew[s]);
-                    nnew += __popc(bnew[s]);
-                }
-                if (sz + nnew <= ef) {
-                    // T stays below ef until the last of them: every new neighbour
-                    // is admitted with no gate.  Rank them by key into ak / ai and
-                    // merge once.
-#pragma unroll
-                    for (int s = 0; s < NPL; ++s) {
-                        const float md = xb[s * 32 + lane];
-                        const uint32_t mi = nb[s];
-                        int rk = 0;
-#pragma unroll
-                        for (int s2 = 0; s2 < NPL; ++s2) {
-                            unsigned bits = bnew[s2];
-                            while (bits) {
-                                const int j = __ffs(bits) - 1;
-                                bits &= bits - 1;
-                                const int o = s2 * 32 + j;
-                                rk += key_lt(xb[o], nbs[o] & IDM, md, mi);
-                            }
-                        }
-                        if (isnew[s]) {
-                            ak[rk] = md;
-                            ai[rk] = nbt[s];   // as stored in T
-                        }
-                    }
-                    __syncwarp();
-                    c_exa += nnew;
-                    c_exact += nnew;
-                    c_adm += nnew;
-                    if (nnew > 0) t_merge<NPL>(Tk, Ti, sz, ak, ai, nnew, ef, IDM, cursor, lane);
-                    sz += nnew;
-                } else {
-                // T fills during this expansion: the sequential scan
-#pragma unroll
-                for (int s = 0; s < NPL; ++s) {
-                    unsigned bits = bnew[s];
-                    c_exa += __popc(bits);
-                    while (bits) {
-                        const int j = __ffs(bits) - 1;
-                        bits &= bits - 1;
-                        const int o = s * 32 + j;
-                        const bool full = sz == ef;
-                        if (use_est && full) {
-                            c_est++;
-                            if (es[o] > Tk[ef - 1]) {
-                                c_skip++;
-                                continue;
-                            }
-                        }
-                        const float d = xb[o];
-                        const uint32_t idt = nbs[o];   // as stored in T
-                        c_exact++;
-                        if (!full || key_lt(d, idt & IDM, Tk[sz - 1], Ti[sz - 1] & IDM)) {
-                            CK(sz, ef + 1, 1016);
-                            t_insert(Tk, Ti, sz, ef, d, idt, cursor, lane, IDM);
-                            c_adm++;
-                        }
-                    }
-                }
-                }
             }
             __syncwarp();
         }
