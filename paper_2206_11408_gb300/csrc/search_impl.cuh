@@ -202,12 +202,25 @@ __device__ __forceinline__ float exact_f32_row(const float* qs, const DevIndex& 
     return warp_sum(acc);
 }
 
-__device__ __forceinline__ int find_next(const uint32_t* Ti, int sz, int from, int lane) {
+// first unexpanded entry of T at or after `from` (sz if none), with the entry
+// itself (id as stored, distance) taken from the lane that loaded it
+__device__ __forceinline__ int find_next_entry(const float* Tk, const uint32_t* Ti, int sz,
+                                               int from, int lane, uint32_t& raw, float& d) {
     for (int b = from; b < sz; b += 32) {
         const int i = b + lane;
-        const bool un = i < sz && !(Ti[i] & EXP);
-        const unsigned m = __ballot_sync(FULLMASK, un);
-        if (m) return b + __ffs(m) - 1;
+        uint32_t v = EXP;
+        float kd = 0.f;
+        if (i < sz) {
+            v = Ti[i];
+            kd = Tk[i];
+        }
+        const unsigned m = __ballot_sync(FULLMASK, !(v & EXP));
+        if (m) {
+            const int src = __ffs(m) - 1;
+            raw = __shfl_sync(FULLMASK, v, src);
+            d = __shfl_sync(FULLMASK, kd, src);
+            return b + src;
+        }
     }
     return sz;
 }
@@ -855,16 +868,17 @@ __global__ void __launch_bounds__(128, OCC) k_search(DevIndex ix, SearchArgs a) 
         bool spill_mode = false;
         int expansions = 0;
         while (!fail) {
-            cursor = find_next(Ti, sz, cursor, lane);
+            uint32_t craw = 0u;
+            float dc = 0.f;
+            cursor = find_next_entry(Tk, Ti, sz, cursor, lane, craw, dc);
             if (cursor >= sz) break;
             if (expansions >= a.max_expansions || nspill + 32 * NPL > a.spill_cap) {
                 fail = true;
                 break;
             }
-            const uint32_t craw = Ti[CK(cursor, ef, 1001)];
+            (void)CK(cursor, ef, 1001);
             const uint32_t c = craw & IDM;
             const bool cfull = craw & TAG;   // FP16 codes: second half of the block needed
-            const float dc = Tk[CK(cursor, ef, 1002)];
             __syncwarp();
             if (lane == 0) Ti[cursor] = craw | EXP;
             expansions++;
