@@ -72,7 +72,9 @@ def parse():
     ap.add_argument("--ablation", action="store_true",
                     help="Sec. 4.3 ablation (basis and matching variants) on --cfg")
     ap.add_argument("--profile-ef", type=int, default=0,
-                    help="profiling run: set up, then only --warmup + 1 FINGER searches at this ef")
+                    help="profiling run: set up, then only --warmup + 1 searches at this ef")
+    ap.add_argument("--profile-mode", type=int, default=4,
+                    help="search mode of the profiling run (default 4: FINGER with FP16 codes)")
     ap.add_argument("--partitioned", type=int, default=0,
                     help="database split into this many parts, each with its own index, results "
                          "merged on the device (under torchrun: one part per rank)")
@@ -1018,7 +1020,7 @@ def main():
     MODES = {"plain": fg.MODE_PLAIN, "finger": fg.MODE_FINGER_F16, "finger_f32": fg.MODE_FINGER,
              "finger_f8": fg.MODE_FINGER_F8}
     if args.profile_ef:
-        ix.set_mode(fg.MODE_FINGER_F16, 5)
+        ix.set_mode(args.profile_mode, 5)
         ids, d = ix.search(q, K, args.profile_ef)
         for _ in range(args.warmup):
             ix.search(q, K, args.profile_ef, ids, d)

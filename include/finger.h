@@ -230,8 +230,8 @@ int64_t finger_table_bytes(int64_t n, int deg0, int r, int lp);
 /* -------------------------------------------------------------- search */
 
 /* Set the search mode (FINGER_MODE_*) and the warm-up: the first `warmup`
- * layer-0 expansions of every query use exact distances only (Algorithm 4,
- * "#updates of cur > 5"; default 5).  warmup < 0 leaves it unchanged. */
+ * layer-0 expansions of every query use exact distances only (Algorithm 4
+ * starts skipping after five updates of cur; default 5).  warmup < 0 leaves it unchanged. */
 finger_status finger_set_mode(finger_index* ix, int mode, int warmup);
 
 /* Greedy search for nq queries (device, nq x m row-major FP32): descent with

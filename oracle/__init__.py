@@ -132,7 +132,7 @@ def hnsw_build(X, M: int, ef_construction: int, seed: int, flat: bool = False) -
     ``flat=True`` puts every node on level 0: the same incremental insertion and
     heuristic selection on a single layer (a navigable small-world graph without
     the hierarchy), searched from node 0 -- a non-HNSW graph for FINGER, which
-    the paper builds "from any existing graph" (Sec. 3.3)."""
+    the paper builds on top of a given graph (Sec. 3.3)."""
     X = _f64(X)
     n, m = X.shape
     lv = np.zeros(n, np.int32) if flat else levels(n, M, seed)

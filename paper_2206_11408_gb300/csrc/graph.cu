@@ -1,5 +1,5 @@
 // HNSW-style graph construction on the device (the graph FINGER accelerates;
-// the paper builds FINGER "from any existing graph G", Sec. 3.3).
+// FINGER is built on top of a given graph, Sec. 3.3).
 //
 // Levels are drawn as in HNSW: level(v) = floor(-ln U_v / ln M) with U_v from
 // the counter-based generator splitmix64(seed ^ v).  Nodes are inserted in id
