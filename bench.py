@@ -359,7 +359,7 @@ def run_reference(args):
 
 # ------------------------------------------------------------ extension legs
 
-def _ext_setup(args, cfg, build_lp=False, half_codes=False):
+def _ext_setup(args, cfg, build_lp=False, half_codes=False, fp8_codes=False):
     import torch
 
     import paper_2206_11408_gb300 as fg
@@ -375,7 +375,7 @@ def _ext_setup(args, cfg, build_lp=False, half_codes=False):
     torch.cuda.synchronize()
     tg = time.perf_counter() - tg
     tt = time.perf_counter()
-    ix.build_tables(c.r, 4000 + cfg, build_lp=build_lp, half_codes=half_codes)
+    ix.build_tables(c.r, 4000 + cfg, build_lp=build_lp, half_codes=half_codes, fp8_codes=fp8_codes)
     torch.cuda.synchronize()
     tt = time.perf_counter() - tt
     q = torch.from_numpy(Q).cuda()
@@ -597,24 +597,29 @@ def leg_mlp(args):
 
 def leg_batch(args):
     """Configuration 5.  (1) The metric on a uniform K = 10 stream: ef sweeps of
-    plain and FINGER on the first 10,000 queries, QPS at recall@10 0.95.
-    (2) The uneven stream: 50,000 queries in batches of 1..4096 with K in
-    {1, 10, 100} and ef in [max(K,10), 400], one captured persistent launch per
-    batch (autotuned per ef bucket).  Plain serves each query at its ef; FINGER
-    at ef scaled by the ratio of the two methods' ef at recall 0.95 in (1), so
-    both serve the stream at about the same recall.  Throughput, p50/p99 batch
-    latency and mean recall@K."""
+    plain and FINGER (FP16 codes, FP8 codes, FP32 tables) on the first 10,000
+    queries, QPS at recall@10 0.95.  (2) The uneven stream: 50,000 queries in
+    batches of 1..4096 with K in {1, 10, 100} and ef in [max(K,10), 400], one
+    captured persistent launch per batch (autotuned per ef bucket).  Plain
+    serves each query at its ef; each FINGER form (FP16 and FP8 codes) at ef
+    scaled by the ratio of its ef to plain's at recall 0.95 in (1), so all serve
+    the stream at about the same recall.  Throughput, p50/p99 batch latency and
+    mean recall@K."""
     import torch
 
     import paper_2206_11408_gb300 as fg
-    c, n, nq, X, Q, ix, q, setup = _ext_setup(args, 5, half_codes=True)
+    c, n, nq, X, Q, ix, q, setup = _ext_setup(args, 5, half_codes=True, fp8_codes=True)
     stream = torch.cuda.current_stream()
     nu = min(nq, 10_000)
     qu = q[:nu]
     gt_ids, _ = ix.knn(q, 100)
     gt = gt_ids.cpu().numpy()
-    # "finger" is the FP16-code form (the stream's FINGER); FP32 tables beside it
-    modes = {"plain": fg.MODE_PLAIN, "finger": fg.MODE_FINGER_F16, "finger_f32": fg.MODE_FINGER}
+    # "finger" is the FP16-code form; FP8 codes and FP32 tables beside it.  At
+    # deg0 = 64 and r = 64 a centre's FP16 block (8 KB) is read in two
+    # dependent rounds, its FP8 block (4 KB) in one, which matters where a
+    # small batch cannot hide latency behind other queries
+    modes = {"plain": fg.MODE_PLAIN, "finger": fg.MODE_FINGER_F16, "finger_f32": fg.MODE_FINGER,
+             "finger_f8": fg.MODE_FINGER_F8}
     curves, choice = _sweep(ix, qu, gt[:nu], c.K, modes, c.ef_grid, nu)
     uni = {}
     ck = None
@@ -625,12 +630,12 @@ def leg_batch(args):
         ck = k or ck
     roof, cpq = _leg_roofline(fg, ix, qu, c, choice["finger"][0], fg.MODE_FINGER_F16,
                               uni["finger"][1])
-    alpha = choice["finger"][0] / choice["plain"][0]
-
     plan = workloads.uneven_batches(nq)
     out = {}
-    for name, mode in (("plain", fg.MODE_PLAIN), ("finger", fg.MODE_FINGER_F16)):
-        scale = alpha if name == "finger" else 1.0
+    for name, mode in (("plain", fg.MODE_PLAIN), ("finger", fg.MODE_FINGER_F16),
+                       ("finger_f8", fg.MODE_FINGER_F8)):
+        # each FINGER form at ef scaled by its ef / plain's ef at recall 0.95
+        scale = choice[name][0] / choice["plain"][0]
         batches = []
         for start, size, K, ef in plan:
             efm = np.minimum(np.maximum(np.ceil(ef * scale), K), 1000).astype(np.int32)
@@ -681,7 +686,8 @@ def leg_batch(args):
     extra = {"impl_mode": "FINGER with FP16 codes; uniform K=10 sweep + uneven batches "
                           "(graph-captured, autotuned persistent launch)",
              "finger_qps": uni["finger"][0], "plain_qps": uni["plain"][0],
-             "finger_f32_qps": uni["finger_f32"][0],
+             "finger_f32_qps": uni["finger_f32"][0], "finger_f8_qps": uni["finger_f8"][0],
+             "finger_f8_over_plain": uni["finger_f8"][0] / uni["plain"][0],
              "finger_over_plain": uni["finger"][0] / uni["plain"][0],
              "finger_f32_over_plain": uni["finger_f32"][0] / uni["plain"][0],
              "ef": {k: v[0] for k, v in choice.items()},
@@ -691,8 +697,9 @@ def leg_batch(args):
              # per ef bucket: [warps per block, hash slots, resident warps per SM,
              # exact rows in flight per warp, best ms]
              "stream": {"queries": nq, "batches": len(plan), "plain": out["plain"],
-                        "finger": out["finger"],
-                        "finger_over_plain": out["finger"]["qps"] / out["plain"]["qps"]},
+                        "finger": out["finger"], "finger_f8": out["finger_f8"],
+                        "finger_over_plain": out["finger"]["qps"] / out["plain"]["qps"],
+                        "finger_f8_over_plain": out["finger_f8"]["qps"] / out["plain"]["qps"]},
              "setup_s": setup,
              "curves": {k: [[e, round(r_, 4), round(v_, 1)] for e, r_, v_ in pts]
                         for k, pts in curves.items()}}
@@ -956,10 +963,13 @@ def extensions(args):
             st = line["stream"]
             keep["stream"] = {"queries": st["queries"], "batches": st["batches"],
                               "finger_over_plain": st["finger_over_plain"],
+                              "finger_f8_over_plain": st.get("finger_f8_over_plain"),
                               "plain": {k: st["plain"][k] for k in ("qps", "p50_batch_ms",
                                                                     "p99_batch_ms", "recall")},
                               "finger": {k: st["finger"][k] for k in ("qps", "p50_batch_ms",
-                                                                      "p99_batch_ms", "recall")}}
+                                                                      "p99_batch_ms", "recall")},
+                              "finger_f8": {k: st["finger_f8"][k] for k in (
+                                  "qps", "p50_batch_ms", "p99_batch_ms", "recall")}}
         if "predictor" in line:
             keep["predictor"] = {k: line["predictor"][k] for k in ("triples", "eps_prime",
                                                                   "heldout_cos_mae")}
