@@ -300,6 +300,15 @@ def test_wide_codes_two_row_groups():
         gi, gd, gc = _gpu_search(ix, q, 10, 80, mode)
         oi, od, oc = oracle.search(g, X, Q, 10, 80, f)
         _compare(gi, gd, gc, oi, od, oc, gt, 10, f"deg0=64 r=64 mode={mode}")
+    # ef 2 and 4: the expansion that fills T leaves up to 63 new neighbours for
+    # the gate replay, most of them below ub, so expansions with 32 or more
+    # candidates take the serial replay
+    gt2, _ = oracle.bruteforce(X, Q, 2)
+    for ef in (2, 4):
+        for mode, f in _modes(fp):
+            gi, gd, gc = _gpu_search(ix, q, 2, ef, mode)
+            oi, od, oc = oracle.search(g, X, Q, 2, ef, f)
+            _compare(gi, gd, gc, oi, od, oc, gt2, 2, f"deg0=64 ef={ef} mode={mode}")
     ix.close()
 
 
