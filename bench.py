@@ -405,6 +405,23 @@ def _sweep(ix, q, gt, K, modes, ef_grid, nq):
                 choice[name] = (ef, rec)
             if name in choice and ef >= choice[name][0] + 40:
                 break
+        if name in choice:
+            # the smallest ef on a step-2 grid below the coarse crossing, as in
+            # the SIFT-like leg
+            def timed_fn(ef, mode=mode):
+                ix.set_mode(mode, 5)
+                ids, d = ix.search(q, K, ef)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                ix.search(q, K, ef, ids, d)
+                e1.record(stream)
+                e1.synchronize()
+                ix.sync()
+                return ids.cpu().numpy(), e0.elapsed_time(e1)
+            fine = _refine(timed_fn, gt, K, nq, pts)
+            if fine is not None:
+                choice[name] = fine
+            pts.sort()
         curves[name] = pts
         if name not in choice:
             best = max(pts, key=lambda p_: p_[1])
