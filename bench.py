@@ -541,11 +541,12 @@ def leg_lp(args):
 
 def leg_mlp(args):
     """Configuration 4: learned predictor (harvest on training queries, GPU
-    training) vs distribution-matched FINGER vs plain, QPS at recall@10 0.95."""
+    training) vs distribution-matched FINGER (FP32 tables, and FP16 codes) vs
+    plain, QPS at recall@10 0.95."""
     import torch
 
     import paper_2206_11408_gb300 as fg
-    c, n, nq, X, Q, ix, q, setup = _ext_setup(args, 4)
+    c, n, nq, X, Q, ix, q, setup = _ext_setup(args, 4, half_codes=True)
     gt_ids, _ = ix.knn(q, c.K)
     gt = gt_ids.cpu().numpy()
     th = time.perf_counter()
@@ -572,6 +573,7 @@ def leg_mlp(args):
     # the predictor on every estimate (delta < 0) and gated to the margin
     # MLP_GATE * ub around the upper bound
     variants = {"plain": (fg.MODE_PLAIN, -1.0), "finger": (fg.MODE_FINGER, -1.0),
+                "finger_f16": (fg.MODE_FINGER_F16, -1.0),
                 "finger_mlp": (fg.MODE_FINGER_MLP, -1.0),
                 "finger_mlp_gated": (fg.MODE_FINGER_MLP, MLP_GATE)}
     curves, choice, res, ck = {}, {}, {}, None
@@ -592,6 +594,9 @@ def leg_mlp(args):
              "roofline": roof, "counters_per_query": cpq,
              "qps_at_recall_interp": {k: qps_at(v) for k, v in curves.items()},
              "finger_qps": res["finger"][0], "plain_qps": res["plain"][0],
+             "finger_f16_qps": res["finger_f16"][0],
+             "f16_over_plain": res["finger_f16"][0] / res["plain"][0],
+             "finger_over_plain": res["finger"][0] / res["plain"][0],
              "mlp_all_qps": res["finger_mlp"][0], "mlp_gate": MLP_GATE,
              "mlp_over_plain": res["finger_mlp_gated"][0] / res["plain"][0],
              "mlp_over_finger": res["finger_mlp_gated"][0] / res["finger"][0],
