@@ -153,9 +153,15 @@ def measured_peaks():
 
 
 def kernel_source_hash() -> str:
+    """Hash of the search kernel's source without comments and blank lines, so
+    that a comment edit leaves a committed capture valid."""
+    import re
     h = hashlib.sha256()
     for f in ("search_impl.cuh", "search_f16_k4.cu"):
-        h.update(open(os.path.join(ROOT, "paper_2206_11408_gb300", "csrc", f), "rb").read())
+        src = open(os.path.join(ROOT, "paper_2206_11408_gb300", "csrc", f)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        lines = (re.sub(r"//.*$", "", ln).rstrip() for ln in src.splitlines())
+        h.update("\n".join(ln for ln in lines if ln.strip()).encode())
     return h.hexdigest()[:16]
 
 

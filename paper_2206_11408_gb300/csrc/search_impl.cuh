@@ -4,7 +4,7 @@
 // arXiv 2206.11408 with these readings of the paper:
 //   * keys are (distance, id) compared lexicographically;
 //   * a neighbour is admitted iff |T| < ef or its key is below the key of the
-//     worst entry of T (Algorithm 1, "dist <= ub or |T| <= efs" read with the
+//     worst entry of T (Algorithm 1's admission test read together with the
 //     eviction that keeps |T| <= ef); entries evicted from T are never
 //     expanded, so the candidate queue C is exactly the unexpanded part of T
 //     and one sorted array holds both;
@@ -21,15 +21,19 @@
 // exact visited hash (16-bit slots, one bucket of eight per id, where the ids
 // fit; else 32-bit slots in probed buckets of four) that spills to a per-warp
 // global bitmap once 3/4 full, the unit residual projection of the query, and
-// staging.  One expansion is three dependent gathers: the adjacency row
-// (coalesced, lane j <- neighbour j), the per-edge rows of the new neighbours
-// (FP32 FINGER: compacted, r/4 lanes per row, eight 16-byte loads per lane in
-// flight, butterfly sums; other modes: one lane per row), and the full rows
-// of the neighbours whose estimate passes (groups of G lanes per row, 16-byte
-// loads, shuffle reduction).  Estimates
-// are formed for every new neighbour against the ub at the start of the
-// expansion; the sequential gate is then replayed in adjacency order so the
-// traversal is exactly the per-neighbour one of Algorithm 4.
+// staging.  An expansion gathers the adjacency row (coalesced, lane j <-
+// neighbour j), in FP32 FINGER then the per-edge rows of the new neighbours
+// (compacted, r/4 lanes per row, eight 16-byte loads per lane in flight,
+// butterfly sums) -- the FP16 / FP8 code modes instead read the centre's
+// whole code block with the adjacency row and form all estimates as one
+// tensor-core product -- and last the full rows of the neighbours whose
+// estimate passes (groups of G lanes per row, 16-byte loads, shuffle
+// reduction).  Estimates are formed for every new neighbour against the ub
+// at the start of the expansion; the sequential gate is then replayed on the
+// whole warp in adjacency order (the running ub read from a 32-deep pool of
+// T's tail and the admitted keys), so the traversal is exactly the
+// per-neighbour one of Algorithm 4, and the admitted keys are merged into T
+// once.
 #pragma once
 
 #include "internal.cuh"
