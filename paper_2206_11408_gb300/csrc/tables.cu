@@ -234,7 +234,7 @@ __global__ void k_jacobi(double* A, double* V, int m, double2* rot, int2* pr, do
         grid.sync();
         if (OFF <= tol * tol * TOT || OFF == 0.0) break;
         for (int r = 0; r < mm - 1; ++r) {
-            // pairs and rotations of this round
+            // pairs and rotations of this step of the sweep
             for (int64_t k = tid; k < half; k += nth) {
                 int a, b;
                 if (k == 0) a = 0;
