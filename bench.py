@@ -1174,6 +1174,22 @@ def main():
         st = ix.stats()
         return dict(zip(fg.COUNTER_NAMES, cnt_t.sum(0).cpu().numpy().astype(np.int64).tolist())), st
 
+    # the FP16 codes against the FP32 tables: the same traversal?  Per query,
+    # at the headline's ef: identical result lists and traversal counters
+    def per_query(mode, ef):
+        cnt_t = torch.zeros((nq, 8), dtype=torch.int32, device="cuda")
+        ix.set_counters(cnt_t)
+        ix.set_mode(mode, 5)
+        ids, d = ix.search(q, K, ef)
+        torch.cuda.synchronize()
+        ix.set_counters(None)
+        return ids.cpu().numpy(), cnt_t.cpu().numpy()
+
+    i16, c16 = per_query(fg.MODE_FINGER_F16, efs["finger"])
+    i32, c32 = per_query(fg.MODE_FINGER, efs["finger"])
+    same_lists = (i16 == i32).all(axis=1)
+    f16_vs_f32 = {"ef": efs["finger"], "identical_lists": float(same_lists.mean()),
+                  "identical_counters": float((c16[:, :7] == c32[:, :7]).all(axis=1).mean())}
     csum, st = counters(fg.MODE_FINGER_F16, efs["finger"])
     algo = algorithmic_bytes(csum, nq, c.m, c.r, info["deg0"], c.M, K, 5, True,
                              code_bytes=st["code_bytes"])
@@ -1265,6 +1281,8 @@ def main():
                     "recall": e2e_rec},
             "clocks": res["finger"]["clocks"], "gpu_launches": args.steps,
             "counters_per_query": {k: v / nq for k, v in csum.items()},
+            # FP16 codes against the FP32 tables, query by query at the same ef
+            "finger_f16_vs_f32_traversal": f16_vs_f32,
             "setup_s": {"total": t_setup, "graph": t_graph, "tables": t_tables},
             "curves": {k: [[e, round(r_, 4), round(v_, 1)] for e, r_, v_ in pts]
                        for k, pts in curves.items()},
