@@ -62,9 +62,11 @@ enum {
                                    dependent round trip to memory fewer than in mode FINGER */
     FINGER_MODE_FINGER_F8 = 5   /* as FINGER_F16 with the codes stored as FP8-e4m3 of
                                    256 u (the LP mode's code table: half the bytes and
-                                   half the registers per code block); FP32 vectors,
-                                   FP32 accumulation.  Needs tables built with
-                                   FINGER_BUILD_FP8_CODES or build_lp */
+                                   half the registers per code block); the product is
+                                   an FP8 tensor-core MMA with 256 u_q split into an
+                                   e4m3 part and the e4m3 rounding of the rest, FP32
+                                   accumulation; FP32 vectors.  Needs tables built
+                                   with FINGER_BUILD_FP8_CODES or build_lp */
 };
 
 /* --------------------------------------------------------------- index */

@@ -409,10 +409,16 @@ static double appx_dist(const double* xc, const double* xd, int m, double cc, co
         for (int k = 0; k < r; ++k) that += (Pq[k] / nq_) * half_rne(Pd[k] / nd_);
     }
     if (codes == 8 && nq_ > 0 && nd_ > 0) {
-        /* the stored code is 256 times the unit P d_res rounded to FP8 E4M3 */
+        /* the stored code is 256 times the unit P d_res rounded to FP8 E4M3;
+         * 256 times the unit P q_res enters as its E4M3 rounding h plus the
+         * E4M3 rounding of the remainder */
         that = 0.0;
-        for (int k = 0; k < r; ++k) that += (Pq[k] / nq_) * e4m3_rne(256.0 * Pd[k] / nd_);
-        that /= 256.0;
+        for (int k = 0; k < r; ++k) {
+            const double s = 256.0 * Pq[k] / nq_;
+            const double h = e4m3_rne(s);
+            that += e4m3_rne(256.0 * Pd[k] / nd_) * (h + e4m3_rne(s - h));
+        }
+        that /= 65536.0;
     }
     double t = (that - muh) * ratio + mu;
     t = t + eps;

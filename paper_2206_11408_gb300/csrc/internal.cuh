@@ -47,9 +47,9 @@ struct DevIndex {
     float alpha, beta;      // t = t_hat * alpha + beta
     // reduced precision
     const uint4* Xh;        // n x m8 (BF16)
-    // FP8-e4m3 codes of edge_u * code_scale (modes LP and FINGER_F8) in the same fragment order
-    // as edge_h, two k steps per 16 bytes: per node 2 NPL tiles x hks / 2 x 32
-    // lanes x 16 bytes
+    // FP8-e4m3 codes of edge_u * code_scale (modes LP and FINGER_F8) in the 8-bit
+    // A-fragment order of mma.m16n8k32: per node 2 NPL tiles x hks / 2 steps of
+    // 32 codes x 32 lanes x 16 bytes
     const uint4* edge_q;
     float code_inv;         // 1 / code_scale
     // FP16 unit residual codes (mode FINGER_F16) in m16n8k16 A-fragment order:

@@ -439,6 +439,15 @@ __device__ __forceinline__ void mma_f16(float* d, const uint4& a, uint32_t b0, u
         : "r"(a.x), "r"(a.y), "r"(a.z), "r"(a.w), "r"(b0), "r"(b1));
 }
 
+// D += A B for one m16n8k32 tile with FP8-e4m3 operands, FP32 accumulation
+__device__ __forceinline__ void mma_e4m3(float* d, const uint4& a, uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k32.row.col.f32.e4m3.e4m3.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a.x), "r"(a.y), "r"(a.z), "r"(a.w), "r"(b0), "r"(b1));
+}
+
 __device__ __forceinline__ uint32_t pack_half2(float lo, float hi) {
     __half2 v = __floats2half2_rn(lo, hi);
     return *reinterpret_cast<uint32_t*>(&v);
@@ -490,35 +499,50 @@ __device__ __forceinline__ void wb_bfrag_store(uint32_t* bsm, float u0, float u1
     }
 }
 
-// t_hat of rows 16(t0+T)+g (v[2(t0+T)]) and +8 (v[2(t0+T)+1]) for the round's
-// tiles; k step outer, so each code register dies at its MMA.
-__device__ __forceinline__ uint32_t e4m3x2_to_half2(uint32_t pair) {
-    const __half2_raw h = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)pair, __NV_E4M3);
-    return (uint32_t)h.x | ((uint32_t)h.y << 16);
+// FP8 codes (modes LP and FINGER_F8): the codes are 256 u_d in the 8-bit
+// A-fragment order of mma.m16n8k32, and 256 u_q enters as an e4m3 high part
+// (even B columns) plus the e4m3 rounding of the remainder (odd columns), so
+// the product needs no conversion.  Byte j of word ((kk * 2 + p) * 4 + t) * 2
+// + w of the B region holds code 32kk + 16w + 4t + j of part p, so lane 4g + t
+// reads its two words of step kk (column g takes part g & 1) with one 8-byte
+// load; lane l forms codes 2l and 2l + 1.
+__device__ __forceinline__ float e4m3_value(uint32_t code) {
+    const __half_raw h = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)code, __NV_E4M3);
+    return __half2float(__half(h));
 }
 
-// the A fragment of k step (2p + h) from a 16-byte FP8 load (h: which half)
-__device__ __forceinline__ uint4 e4m3_frag(const uint4& x, int h) {
-    const uint32_t lo = h ? x.z : x.x, hi = h ? x.w : x.y;
-    return make_uint4(e4m3x2_to_half2(lo & 0xFFFFu), e4m3x2_to_half2(lo >> 16),
-                      e4m3x2_to_half2(hi & 0xFFFFu), e4m3x2_to_half2(hi >> 16));
+__device__ __forceinline__ void wb_bfrag_store8(uint32_t* bsm, float u0, float u1, int kp_n,
+                                                int lane) {
+    const float s0 = 256.f * u0, s1 = 256.f * u1;
+    const uint32_t h0 = __nv_cvt_float_to_fp8(s0, __NV_SATFINITE, __NV_E4M3);
+    const uint32_t h1 = __nv_cvt_float_to_fp8(s1, __NV_SATFINITE, __NV_E4M3);
+    const uint32_t l0 = __nv_cvt_float_to_fp8(s0 - e4m3_value(h0), __NV_SATFINITE, __NV_E4M3);
+    const uint32_t l1 = __nv_cvt_float_to_fp8(s1 - e4m3_value(h1), __NV_SATFINITE, __NV_E4M3);
+    const int kk = lane >> 4, w = (lane >> 3) & 1, t = (lane >> 1) & 3, j = 2 * (lane & 1);
+    if (kk < kp_n) {
+        uint16_t* b16 = reinterpret_cast<uint16_t*>(bsm);
+        b16[((((kk * 2 + 0) * 4 + t) * 2 + w) * 4 + j) >> 1] = (uint16_t)(h0 | h1 << 8);
+        b16[((((kk * 2 + 1) * 4 + t) * 2 + w) * 4 + j) >> 1] = (uint16_t)(l0 | l1 << 8);
+    }
 }
+
+// t_hat of rows 16(t0+T)+g (v[2(t0+T)]) and +8 (v[2(t0+T)+1]) for the round's
+// tiles; k step outer, so each code register dies at its MMA.
 
 template <int KS, int NT, bool W8 = false>
 __device__ __forceinline__ void wb_mma(const uint4 (&hx)[8], const uint32_t* bsm, int t0,
                                        float (&v)[8], int lane) {
-    if constexpr (W8) {   // every tile, FP8 fragments converted to FP16 in registers
+    if constexpr (W8) {   // every tile, 32 FP8 codes per MMA
         constexpr int KP = KS / 2;
         const uint2* bf = reinterpret_cast<const uint2*>(bsm) + ((lane >> 2) & 1) * 4 + (lane & 3);
         float acc[NT][4];
 #pragma unroll
         for (int T = 0; T < NT; ++T) acc[T][0] = acc[T][1] = acc[T][2] = acc[T][3] = 0.f;
 #pragma unroll
-        for (int ks = 0; ks < KS; ++ks) {
-            const uint2 b = bf[ks * 8];
+        for (int kk = 0; kk < KP; ++kk) {
+            const uint2 b = bf[kk * 8];
 #pragma unroll
-            for (int T = 0; T < NT; ++T)
-                mma_f16(acc[T], e4m3_frag(hx[T * KP + ks / 2], ks & 1), b.x, b.y);
+            for (int T = 0; T < NT; ++T) mma_e4m3(acc[T], hx[T * KP + kk], b.x, b.y);
         }
 #pragma unroll
         for (int T = 0; T < NT; ++T) {
@@ -944,7 +968,8 @@ __global__ void __launch_bounds__(128, OCC) k_search(DevIndex ix, SearchArgs a) 
                     const float nrm = warp_sum(u0 * u0 + u1 * u1);
                     const float inv = nrm > 0.f ? rsqrtf(nrm) : 0.f;
                     uint32_t* bsm = reinterpret_cast<uint32_t*>(uq);
-                    wb_bfrag_store(bsm, u0 * inv, u1 * inv, WKS, lane);
+                    if constexpr (W8) wb_bfrag_store8(bsm, u0 * inv, u1 * inv, WKS / 2, lane);
+                    else wb_bfrag_store(bsm, u0 * inv, u1 * inv, WKS, lane);
                     __syncwarp();
                     float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
                     wb_mma<WKS, WNT, W8>(hx, bsm, 0, v, lane);
@@ -955,9 +980,9 @@ __global__ void __launch_bounds__(128, OCC) k_search(DevIndex ix, SearchArgs a) 
                         }
                     }
                     wb_route<NPL>(v, th, lane);
-                    if constexpr (W8) {   // the FP8 codes hold 256 u
+                    if constexpr (W8) {   // codes of 256 u_d times parts of 256 u_q
 #pragma unroll
-                        for (int s = 0; s < NPL; ++s) th[s] *= ix.code_inv;
+                        for (int s = 0; s < NPL; ++s) th[s] *= ix.code_inv * (1.f / 256.f);
                     }
                 }
             }

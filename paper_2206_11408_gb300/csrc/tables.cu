@@ -589,17 +589,18 @@ __global__ void k_sum_final(const double* part, int nb, double* out) {
     out[2] = c;
 }
 
-// FP8-e4m3 codes of scale * u in the FP16 codes' fragment order, two k steps
-// per 16 bytes: thread i writes lane l = i % 32 of (node c, tile T, k pair p) =
-// i / 32: bytes 0..7 for k step 2p, 8..15 for 2p + 1, each as rows 16T + g and
-// 16T + g + 8 (g = l / 4) at codes 16ks + 2t, +1, +8, +9 (t = l % 4).
+// FP8-e4m3 codes of scale * u in the A-fragment order of mma.m16n8k32 with
+// 8-bit operands: thread i writes lane l = i % 32 of (node c, tile T, k step
+// kk) = i / 32, 16 bytes: rows 16T + g (words 0, 2) and 16T + g + 8 (words 1,
+// 3), g = l / 4, at codes 32kk + 4t .. + 3 (words 0, 1) and 32kk + 16 + 4t ..
+// + 3 (words 2, 3), t = l % 4, the lower code in the lower byte.
 __global__ void k_lp_codes(const float* edge_u, int64_t n, int deg0, int r_pad, int tiles,
                            int kp_n, float scale, uint4* out) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n * tiles * kp_n * 32) return;
     const int l = (int)(i & 31);
     int64_t f = i >> 5;
-    const int kp = (int)(f % kp_n);
+    const int kk = (int)(f % kp_n);
     f /= kp_n;
     const int T = (int)(f % tiles);
     const int64_t c = f / tiles;
@@ -609,11 +610,10 @@ __global__ void k_lp_codes(const float* edge_u, int64_t n, int deg0, int r_pad, 
         return (uint32_t)__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
     };
     uint32_t w[4];
-    for (int h = 0; h < 2; ++h) {
-        const int ks = 2 * kp + h;
-        const int r0 = 16 * T + g, r1 = r0 + 8, k0 = 16 * ks + 2 * t, k1 = k0 + 8;
-        w[2 * h] = code(r0, k0) | code(r0, k0 + 1) << 8 | code(r1, k0) << 16 | code(r1, k0 + 1) << 24;
-        w[2 * h + 1] = code(r0, k1) | code(r0, k1 + 1) << 8 | code(r1, k1) << 16 | code(r1, k1 + 1) << 24;
+    for (int q = 0; q < 4; ++q) {
+        const int row = 16 * T + g + ((q & 1) ? 8 : 0);
+        const int k0 = 32 * kk + 4 * t + ((q & 2) ? 16 : 0);
+        w[q] = code(row, k0) | code(row, k0 + 1) << 8 | code(row, k0 + 2) << 16 | code(row, k0 + 3) << 24;
     }
     out[i] = make_uint4(w[0], w[1], w[2], w[3]);
 }

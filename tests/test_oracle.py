@@ -143,6 +143,22 @@ def test_estimate_fp8_codes_hand_example():
     assert oracle.estimate(q, c, d, fp) == 32.5
 
 
+def test_estimate_fp8_codes_query_split_hand_example():
+    """With FP8 codes 256 u_q enters the product as its E4M3 rounding h plus
+    the E4M3 rounding of the remainder.  c = e3, P = [e1; e2], d = (3,4,5),
+    q = (6,8,2): b = 5, a = 2, u_d = u_q = (0.6, 0.8), so the exact t is 1 and
+    the estimate 134 - 100 t is ||q - d||^2 = 34.  256 u = (153.6, 204.8): the
+    codes and h are (160, 208), the remainders (-6.4, -3.2) round to (-6.5,
+    -3.25), so t_hat = (160 * 153.5 + 208 * 204.75) / 65536 = 1.02459716796875
+    and the estimate is 31.540283203125."""
+    P = np.array([[1.0, 0, 0], [0, 1.0, 0]])
+    q, c, d = np.array([6.0, 8, 2]), np.array([0, 0, 1.0]), np.array([3.0, 4, 5])
+    assert oracle.estimate(q, c, d, _stats(P=P)) == pytest.approx(34.0, abs=1e-12)
+    fp = _stats(P=P)
+    fp.codes = 8
+    assert oracle.estimate(q, c, d, fp) == 31.540283203125
+
+
 def test_estimate_full_rank_is_exact_distance():
     """Eq. (2): with an orthogonal P (r = m) and identity matching the estimate
     is ||q - d||^2 exactly (the cross term q_proj^T q_res vanishes)."""
