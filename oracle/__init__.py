@@ -195,7 +195,9 @@ class FingerParams:
     eps: float
     corr: float = float("nan")      # Pearson correlation of X and Y over S (Supp. E)
     codes: int = 0                  # 16: the per-edge unit P d_res stored as binary16 codes;
-                                    # 8: 256 times it stored as FP8 E4M3 codes
+                                    # 8: 256 times it stored as FP8 E4M3 codes, 256 u_q as
+                                    # its E4M3 rounding plus that of the remainder;
+                                    # 9: the same codes against u_q itself
 
     def stats(self):
         return np.array([self.mu, self.sigma, self.mu_hat, self.sigma_hat, self.eps], np.float64)

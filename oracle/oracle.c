@@ -420,6 +420,12 @@ static double appx_dist(const double* xc, const double* xd, int m, double cc, co
         }
         that /= 65536.0;
     }
+    if (codes == 9 && nq_ > 0 && nd_ > 0) {
+        /* the same FP8 codes against the unit P q_res itself */
+        that = 0.0;
+        for (int k = 0; k < r; ++k) that += (Pq[k] / nq_) * e4m3_rne(256.0 * Pd[k] / nd_);
+        that /= 256.0;
+    }
     double t = (that - muh) * ratio + mu;
     t = t + eps;
     int use_mlp = mlp != NULL;

@@ -526,23 +526,54 @@ __device__ __forceinline__ void wb_bfrag_store8(uint32_t* bsm, float u0, float u
     }
 }
 
+// A block with more than four FP8 products per expansion (64 slots and r > 32)
+// measured faster the other way: its codes follow the FP16 fragment order of
+// m16n8k16, two k steps per 16 bytes, each FP8 pair becomes one FP16 pair of
+// the A operand by a single conversion (exact), and u_q takes the FP16 high /
+// low split of the FP16-code mode.
+__device__ __forceinline__ uint32_t e4m3x2_to_half2(uint32_t pair) {
+    const __half2_raw h = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)pair, __NV_E4M3);
+    return (uint32_t)h.x | ((uint32_t)h.y << 16);
+}
+
+// the A fragment of k step (2p + h) from a 16-byte FP8 load (h: which half)
+__device__ __forceinline__ uint4 e4m3_frag(const uint4& x, int h) {
+    const uint32_t lo = h ? x.z : x.x, hi = h ? x.w : x.y;
+    return make_uint4(e4m3x2_to_half2(lo & 0xFFFFu), e4m3x2_to_half2(lo >> 16),
+                      e4m3x2_to_half2(hi & 0xFFFFu), e4m3x2_to_half2(hi >> 16));
+}
+
+// whether a code block of NT tiles and KS k steps of 16 is multiplied in FP8
+template <int NT, int KS>
+__host__ __device__ constexpr bool fp8_product() { return NT * (KS / 2) <= 4; }
+
 // t_hat of rows 16(t0+T)+g (v[2(t0+T)]) and +8 (v[2(t0+T)+1]) for the round's
 // tiles; k step outer, so each code register dies at its MMA.
 
 template <int KS, int NT, bool W8 = false>
 __device__ __forceinline__ void wb_mma(const uint4 (&hx)[8], const uint32_t* bsm, int t0,
                                        float (&v)[8], int lane) {
-    if constexpr (W8) {   // every tile, 32 FP8 codes per MMA
+    if constexpr (W8) {   // every tile
         constexpr int KP = KS / 2;
         const uint2* bf = reinterpret_cast<const uint2*>(bsm) + ((lane >> 2) & 1) * 4 + (lane & 3);
         float acc[NT][4];
 #pragma unroll
         for (int T = 0; T < NT; ++T) acc[T][0] = acc[T][1] = acc[T][2] = acc[T][3] = 0.f;
+        if constexpr (fp8_product<NT, KS>()) {   // 32 FP8 codes per MMA
 #pragma unroll
-        for (int kk = 0; kk < KP; ++kk) {
-            const uint2 b = bf[kk * 8];
+            for (int kk = 0; kk < KP; ++kk) {
+                const uint2 b = bf[kk * 8];
 #pragma unroll
-            for (int T = 0; T < NT; ++T) mma_e4m3(acc[T], hx[T * KP + kk], b.x, b.y);
+                for (int T = 0; T < NT; ++T) mma_e4m3(acc[T], hx[T * KP + kk], b.x, b.y);
+            }
+        } else {   // FP8 pairs converted to FP16 pairs, 16 codes per MMA
+#pragma unroll
+            for (int ks = 0; ks < KS; ++ks) {
+                const uint2 b = bf[ks * 8];
+#pragma unroll
+                for (int T = 0; T < NT; ++T)
+                    mma_f16(acc[T], e4m3_frag(hx[T * KP + ks / 2], ks & 1), b.x, b.y);
+            }
         }
 #pragma unroll
         for (int T = 0; T < NT; ++T) {
@@ -968,8 +999,10 @@ __global__ void __launch_bounds__(128, OCC) k_search(DevIndex ix, SearchArgs a) 
                     const float nrm = warp_sum(u0 * u0 + u1 * u1);
                     const float inv = nrm > 0.f ? rsqrtf(nrm) : 0.f;
                     uint32_t* bsm = reinterpret_cast<uint32_t*>(uq);
-                    if constexpr (W8) wb_bfrag_store8(bsm, u0 * inv, u1 * inv, WKS / 2, lane);
-                    else wb_bfrag_store(bsm, u0 * inv, u1 * inv, WKS, lane);
+                    if constexpr (W8 && fp8_product<WNT, WKS>())
+                        wb_bfrag_store8(bsm, u0 * inv, u1 * inv, WKS / 2, lane);
+                    else
+                        wb_bfrag_store(bsm, u0 * inv, u1 * inv, WKS, lane);
                     __syncwarp();
                     float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
                     wb_mma<WKS, WNT, W8>(hx, bsm, 0, v, lane);
@@ -980,9 +1013,11 @@ __global__ void __launch_bounds__(128, OCC) k_search(DevIndex ix, SearchArgs a) 
                         }
                     }
                     wb_route<NPL>(v, th, lane);
-                    if constexpr (W8) {   // codes of 256 u_d times parts of 256 u_q
+                    if constexpr (W8) {   // codes of 256 u_d (times parts of 256 u_q)
+                        const float sc = fp8_product<WNT, WKS>() ? ix.code_inv * (1.f / 256.f)
+                                                                : ix.code_inv;
 #pragma unroll
-                        for (int s = 0; s < NPL; ++s) th[s] *= ix.code_inv * (1.f / 256.f);
+                        for (int s = 0; s < NPL; ++s) th[s] *= sc;
                     }
                 }
             }

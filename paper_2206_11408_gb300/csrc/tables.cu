@@ -589,13 +589,17 @@ __global__ void k_sum_final(const double* part, int nb, double* out) {
     out[2] = c;
 }
 
-// FP8-e4m3 codes of scale * u in the A-fragment order of mma.m16n8k32 with
-// 8-bit operands: thread i writes lane l = i % 32 of (node c, tile T, k step
-// kk) = i / 32, 16 bytes: rows 16T + g (words 0, 2) and 16T + g + 8 (words 1,
-// 3), g = l / 4, at codes 32kk + 4t .. + 3 (words 0, 1) and 32kk + 16 + 4t ..
-// + 3 (words 2, 3), t = l % 4, the lower code in the lower byte.
+// FP8-e4m3 codes of scale * u, 16 bytes per (node c, tile T, step kk of 32
+// codes, lane l = 4g + t).  With k32 (a block of at most four such products,
+// the shapes the search kernel multiplies in FP8) they are in the A-fragment
+// order of mma.m16n8k32 with 8-bit operands: rows 16T + g (words 0, 2) and
+// 16T + g + 8 (words 1, 3) at codes 32kk + 4t .. + 3 (words 0, 1) and
+// 32kk + 16 + 4t .. + 3 (words 2, 3), the lower code in the lower byte.
+// Otherwise they follow the FP16 A-fragment order of m16n8k16 for the k steps
+// 2kk (bytes 0..7) and 2kk + 1 (bytes 8..15): rows 16T + g and 16T + g + 8 at
+// codes 16ks + 2t, +1, +8, +9 (the kernel converts them to FP16 pairs).
 __global__ void k_lp_codes(const float* edge_u, int64_t n, int deg0, int r_pad, int tiles,
-                           int kp_n, float scale, uint4* out) {
+                           int kp_n, float scale, int k32, uint4* out) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n * tiles * kp_n * 32) return;
     const int l = (int)(i & 31);
@@ -610,10 +614,19 @@ __global__ void k_lp_codes(const float* edge_u, int64_t n, int deg0, int r_pad, 
         return (uint32_t)__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
     };
     uint32_t w[4];
-    for (int q = 0; q < 4; ++q) {
-        const int row = 16 * T + g + ((q & 1) ? 8 : 0);
-        const int k0 = 32 * kk + 4 * t + ((q & 2) ? 16 : 0);
-        w[q] = code(row, k0) | code(row, k0 + 1) << 8 | code(row, k0 + 2) << 16 | code(row, k0 + 3) << 24;
+    if (k32) {
+        for (int q = 0; q < 4; ++q) {
+            const int row = 16 * T + g + ((q & 1) ? 8 : 0);
+            const int k0 = 32 * kk + 4 * t + ((q & 2) ? 16 : 0);
+            w[q] = code(row, k0) | code(row, k0 + 1) << 8 | code(row, k0 + 2) << 16 | code(row, k0 + 3) << 24;
+        }
+    } else {
+        for (int h = 0; h < 2; ++h) {
+            const int ks = 2 * kk + h;
+            const int r0 = 16 * T + g, r1 = r0 + 8, k0 = 16 * ks + 2 * t, k1 = k0 + 8;
+            w[2 * h] = code(r0, k0) | code(r0, k0 + 1) << 8 | code(r1, k0) << 16 | code(r1, k0 + 1) << 24;
+            w[2 * h + 1] = code(r0, k1) | code(r0, k1 + 1) << 8 | code(r1, k1) << 16 | code(r1, k1 + 1) << 24;
+        }
     }
     out[i] = make_uint4(w[0], w[1], w[2], w[3]);
 }
@@ -738,8 +751,11 @@ cudaError_t fp8_rebuild(finger_index* ix) {
         ix->edge_q = nullptr;
         return e;
     }
+    // FP8 products where a block needs at most four of them (the search
+    // kernel's rule), else the FP16 layout its conversions expect
+    const int k32 = tiles * (hks / 2) <= 4;
     k_lp_codes<<<(unsigned)((units + 255) / 256), 256>>>(ix->edge_u, n, ix->deg0, ix->r_pad, tiles,
-                                                         hks / 2, ix->code_scale,
+                                                         hks / 2, ix->code_scale, k32,
                                                          reinterpret_cast<uint4*>(ix->edge_q));
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaDeviceSynchronize();

@@ -50,15 +50,18 @@ def _f16(fp):
     return dataclasses.replace(fp, codes=16)
 
 
-def _f8(fp):
+def _f8(fp, deg0=32):
     """The oracle's FINGER parameters with the per-edge codes stored as FP8 E4M3
-    codes of 256 u."""
-    return dataclasses.replace(fp, codes=8)
+    codes of 256 u: u_q split into E4M3 parts where the kernel multiplies in
+    FP8 (at most four products per code block: not both deg0 > 32 and r > 32),
+    else u_q itself."""
+    tiles, kp = (4 if deg0 > 32 else 2), (2 if fp.P.shape[0] > 32 else 1)
+    return dataclasses.replace(fp, codes=8 if tiles * kp <= 4 else 9)
 
 
-def _modes(fp):
+def _modes(fp, deg0=32):
     return ((fg.MODE_PLAIN, None), (fg.MODE_FINGER, fp), (fg.MODE_FINGER_F16, _f16(fp)),
-            (fg.MODE_FINGER_F8, _f8(fp)))
+            (fg.MODE_FINGER_F8, _f8(fp, deg0)))
 
 
 def test_bruteforce_knn_matches_oracle(cfg1):
@@ -296,7 +299,7 @@ def test_wide_codes_two_row_groups():
     assert ix.info()["deg0"] == 64
     q = torch.from_numpy(Q).cuda()
     gt, _ = oracle.bruteforce(X, Q, 10)
-    for mode, f in _modes(fp)[1:]:
+    for mode, f in _modes(fp, 64)[1:]:
         gi, gd, gc = _gpu_search(ix, q, 10, 80, mode)
         oi, od, oc = oracle.search(g, X, Q, 10, 80, f)
         _compare(gi, gd, gc, oi, od, oc, gt, 10, f"deg0=64 r=64 mode={mode}")
@@ -305,7 +308,7 @@ def test_wide_codes_two_row_groups():
     # candidates take the serial replay
     gt2, _ = oracle.bruteforce(X, Q, 2)
     for ef in (2, 4):
-        for mode, f in _modes(fp):
+        for mode, f in _modes(fp, 64):
             gi, gd, gc = _gpu_search(ix, q, 2, ef, mode)
             oi, od, oc = oracle.search(g, X, Q, 2, ef, f)
             _compare(gi, gd, gc, oi, od, oc, gt2, 2, f"deg0=64 ef={ef} mode={mode}")

@@ -159,6 +159,16 @@ def test_estimate_fp8_codes_query_split_hand_example():
     assert oracle.estimate(q, c, d, fp) == 31.540283203125
 
 
+def test_estimate_fp8_codes_exact_query_hand_example():
+    """codes = 9: the FP8 codes (160, 208) / 256 against u_q = (0.6, 0.8)
+    itself: t_hat = (0.6 * 160 + 0.8 * 208) / 256 = 1.025, estimate 31.5."""
+    P = np.array([[1.0, 0, 0], [0, 1.0, 0]])
+    q, c, d = np.array([6.0, 8, 2]), np.array([0, 0, 1.0]), np.array([3.0, 4, 5])
+    fp = _stats(P=P)
+    fp.codes = 9
+    assert oracle.estimate(q, c, d, fp) == pytest.approx(31.5, abs=1e-12)
+
+
 def test_estimate_full_rank_is_exact_distance():
     """Eq. (2): with an orthogonal P (r = m) and identity matching the estimate
     is ||q - d||^2 exactly (the cross term q_proj^T q_res vanishes)."""
